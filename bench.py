@@ -1,0 +1,383 @@
+"""Benchmark of the BOS forward model (and its adjoint) on one GB300, one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload room_adj|room_fwd]
+                    [--prec fp32_comp|bf16_comp|fp32|fp64] [--impl ours|reference]
+
+A step is one pass of the whole hot path over one frame of synthetic input:
+  room_adj  (default) 256x256x192 plume grid, 2048^2 camera, 1 ray/pixel:
+            build the field store from T, render I_flow saving checkpoints every 16 steps,
+            L_BOS against a seeded target image, backward to dL/dT.
+  room_fwd  128x128x96 plume grid, 1024^2 camera, 4 jittered rays/pixel: build the
+            field store, render I_flow with the displacement field, render I_ref.
+Metric: ray-steps per second, one ray-step = one integrator step of one ray (sum of the
+per-ray step counts N of the flow render), whole job (all ranks).
+
+Under torchrun every rank renders its own frame (independent seeds): weak scaling, no
+collective on the data path (the barrier only brackets the timing).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload on
+the host cores (the only GPU-free arm; it needs no GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2509_14442_gb300 import scenes as S  # noqa: E402
+
+WORKLOADS = {
+    "room_adj": dict(desc="room 256x256x192 plume, 2048^2 camera, 1 spp, forward + adjoint (K=16)",
+                     make=lambda seed: S.room_adjoint(seed), adjoint=True),
+    "room_fwd": dict(desc="room 128x128x96 plume, 1024^2 camera, 4 jittered spp, forward + I_ref",
+                     make=lambda seed: S.room_forward(seed), adjoint=False),
+    # small case of the same kernels for profiler captures (not a benchmark line)
+    "room_fwd_small": dict(desc="room 128x128x96 plume, 256^2 camera, 4 jittered spp, forward + I_ref",
+                           make=lambda seed: S.room((128, 128, 96), 256, 256, 4, seed), adjoint=False),
+    "room_adj_small": dict(desc="room 256x256x192 plume, 512^2 camera, 1 spp, forward + adjoint (K=16)",
+                           make=lambda seed: S.room((256, 256, 192), 512, 512, 1, seed), adjoint=True),
+}
+# Algorithmic bytes of one Sharma ray-step of the float32 store: 3 field evaluations x 8
+# trilinear corners x one 16-byte (deta, grad eta) record.
+BYTES_PER_STEP = {"fp32_comp": 384, "fp32": 384, "bf16_comp": 192, "fp64": 768}
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--workload", default="room_fwd", choices=sorted(WORKLOADS))
+    p.add_argument("--prec", default="fp32_comp", choices=sorted(BYTES_PER_STEP))
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ oracle (CPU) arm
+
+def oracle_rate(scene, adjoint: bool, seconds: float, seed: int = 0):
+    """Time the FP64 oracle on a pixel sample sized for ~`seconds` on all host cores.
+    Returns (ray-steps/s, threads, sample description)."""
+    from oracle import oracle as O
+
+    O.build()
+    threads = os.cpu_count() or 1
+    field = O.field_from_T(scene.grid, scene.T)
+    rng = np.random.default_rng(seed)
+    npix = scene.pixels
+
+    def run(pix):
+        t0 = time.perf_counter()
+        out = O.render(scene, field=field, pix=pix, threads=threads, nsteps=True)
+        steps = int(out["nsteps"].sum())
+        if adjoint:
+            w = np.zeros((scene.camera.height, scene.camera.width))
+            w.reshape(-1)[pix] = 1.0
+            O.grad(scene, w, threads=threads)
+        return steps, time.perf_counter() - t0
+
+    probe = np.sort(rng.choice(npix, min(npix, 2000), replace=False))
+    s0, t0 = run(probe)
+    per_pix = t0 / len(probe)
+    m = int(min(npix, max(len(probe), seconds / max(per_pix, 1e-9))))
+    pix = np.sort(rng.choice(npix, m, replace=False))
+    steps, t = run(pix)
+    kind = "forward + adjoint" if adjoint else "forward"
+    return steps / t, threads, f"{m} of {npix} pixels ({kind}), {steps} ray-steps in {t:.1f} s"
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    scene = wl["make"](S.BASE_SEED + 2 if wl["adjoint"] else S.BASE_SEED + 1)
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    rates = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        r, threads, desc = oracle_rate(scene, wl["adjoint"], per_step, seed=i)
+        if i >= args.warmup:
+            rates.append(r)
+    v = statistics.mean(rates)
+    unit = "ray-steps/s"
+    print(json.dumps({
+        "impl": "reference", "metric": metric_name(args), "value": v, "unit": unit, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args, wl, None),
+        "cpu_baseline": {"value": v, "unit": unit, "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def metric_name(args):
+    wl = WORKLOADS[args.workload]
+    return "ray-steps/s (forward + adjoint)" if wl["adjoint"] else "ray-steps/s (forward)"
+
+
+def config_of(args, wl, scene):
+    c = {"workload": args.workload, "description": wl["desc"], "prec": args.prec,
+         "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{args.gpus}"}
+    if scene is not None:
+        c.update(grid=list(scene.grid.n), image=[scene.camera.width, scene.camera.height],
+                 spp=scene.camera.spp, ckpt_every=scene.integ.ckpt_every)
+    return c
+
+
+class Clocks:
+    """nvidia-smi samples (every 100 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def l2_copy_peak(torch, dev):
+    """L2-resident copy bandwidth (read + write) of a 32 MiB buffer, best of 20."""
+    a = torch.empty(8 * 2 ** 20, dtype=torch.float32, device=dev).fill_(1.0)
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    best = 1e30
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 10)
+    return 2 * a.numel() * 4 / (best * 1e-3) / 1e9
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_14442_gb300 import bos
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[args.workload]
+    prec = bos.PRECISIONS[args.prec]
+    scene = wl["make"]((S.BASE_SEED + 2 if wl["adjoint"] else S.BASE_SEED + 1) + 1000 * rank)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    T_host = torch.from_numpy(np.ascontiguousarray(scene.T)).pin_memory()
+    T = T_host.to(dev)
+    ctx = bos.Context(local)
+    ctx.set_scene(scene, prec, T=T)
+    H, W = scene.camera.height, scene.camera.width
+    I = torch.empty((H, W), dtype=torch.float32, device=dev)
+    Iref = torch.empty_like(I)
+    disp = torch.empty((H, W, 2), dtype=torch.float32, device=dev)
+    target = None
+    if wl["adjoint"]:
+        # target image: a render of the same plume family drawn with the next seed
+        Tt = torch.from_numpy(S.with_target_seed(scene, scene.camera.seed % 100000 + 1)).to(dev)
+        ctx.set_grid(scene.grid, Tt, prec)
+        target = torch.empty_like(I)
+        ctx.render(disp=False, out=(target, None, None))
+        ctx.set_grid(scene.grid, T, prec)
+        target_host = target.cpu().pin_memory()
+    loss = torch.empty((1,), dtype=torch.float64, device=dev)
+    dLdI = torch.empty_like(I)
+    dLdT = torch.empty_like(T)
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    ev_r = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    launches_per_step = 0
+
+    def step(T_in, ev=None):
+        nonlocal launches_per_step
+        L = bos.lib()
+        bos.check(L.bos_set_grid(ctx.h, bos.C.byref(bos.grid_desc(scene.grid, prec)), T_in.data_ptr(), sp),
+                  "set_grid")
+        if ev is not None:
+            ev[0].record(stream)
+        if wl["adjoint"]:
+            bos.check(L.bos_render(ctx.h, I.data_ptr(), None, None, 1, sp), "render")
+        else:
+            bos.check(L.bos_render(ctx.h, I.data_ptr(), disp.data_ptr(), None, 0, sp), "render")
+        if ev is not None:
+            ev[1].record(stream)
+        if wl["adjoint"]:
+            bos.check(L.bos_loss_l2(I.data_ptr(), target.data_ptr(), I.numel(), loss.data_ptr(), dLdI.data_ptr(),
+                                    sp), "loss")
+            bos.check(L.bos_backward(ctx.h, dLdI.data_ptr(), dLdT.data_ptr(), sp), "backward")
+            launches_per_step = 5          # build_store, render, loss_l2, adjoint, gradient
+        else:
+            bos.check(L.bos_render_reference(ctx.h, Iref.data_ptr(), None, None, sp), "render_ref")
+            launches_per_step = 3          # build_store, render, render (reference)
+
+    for _ in range(args.warmup):
+        step(T)
+    torch.cuda.synchronize()
+    ctx.status()
+    steps_per_frame = ctx.last_ray_steps()
+
+    # ---- timed region: device time of K steps, L2 flushed between steps
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    step_ms, render_ms = [], []
+    with clocks:
+        for _ in range(args.steps):
+            flush.fill_(0.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(T, ev_r)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            render_ms.append(ev_r[0].elapsed_time(ev_r[1]))
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ctx.status()
+    my_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([my_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        my_ms = float(t.item())
+    total_ms = my_ms
+    value = steps_per_frame * world * args.steps / (total_ms * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers: H2D inputs, D2H result
+    e2e_ms = []
+    h2d = T_host.numel() * 4 + (target_host.numel() * 4 if target is not None else 0)
+    out_host = torch.empty_like(dLdT if wl["adjoint"] else I, device="cpu").pin_memory()
+    loss_host = torch.empty((1,), dtype=torch.float64).pin_memory()
+    d2h = out_host.numel() * 4 + (8 if wl["adjoint"] else 0)
+    T_dev2 = torch.empty_like(T)
+    for i in range(args.warmup + args.steps):
+        flush.fill_(0.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        T_dev2.copy_(T_host, non_blocking=True)
+        if target is not None:
+            target.copy_(target_host, non_blocking=True)
+        step(T_dev2)
+        if wl["adjoint"]:
+            out_host.copy_(dLdT, non_blocking=True)
+            loss_host.copy_(loss, non_blocking=True)
+        else:
+            out_host.copy_(I, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = steps_per_frame * args.steps / (sum(e2e_ms) * 1e-3) * world
+
+    # ---- roofline of the tracer (the dominant forward kernel)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    l2_peak = l2_copy_peak(torch, dev)
+    render_avg_ms = statistics.mean(render_ms)
+    achieved = BYTES_PER_STEP[args.prec] * steps_per_frame / (render_avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "l2", "kernel": "render_kernel (tracer)", "achieved": achieved, "peak": l2_peak,
+                "unit": "GB/s", "frac": achieved / l2_peak, "traffic": None,
+                "peak_source": "in-run L2-resident copy of 32 MiB (read + write), best of 20",
+                "bytes_per_ray_step": BYTES_PER_STEP[args.prec],
+                "render_ms": render_avg_ms,
+                "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                "hbm_algorithmic_gbs": (scene.grid.cells * 16 * 1.42 + scene.pixels * 4) / (render_avg_ms * 1e-3) / 1e9}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r, threads, desc = oracle_rate(scene, wl["adjoint"], args.cpu_seconds)
+        cpu = {"value": r, "unit": "ray-steps/s", "cores": threads, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps({
+            "metric": metric_name(args), "value": value, "unit": "ray-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded plume fields and speckle patterns)",
+            "config": config_of(args, wl, scene),
+            "ray_steps_per_frame": steps_per_frame,
+            "clocks": clocks.summary(),
+            "e2e": {"value": e2e_value, "unit": "ray-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+        }))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * bos.h -- C ABI of the GB300 (sm_103a) BOS forward model and its adjoint.
+ *
+ * The library renders what a camera sees of a patterned back wall through a
+ * heated, refracting air volume, and differentiates an image loss with respect
+ * to the temperature field (single-view background-oriented schlieren,
+ * arxiv 2509.14442):
+ *
+ *   a1  eta(T) = 1 + rho0 G T0 / T on the cell grid, grad eta by central
+ *       differences (Sec. 2.1), stored in bricks              -> bos_set_grid
+ *   a2  pinhole rays, tent-filter Monte Carlo over each pixel (Sec. 2.3)
+ *   a3  nonlinear ray tracing dr/dt = v, dv/dt = eta grad eta (Sec. 2.2, Eq. 1)
+ *       with Sharma's Runge-Kutta-Nystrom steps
+ *   a4  straight extrapolation to the back wall
+ *   a5  radiance L_wall <n_w, v_w> / |path| per ray, averaged over the pixel
+ *       (Sec. 2.3, Eq. 2)                                      -> bos_render
+ *   a6  gradient of L_BOS = sum_j (I_flow_j - I_j)^2 (Sec. 2.4) with respect
+ *       to T by a discrete adjoint                            -> bos_backward
+ *
+ * Conventions (every call):
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *    library never frees them.  The library owns its own device buffers (the
+ *    brick store, checkpoints, accumulators) and frees them in bos_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Every call that launches work is asynchronous on that stream and
+ *    returns as soon as the work is enqueued.
+ *  - Every call returns a bos_status_t; no exception or abort crosses the ABI.
+ *    bos_last_error() gives a message for the most recent failure on the
+ *    calling thread.  Errors found by a kernel (bounded waits that timed out,
+ *    step budgets exceeded) are sticky in the context and read by bos_status()
+ *    after the caller has synchronised the stream.
+ *  - A context is not thread-safe: use one context per host thread / stream.
+ *  - Layouts: T is (nz, ny, nx) float32, x fastest.  Images are (height, width)
+ *    row-major, row 0 at the top.  Wall coordinates are metres along (eu, ev).
+ */
+#ifndef BOS_H
+#define BOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bos_ctx bos_ctx;
+
+typedef enum {
+    BOS_OK = 0,
+    BOS_ERR_INVALID_ARG = 1,   /* a descriptor or pointer failed validation */
+    BOS_ERR_NOT_READY = 2,     /* a call needs set_grid / set_geometry / a saved render first */
+    BOS_ERR_OOM = 3,           /* a device allocation failed or would exceed the context limit */
+    BOS_ERR_ADMISSION = 4,     /* the request does not fit the server's memory limit */
+    BOS_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    BOS_ERR_TIMEOUT = 6,       /* a bounded wait ran out */
+    BOS_ERR_DEVICE_CHECK = 7,  /* a kernel flagged an error (see bos_last_error) */
+    BOS_ERR_UNIMPLEMENTED = 8  /* the combination of options is not supported */
+} bos_status_t;
+
+/* Arithmetic of the field store and of the integrator.
+ *  FP64:       float64 store (32 B per cell), float64 ray state.
+ *  FP32:       float32 store (16 B per cell), plain float32 absolute ray state.
+ *  FP32_COMP:  float32 store; each ray keeps its straight line in 32.32 fixed
+ *              point (grid units) derived from its float64 origin and integrates
+ *              only its small deviation from that line in float32 with
+ *              compensated (Kahan) sums; float64 only at the ray origin and the
+ *              wall intersection.
+ *  BF16_COMP:  as FP32_COMP with a bfloat16 store (8 B per cell). */
+typedef enum {
+    BOS_PREC_FP64 = 0,
+    BOS_PREC_FP32 = 1,
+    BOS_PREC_FP32_COMP = 2,
+    BOS_PREC_BF16_COMP = 3
+} bos_precision_t;
+
+/* Voxel grid: nx*ny*nz cells over the box [origin, origin + extent]; the
+ * sample of cell (i, j, k) sits at its centre origin + (i + 1/2, j + 1/2, k + 1/2) h,
+ * h = extent / n.  T0 (K), rho0 (kg/m^3) and G (m^3/kg) enter eta(T) = 1 + rho0 G T0 / T
+ * (Sec. 2.1).  Requires 2 <= n <= 8192 along every axis and fewer than 2^31 cells,
+ * extent > 0, T0 rho0 G > 0. */
+typedef struct {
+    int nx, ny, nz;
+    double origin[3];
+    double extent[3];
+    double T0, rho0, G;
+    int prec;                   /* bos_precision_t */
+} bos_grid_desc;
+
+/* Pinhole camera (and projector): position, unit viewing direction `fwd`, unit
+ * `up` orthogonal to it; right = fwd x up.  Image point (x, y) in pixels (y down)
+ * looks along normalise(((x - cx)/fx) right - ((y - cy)/fy) up + fwd).
+ * spp rays per pixel: one ray through the pixel centre if spp == 1, otherwise
+ * tent-filter (radius 1 px) offsets drawn from splitmix64 output k = 1 + (pixel*spp + s)
+ * for `seed` (Sec. 2.3: triangular filter, Monte Carlo over the pixel). */
+typedef struct {
+    double pos[3], fwd[3], up[3];
+    double fx, fy, cx, cy;
+    int width, height, spp;
+    uint64_t seed;
+} bos_camera_desc;
+
+/* Back-wall plane through `origin` spanned by unit eu, ev; unit `normal` points
+ * away from the camera (so <normal, v> > 0 for rays that reach it). */
+typedef struct {
+    double origin[3], eu[3], ev[3], normal[3];
+    double size_u, size_v;
+} bos_wall_desc;
+
+/* Wall luminance (Sec. 2.3): mode 0 -- a tw x th texture covering the wall
+ * rectangle [0, size_u] x [0, size_v]; mode 1 -- a pinhole projector `proj`
+ * casting a tw x th pattern, connected to the wall point by a straight line.
+ * Both are bilinear on texel centres and zero outside the pattern. */
+typedef struct {
+    int mode;
+    bos_camera_desc proj;
+    int tw, th;
+} bos_light_desc;
+
+/* Integrator: fixed_steps > 0 gives every ray that many steps, otherwise
+ * N = ceil(ell / (max_step_vox * min h)) for the straight in-box segment of
+ * length ell.  integrator 0 = Sharma's Runge-Kutta-Nystrom, 1 = classic RK4
+ * (forward only).  ckpt_every = K: the adjoint keeps the ray state every K steps. */
+typedef struct {
+    int fixed_steps;
+    double max_step_vox;
+    int integrator;
+    int ckpt_every;
+} bos_integrator_desc;
+
+/* Create a context on CUDA `device`.  mem_limit_bytes caps the library's own
+ * device allocations (0 = no cap); exceeding it gives BOS_ERR_OOM. */
+bos_status_t bos_create(bos_ctx** out, int device, uint64_t mem_limit_bytes);
+
+/* Free every buffer the context owns.  The caller must have synchronised the
+ * streams the context used.  NULL is accepted. */
+bos_status_t bos_destroy(bos_ctx* ctx);
+
+/* Step a1 (Sec. 2.1): build the field store from T_dev (nz*ny*nx float32 kelvin,
+ * all > 0).  Per cell, in float64: deta = rho0 G T0 / T; grad eta by central
+ * differences (deta[i+1] - deta[i-1]) / (2h), one-sided (deta[1]-deta[0])/h at the
+ * faces; then rounded to the store type of desc->prec.  The store is a Morton-ordered
+ * array of 8x8x8-cell bricks with a one-cell apron, so every trilinear corner is one
+ * 16-byte (bf16: 8-byte, fp64: 32-byte) load at a fixed offset.
+ * T_dev must stay allocated and unchanged until the last bos_backward that uses
+ * this grid (the adjoint's chain rule d eta / dT = -rho0 G T0 / T^2 reads it). */
+bos_status_t bos_set_grid(bos_ctx* ctx, const bos_grid_desc* desc, const float* T_dev, void* stream);
+
+/* Camera, wall, light and integrator (Sec. 2.3).  Descriptors are copied;
+ * pattern_dev (th*tw float32, row 0 = v 0 for a texture, = top row for a
+ * projector) is caller-owned and must stay valid until the last render/backward. */
+bos_status_t bos_set_geometry(bos_ctx* ctx, const bos_camera_desc* cam, const bos_wall_desc* wall,
+                              const bos_light_desc* light, const float* pattern_dev,
+                              const bos_integrator_desc* integ);
+
+/* Steps a2-a5 (Eq. 1, Eq. 2): trace every ray of every pixel through the field
+ * and write per pixel
+ *   I_dev    (height*width float32): mean over the pixel's rays of L_wall <n_w, v_w>/(|v_w| len),
+ *   disp_dev (height*width*2 float32, nullable): mean wall-plane displacement of the
+ *            hit from the straight (no-flow) hit of the same ray, metres along (eu, ev),
+ *   hit_dev  (height*width*2 float64, nullable): mean wall coordinates of the hits.
+ * Rays that never reach the wall plane contribute zero.  save_for_backward != 0
+ * stores the ray state every ckpt_every steps for bos_backward (Sharma RKN, and the
+ * FP32_COMP / BF16_COMP / FP64 precisions). */
+bos_status_t bos_render(bos_ctx* ctx, float* I_dev, float* disp_dev, double* hit_dev, int save_for_backward,
+                        void* stream);
+
+/* The reference image I_ref (Sec. 2.1: no flow): the same rays, straight, with
+ * the ambient index.  Same outputs as bos_render. */
+bos_status_t bos_render_reference(bos_ctx* ctx, float* I_dev, float* disp_dev, double* hit_dev, void* stream);
+
+/* Step count of every ray (height*width*spp int32, ray = pixel*spp + s): the
+ * integer decision of step a2, for checks. */
+bos_status_t bos_ray_steps(bos_ctx* ctx, int32_t* nsteps_dev, void* stream);
+
+/* Total ray-steps of the most recent bos_render (sum over rays of N), read after
+ * the render's stream has been synchronised. */
+bos_status_t bos_last_ray_steps(bos_ctx* ctx, uint64_t* out);
+
+/* L_BOS (Sec. 2.4) for n pixels: loss_dev (1 float64) = sum_j (target_j - I_j)^2 and
+ * dLdI_dev (n float32, nullable) = -2 (target_j - I_j). */
+bos_status_t bos_loss_l2(const float* I_dev, const float* target_dev, int64_t n, double* loss_dev,
+                         float* dLdI_dev, void* stream);
+
+/* Step a6 (Sec. 2.4): given dL/dI (height*width float32) for the most recent
+ * bos_render(save_for_backward=1), write dL/dT (nz*ny*nx float32).  Needs the
+ * FP32_COMP or BF16_COMP precision, Sharma RKN and ckpt_every <= 64 (else
+ * BOS_ERR_UNIMPLEMENTED).  dLdI_dev must not alias the accumulators.  Reverses the
+ * Sharma steps of every ray from its checkpoints, scatters d L / d(deta, grad eta)
+ * into the grid with warp-aggregated atomics, then applies the transpose of the
+ * difference stencil and d deta/dT = -rho0 G T0 / T^2. */
+bos_status_t bos_backward(bos_ctx* ctx, const float* dLdI_dev, float* dLdT_dev, void* stream);
+
+/* Copy the stored node values back in grid order: out_dev receives nz*ny*nx*4
+ * values (deta, d eta/dx, d eta/dy, d eta/dz) of the store type (float32, bf16 as
+ * uint16 bit patterns, or float64), read through the brick addressing. */
+bos_status_t bos_export_nodes(bos_ctx* ctx, void* out_dev, void* stream);
+
+/* Sticky device-side status of the context (call after synchronising). */
+bos_status_t bos_status(bos_ctx* ctx);
+
+/* Static description of a status code. */
+const char* bos_error_string(bos_status_t s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* bos_last_error(void);
+
+/* Bytes of device memory the context currently owns. */
+uint64_t bos_device_bytes(bos_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BOS_H */

@@ -894,6 +894,7 @@ void orc_grad(const orc_grid* g, const double* T, const orc_camera* cam, const o
         for (;;) {
             long p = next.fetch_add(1);
             if (p >= npix) break;
+            if (dLdI[p] == 0.0) continue;   // no sensitivity: nothing to propagate
             for (int s = 0; s < spp; ++s) {
                 RayGeom R = pixel_ray(sc, p, s);
                 ray_adjoint(sc, F, R, dLdI[p] / spp, acc, tape);

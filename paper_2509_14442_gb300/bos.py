@@ -1,0 +1,342 @@
+"""Thin ctypes binding of the BOS C ABI (include/bos.h) with the same names.
+
+Argument marshalling only: every step of the forward model and of its adjoint runs
+in the CUDA library (libbos.so, built in-tree for sm_103a).  PyTorch provides device
+memory and streams.  There is no CPU fallback: if the library cannot be loaded the
+import of `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+BOS_OK = 0
+BOS_ERR_INVALID_ARG = 1
+BOS_ERR_NOT_READY = 2
+BOS_ERR_OOM = 3
+BOS_ERR_ADMISSION = 4
+BOS_ERR_CUDA = 5
+BOS_ERR_TIMEOUT = 6
+BOS_ERR_DEVICE_CHECK = 7
+BOS_ERR_UNIMPLEMENTED = 8
+
+BOS_PREC_FP64 = 0
+BOS_PREC_FP32 = 1
+BOS_PREC_FP32_COMP = 2
+BOS_PREC_BF16_COMP = 3
+
+PRECISIONS = {"fp64": BOS_PREC_FP64, "fp32": BOS_PREC_FP32, "fp32_comp": BOS_PREC_FP32_COMP,
+              "bf16_comp": BOS_PREC_BF16_COMP}
+
+
+class BosError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+class bos_grid_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("origin", C.c_double * 3),
+                ("extent", C.c_double * 3), ("T0", C.c_double), ("rho0", C.c_double), ("G", C.c_double),
+                ("prec", C.c_int)]
+
+
+class bos_camera_desc(C.Structure):
+    _fields_ = [("pos", C.c_double * 3), ("fwd", C.c_double * 3), ("up", C.c_double * 3), ("fx", C.c_double),
+                ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double), ("width", C.c_int),
+                ("height", C.c_int), ("spp", C.c_int), ("seed", C.c_uint64)]
+
+
+class bos_wall_desc(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("eu", C.c_double * 3), ("ev", C.c_double * 3),
+                ("normal", C.c_double * 3), ("size_u", C.c_double), ("size_v", C.c_double)]
+
+
+class bos_light_desc(C.Structure):
+    _fields_ = [("mode", C.c_int), ("proj", bos_camera_desc), ("tw", C.c_int), ("th", C.c_int)]
+
+
+class bos_integrator_desc(C.Structure):
+    _fields_ = [("fixed_steps", C.c_int), ("max_step_vox", C.c_double), ("integrator", C.c_int),
+                ("ckpt_every", C.c_int)]
+
+
+# every exported symbol of include/bos.h: name -> (restype, argtypes)
+_v, _i, _u64, _i64, _d = C.c_void_p, C.c_int, C.c_uint64, C.c_int64, C.c_double
+_P = C.POINTER
+SIGNATURES = {
+    "bos_create": (_i, [_P(_v), _i, _u64]),
+    "bos_destroy": (_i, [_v]),
+    "bos_set_grid": (_i, [_v, _P(bos_grid_desc), _v, _v]),
+    "bos_set_geometry": (_i, [_v, _P(bos_camera_desc), _P(bos_wall_desc), _P(bos_light_desc), _v,
+                              _P(bos_integrator_desc)]),
+    "bos_render": (_i, [_v, _v, _v, _v, _i, _v]),
+    "bos_render_reference": (_i, [_v, _v, _v, _v, _v]),
+    "bos_ray_steps": (_i, [_v, _v, _v]),
+    "bos_last_ray_steps": (_i, [_v, _P(_u64)]),
+    "bos_loss_l2": (_i, [_v, _v, _i64, _v, _v, _v]),
+    "bos_backward": (_i, [_v, _v, _v, _v]),
+    "bos_export_nodes": (_i, [_v, _v, _v]),
+    "bos_status": (_i, [_v]),
+    "bos_error_string": (C.c_char_p, [_i]),
+    "bos_last_error": (C.c_char_p, []),
+    "bos_device_bytes": (_u64, [_v]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build: bool = True):
+    """Load libbos.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"BOS CUDA library not found at {path}; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status: int, where: str) -> None:
+    if status != BOS_OK:
+        L = lib()
+        msg = L.bos_last_error().decode() or L.bos_error_string(status).decode()
+        raise BosError(status, where, msg)
+
+
+# ------------------------------------------------------------------ descriptors
+
+def _v3(x):
+    return (C.c_double * 3)(*[float(a) for a in x])
+
+
+def grid_desc(g, prec: int) -> bos_grid_desc:
+    return bos_grid_desc(g.n[0], g.n[1], g.n[2], _v3(g.origin), _v3(g.extent), g.T0, g.rho0, g.G, prec)
+
+
+def camera_desc(c) -> bos_camera_desc:
+    return bos_camera_desc(_v3(c.pos), _v3(c.fwd), _v3(c.up), c.fx, c.fy, c.cx, c.cy, c.width, c.height, c.spp,
+                           int(c.seed) & 0xFFFFFFFFFFFFFFFF)
+
+
+def wall_desc(w) -> bos_wall_desc:
+    return bos_wall_desc(_v3(w.origin), _v3(w.eu), _v3(w.ev), _v3(w.normal), w.size_u, w.size_v)
+
+
+def light_desc(L) -> bos_light_desc:
+    th, tw = L.pattern.shape
+    proj = camera_desc(L.proj) if L.proj is not None else bos_camera_desc()
+    return bos_light_desc(L.mode, proj, tw, th)
+
+
+def integ_desc(it) -> bos_integrator_desc:
+    return bos_integrator_desc(it.fixed_steps, it.max_step_vox, it.integrator, it.ckpt_every)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+# ------------------------------------------------------------------ raw calls (same names)
+
+def bos_create(device: int = 0, mem_limit_bytes: int = 0) -> int:
+    h = C.c_void_p()
+    check(lib().bos_create(C.byref(h), device, mem_limit_bytes), "bos_create")
+    return h.value
+
+
+def bos_destroy(ctx: int) -> None:
+    check(lib().bos_destroy(ctx), "bos_destroy")
+
+
+def bos_set_grid(ctx: int, desc: bos_grid_desc, T_dev: int, stream: int) -> None:
+    check(lib().bos_set_grid(ctx, C.byref(desc), T_dev, stream), "bos_set_grid")
+
+
+def bos_set_geometry(ctx, cam, wall, light, pattern_dev, integ) -> None:
+    check(lib().bos_set_geometry(ctx, C.byref(cam), C.byref(wall), C.byref(light), pattern_dev, C.byref(integ)),
+          "bos_set_geometry")
+
+
+def bos_render(ctx, I_dev, disp_dev, hit_dev, save_for_backward: int, stream) -> None:
+    check(lib().bos_render(ctx, I_dev, disp_dev, hit_dev, int(save_for_backward), stream), "bos_render")
+
+
+def bos_render_reference(ctx, I_dev, disp_dev, hit_dev, stream) -> None:
+    check(lib().bos_render_reference(ctx, I_dev, disp_dev, hit_dev, stream), "bos_render_reference")
+
+
+def bos_ray_steps(ctx, nsteps_dev, stream) -> None:
+    check(lib().bos_ray_steps(ctx, nsteps_dev, stream), "bos_ray_steps")
+
+
+def bos_last_ray_steps(ctx) -> int:
+    v = C.c_uint64()
+    check(lib().bos_last_ray_steps(ctx, C.byref(v)), "bos_last_ray_steps")
+    return v.value
+
+
+def bos_loss_l2(I_dev, target_dev, n: int, loss_dev, dLdI_dev, stream) -> None:
+    check(lib().bos_loss_l2(I_dev, target_dev, n, loss_dev, dLdI_dev, stream), "bos_loss_l2")
+
+
+def bos_backward(ctx, dLdI_dev, dLdT_dev, stream) -> None:
+    check(lib().bos_backward(ctx, dLdI_dev, dLdT_dev, stream), "bos_backward")
+
+
+def bos_export_nodes(ctx, out_dev, stream) -> None:
+    check(lib().bos_export_nodes(ctx, out_dev, stream), "bos_export_nodes")
+
+
+def bos_status(ctx) -> None:
+    check(lib().bos_status(ctx), "bos_status")
+
+
+def bos_device_bytes(ctx) -> int:
+    return int(lib().bos_device_bytes(ctx))
+
+
+# ------------------------------------------------------------------ tensor-level context
+
+class Context:
+    """A BOS context bound to torch tensors.  Holds the T and pattern tensors it was
+    given for as long as the library may read them."""
+
+    def __init__(self, device: int = 0, mem_limit_bytes: int = 0):
+        import torch
+
+        self.device = device
+        self.torch_device = torch.device("cuda", device)
+        self.h = bos_create(device, mem_limit_bytes)
+        self.T = None
+        self.pattern = None
+        self.scene = None
+        self.prec = None
+
+    def close(self):
+        if self.h:
+            import torch
+
+            torch.cuda.synchronize(self.torch_device)
+            bos_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_grid(self, grid, T, prec: int = BOS_PREC_FP32_COMP, stream=None):
+        import torch
+
+        assert T.is_cuda and T.dtype == torch.float32 and T.is_contiguous()
+        assert tuple(T.shape) == (grid.n[2], grid.n[1], grid.n[0])
+        bos_set_grid(self.h, grid_desc(grid, prec), T.data_ptr(), _stream(stream))
+        self.T = T
+        self.grid = grid
+        self.prec = prec
+
+    def set_geometry(self, camera, wall, light, integ, pattern=None):
+        import torch
+
+        pat = pattern if pattern is not None else torch.as_tensor(np.ascontiguousarray(light.pattern),
+                                                                  device=self.torch_device)
+        assert pat.is_cuda and pat.dtype == torch.float32 and pat.is_contiguous()
+        bos_set_geometry(self.h, camera_desc(camera), wall_desc(wall), light_desc(light), pat.data_ptr(),
+                         integ_desc(integ))
+        self.pattern = pat
+        self.camera = camera
+
+    def set_scene(self, scene, prec: int = BOS_PREC_FP32_COMP, T=None, stream=None):
+        import torch
+
+        if T is None:
+            T = torch.as_tensor(np.ascontiguousarray(scene.T, dtype=np.float32), device=self.torch_device)
+        self.set_grid(scene.grid, T, prec, stream)
+        self.set_geometry(scene.camera, scene.wall, scene.light, scene.integ)
+        self.scene = scene
+
+    def _outputs(self, disp: bool, hit: bool):
+        import torch
+
+        H, W = self.camera.height, self.camera.width
+        I = torch.empty((H, W), dtype=torch.float32, device=self.torch_device)
+        D = torch.empty((H, W, 2), dtype=torch.float32, device=self.torch_device) if disp else None
+        X = torch.empty((H, W, 2), dtype=torch.float64, device=self.torch_device) if hit else None
+        return I, D, X
+
+    def render(self, disp: bool = True, hit: bool = False, save_for_backward: bool = False, stream=None, out=None):
+        I, D, X = out if out is not None else self._outputs(disp, hit)
+        bos_render(self.h, _ptr(I), _ptr(D), _ptr(X), int(save_for_backward), _stream(stream))
+        return I, D, X
+
+    def render_reference(self, disp: bool = False, hit: bool = False, stream=None):
+        I, D, X = self._outputs(disp, hit)
+        bos_render_reference(self.h, _ptr(I), _ptr(D), _ptr(X), _stream(stream))
+        return I, D, X
+
+    def ray_steps(self, stream=None):
+        import torch
+
+        c = self.camera
+        n = torch.empty((c.height * c.width * c.spp,), dtype=torch.int32, device=self.torch_device)
+        bos_ray_steps(self.h, n.data_ptr(), _stream(stream))
+        return n
+
+    def last_ray_steps(self) -> int:
+        return bos_last_ray_steps(self.h)
+
+    def export_nodes(self, stream=None):
+        import torch
+
+        g = self.grid
+        shape = (g.n[2], g.n[1], g.n[0], 4)
+        dt = {BOS_PREC_FP64: torch.float64, BOS_PREC_BF16_COMP: torch.int16}.get(self.prec, torch.float32)
+        out = torch.empty(shape, dtype=dt, device=self.torch_device)
+        bos_export_nodes(self.h, out.data_ptr(), _stream(stream))
+        return out
+
+    def backward(self, dLdI, stream=None):
+        import torch
+
+        assert dLdI.is_cuda and dLdI.dtype == torch.float32 and dLdI.is_contiguous()
+        dT = torch.empty_like(self.T)
+        bos_backward(self.h, dLdI.data_ptr(), dT.data_ptr(), _stream(stream))
+        return dT
+
+    def status(self):
+        bos_status(self.h)
+
+
+def loss_l2(I, target, stream=None):
+    """L_BOS = sum (target - I)^2 and dL/dI = -2 (target - I), both on the device."""
+    import torch
+
+    loss = torch.empty((1,), dtype=torch.float64, device=I.device)
+    g = torch.empty_like(I)
+    bos_loss_l2(I.data_ptr(), target.data_ptr(), I.numel(), loss.data_ptr(), g.data_ptr(), _stream(stream))
+    return loss, g

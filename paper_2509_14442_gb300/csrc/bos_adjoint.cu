@@ -1,0 +1,386 @@
+// Adjoint of the BOS forward model (step a6, Sec. 2.4): dL/dT for a given dL/dI.
+//
+//   adjoint_kernel  -- per ray, reverse Sharma's steps segment by segment from the
+//                      checkpoints the forward kept every K steps (each segment is
+//                      recomputed forward into shared memory, then reversed), starting
+//                      from the adjoint of the wall epilogue (luminance, cosine, path
+//                      length of Eq. 2).  At every stage evaluation the sensitivities of
+//                      the 8 trilinear corners are scattered into per-node accumulators
+//                      (d L/d deta, d L/d grad eta) with warp-aggregated atomics: lanes
+//                      whose stage point lies in the same cell are summed in shared
+//                      memory first, so each (corner, channel) gets one atomic per cell
+//                      per warp instead of one per ray.
+//   gradient_kernel -- per node: the transpose of the central-difference stencil applied
+//                      to the grad-eta sensitivities, plus the deta sensitivity, times
+//                      d deta/dT = -rho0 G T0 / T^2.  A gather, so it is deterministic.
+#include "bos_comp.cuh"
+#include "bos_device.cuh"
+#include "bos_internal.h"
+
+namespace bos {
+
+constexpr int kAdjWarps = 2;          // warps per block
+constexpr int kScatterStride = 36;    // floats per lane row of the scatter buffer (16-byte aligned rows)
+constexpr uint32_t kNoKey = 0xffffffffu;
+
+struct InterpGrad {
+    float4 v, d0, d1, d2;   // value and derivatives with respect to the three fractions
+};
+
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+
+// Same lerp order as the forward `trilinear`, so v matches it bit for bit.
+template <class E>
+__device__ __forceinline__ InterpGrad trilinear_grad(const E* s, uint32_t o, float f0, float f1, float f2) {
+    float4 c000 = load_cell(s, o), c100 = load_cell(s, o + 1);
+    float4 c010 = load_cell(s, o + 9), c110 = load_cell(s, o + 10);
+    float4 c001 = load_cell(s, o + 81), c101 = load_cell(s, o + 82);
+    float4 c011 = load_cell(s, o + 90), c111 = load_cell(s, o + 91);
+    float4 a0 = lerp4(c000, c100, f0), a1 = lerp4(c010, c110, f0);
+    float4 a2 = lerp4(c001, c101, f0), a3 = lerp4(c011, c111, f0);
+    float4 b0 = lerp4(a0, a1, f1), b1 = lerp4(a2, a3, f1);
+    InterpGrad r;
+    r.v = lerp4(b0, b1, f2);
+    r.d2 = sub4(b1, b0);
+    r.d1 = lerp4(sub4(a1, a0), sub4(a3, a2), f2);
+    r.d0 = lerp4(lerp4(sub4(c100, c000), sub4(c110, c010), f1), lerp4(sub4(c101, c001), sub4(c111, c011), f1), f2);
+    return r;
+}
+
+struct Stage {
+    int ci[3];
+    float cf[3];
+    float D[3];
+};
+
+// Adjoint of D = (1 + deta) grad at a stage point: given Db, the position adjoint (metres)
+// and the per-corner record Q (corner c receives w_c Q).
+template <class E>
+__device__ __forceinline__ void rhs_adjoint(const CompField<E>& F, const Stage& s, const float Db[3], float pb[3],
+                                            float4& Q) {
+    uint32_t o = brick_offset(s.ci[0], s.ci[1], s.ci[2]);
+    InterpGrad ig = trilinear_grad(F.store, o, s.cf[0], s.cf[1], s.cf[2]);
+    float eta = 1.0f + ig.v.x;
+    float Dg = Db[0] * ig.v.y + Db[1] * ig.v.z + Db[2] * ig.v.w;
+    const float4 dv[3] = {ig.d0, ig.d1, ig.d2};
+    for (int a = 0; a < 3; ++a)
+        pb[a] = F.inv_h[a] * (dv[a].x * Dg + eta * (Db[0] * dv[a].y + Db[1] * dv[a].z + Db[2] * dv[a].w));
+    Q = make_float4(Dg, eta * Db[0], eta * Db[1], eta * Db[2]);
+}
+
+// Warp-collective scatter of w_c(f) * Q into the 8 corner nodes of each lane's cell.
+// Every lane of the warp must call it (inactive lanes with act = false).
+__device__ __forceinline__ void scatter_warp(float* buf, bool act, const int ci[3], const float cf[3], float4 Q,
+                                             float* acc, int nx, int nxy) {
+    const int lane = threadIdx.x & 31;
+    unsigned pend = __ballot_sync(0xffffffffu, act);
+    if (!pend) return;
+    uint32_t key = act ? (uint32_t)ci[0] + (uint32_t)ci[1] * (uint32_t)nx + (uint32_t)ci[2] * (uint32_t)nxy : kNoKey;
+    float4* row = reinterpret_cast<float4*>(buf + lane * kScatterStride);
+    const float g0 = 1.0f - cf[0], g1 = 1.0f - cf[1], g2 = 1.0f - cf[2];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        float w = ((c & 1) ? cf[0] : g0) * ((c & 2) ? cf[1] : g1) * ((c & 4) ? cf[2] : g2);
+        if (!act) w = 0.0f;
+        row[c] = make_float4(w * Q.x, w * Q.y, w * Q.z, w * Q.w);
+    }
+    __syncwarp();
+    const int corner = lane >> 2;
+    const uint32_t off = (uint32_t)(corner & 1) + (uint32_t)((corner >> 1) & 1) * (uint32_t)nx +
+                         (uint32_t)(corner >> 2) * (uint32_t)nxy;
+    while (pend) {
+        const int leader = __ffs(pend) - 1;
+        const uint32_t lk = __shfl_sync(0xffffffffu, key, leader);
+        const unsigned grp = __ballot_sync(0xffffffffu, key == lk);
+        pend &= ~grp;
+        float sum = 0.0f;
+        for (unsigned m = grp; m; m &= m - 1) sum += buf[(__ffs(m) - 1) * kScatterStride + lane];
+        if (sum != 0.0f) atomicAdd(acc + ((size_t)(lk + off) << 2) + (lane & 3), sum);
+    }
+    __syncwarp();
+}
+
+// Adjoint of the wall epilogue for seed Ib = dL/dI of this ray: returns the adjoints of
+// (r_N, v_N) and of the path length (which the per-step lengths feed).
+__device__ __forceinline__ void wall_adjoint(const SceneDev& S, const double rN[3], const double vN[3],
+                                             double len_before, double Ib, double rb[3], double vb[3],
+                                             double& lenb) {
+    const WallDev& w = S.w;
+    rb[0] = rb[1] = rb[2] = vb[0] = vb[1] = vb[2] = 0.0;
+    lenb = 0.0;
+    double vn = vN[0] * w.normal[0] + vN[1] * w.normal[1] + vN[2] * w.normal[2];
+    if (!(vn > 0.0)) return;
+    double q[3] = {w.origin[0] - rN[0], w.origin[1] - rN[1], w.origin[2] - rN[2]};
+    double ts = (q[0] * w.normal[0] + q[1] * w.normal[1] + q[2] * w.normal[2]) / vn;
+    double xw[3], so[3];
+    for (int a = 0; a < 3; ++a) {
+        xw[a] = rN[a] + ts * vN[a];
+        so[a] = xw[a] - rN[a];
+    }
+    double vl = sqrt(vN[0] * vN[0] + vN[1] * vN[1] + vN[2] * vN[2]);
+    double lout = fabs(ts) * vl;
+    double len = len_before + lout;
+    double cw = vn / vl;
+    double gL[3];
+    double Lw = wall_luminance(S.L, w, xw, gL);
+    double Lb = Ib * cw / len, cb = Ib * Lw / len;
+    lenb = -Ib * Lw * cw / (len * len);
+    double xwb[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = lout > 0.0 ? so[a] / lout : 0.0;
+        xwb[a] = Lb * gL[a] + lenb * u;
+        rb[a] = -lenb * u;
+        vb[a] = cb * (w.normal[a] / vl - vn * vN[a] / (vl * vl * vl));
+    }
+    double tb = xwb[0] * vN[0] + xwb[1] * vN[1] + xwb[2] * vN[2];
+    for (int a = 0; a < 3; ++a) {
+        rb[a] += xwb[a] - tb * w.normal[a] / vn;
+        vb[a] += ts * xwb[a] - tb * ts * w.normal[a] / vn;
+    }
+}
+
+template <class E>
+__global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int K = ck.every;
+    float* st_buf = smem + (size_t)warp * (K * 6 * 32 + 32 * kScatterStride);   // [K][6][32]
+    float* sc_buf = st_buf + K * 6 * 32;
+    const CompField<E> F = {static_cast<const E*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
+                            {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
+    const int nx = S.g.n[0], nxy = S.g.n[0] * S.g.n[1];
+    const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
+    const TileShape ts = tile_shape(W, H, spp);
+    const int ntiles = ts.tiles_x * ts.tiles_y;
+    float* acc = reinterpret_cast<float*>(adj.acc);
+
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntiles) break;
+        const int tx = t % ts.tiles_x, ty = t / ts.tiles_x;
+        const int lp = lane / ts.G, sl = lane % ts.G;
+        const int px = tx * ts.TW + lp % ts.TW, py = ty * ts.TH + lp / ts.TW;
+        const bool valid = px < W && py < H;
+        for (int qs = 0; qs < ts.samples_per_lane; ++qs) {
+            const int s = ts.samples_per_lane == 1 ? sl : qs;
+            const long long slot = ((long long)t * 32 + lane) * ts.samples_per_lane + qs;
+            bool act = valid;
+            Ray R;
+            R.N = 0;
+            R.wall = false;
+            double Ib = 0.0;
+            if (act) {
+                R = ray_setup(S, px, py, s);
+                Ib = (double)adj.dLdI[(size_t)py * W + px] / spp;
+            }
+            act = act && R.wall && R.N > 0 && Ib != 0.0;
+            CompState st0;
+            CompConst k;
+            double eta_in = 1.0, rin[3] = {0, 0, 0};
+            if (act) comp_setup(S, F, R, st0, k, eta_in, rin);
+            const int N = act ? R.N : 0;
+            const int nseg = (N + K - 1) / K;
+            const int nseg_max = __reduce_max_sync(0xffffffffu, (unsigned)nseg);
+            float rb[3] = {0, 0, 0}, vb[3] = {0, 0, 0}, dtb = 0.0f, lenb = 0.0f;
+            double etab = 0.0;
+            const float dt = act ? k.dt : 0.0f;
+            for (int c = nseg_max - 1; c >= 0; --c) {
+                const int n0 = c * K;
+                const int n1 = min(n0 + K, N);
+                const bool seg = act && n0 < N;
+                // ---- recompute the segment from its checkpoint, keeping each step's state
+                CompState st;
+                BrickCache bc = {kNoKey, 0u};
+                if (seg) {
+                    float4 s0 = ck.state[((size_t)c * 3 + 0) * ck.nrays + slot];
+                    float4 s1 = ck.state[((size_t)c * 3 + 1) * ck.nrays + slot];
+                    float4 s2 = ck.state[((size_t)c * 3 + 2) * ck.nrays + slot];
+                    st.dr[0] = s0.x; st.dr[1] = s0.y; st.dr[2] = s0.z;
+                    st.dv[0] = s1.x; st.dv[1] = s1.y; st.dv[2] = s1.z;
+                    st.cv[0] = s2.x; st.cv[1] = s2.y; st.cv[2] = s2.z;
+                    st.cr[0] = s0.w; st.cr[1] = s1.w; st.cr[2] = s2.w;
+                    st.excess = 0.0f;
+                    for (int a = 0; a < 3; ++a) st.U[a] = st0.U[a] + (long long)n0 * k.dU[a];
+                    for (int n = n0; n < n1; ++n) {
+                        float* p = st_buf + (size_t)(n - n0) * 6 * 32 + lane;
+                        p[0] = st.dr[0]; p[32] = st.dr[1]; p[64] = st.dr[2];
+                        p[96] = st.dv[0]; p[128] = st.dv[1]; p[160] = st.dv[2];
+                        comp_step<E, 0>(F, st, k, bc);
+                    }
+                    if (c == nseg - 1) {
+                        // the lane's last segment: start from the adjoint of the wall epilogue
+                        double rN[3], vN[3], drb[3], dvb[3], lb;
+                        for (int a = 0; a < 3; ++a) {
+                            rN[a] = rin[a] + R.ell * R.d[a] + ((double)st.dr[a] - (double)st.cr[a]);
+                            vN[a] = eta_in * R.d[a] + ((double)st.dv[a] - (double)st.cv[a]);
+                        }
+                        double len_before = R.t_in + R.ell + (double)ck.excess[slot];
+                        wall_adjoint(S, rN, vN, len_before, Ib, drb, dvb, lb);
+                        for (int a = 0; a < 3; ++a) {
+                            rb[a] = (float)drb[a];
+                            vb[a] = (float)dvb[a];
+                        }
+                        lenb = (float)lb;
+                        etab += dvb[0] * R.d[0] + dvb[1] * R.d[1] + dvb[2] * R.d[2];
+                    }
+                }
+                __syncwarp();
+                // ---- reverse the segment's steps
+                const int n_hi = __reduce_max_sync(0xffffffffu, (unsigned)(seg ? n1 : 0));
+                for (int n = n_hi - 1; n >= n0; --n) {
+                    const bool a_ = seg && n < n1;
+                    Stage s1 = {}, s2 = {}, s3 = {};
+                    float A[3] = {0, 0, 0}, B[3] = {0, 0, 0}, dr[3] = {0, 0, 0}, dvv[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+                    if (a_) {
+                        const float* p = st_buf + (size_t)(n - n0) * 6 * 32 + lane;
+                        dr[0] = p[0]; dr[1] = p[32]; dr[2] = p[64];
+                        dvv[0] = p[96]; dvv[1] = p[128]; dvv[2] = p[160];
+                        long long U[3], U2[3], U3[3];
+                        for (int a = 0; a < 3; ++a) {
+                            U[a] = st0.U[a] + (long long)n * k.dU[a];
+                            U2[a] = U[a] + k.dUh[a];
+                            U3[a] = U[a] + k.dU[a];
+                        }
+                        float q[3];
+                        rhs_of(comp_eval(F, U, dr, bc, s1.ci, s1.cf), s1.D);
+                        for (int a = 0; a < 3; ++a) A[a] = dt * s1.D[a];
+                        for (int a = 0; a < 3; ++a) q[a] = dr[a] + (0.5f * dt) * dvv[a] + (0.125f * dt) * A[a];
+                        rhs_of(comp_eval(F, U2, q, bc, s2.ci, s2.cf), s2.D);
+                        for (int a = 0; a < 3; ++a) B[a] = dt * s2.D[a];
+                        for (int a = 0; a < 3; ++a) q[a] = dr[a] + dt * dvv[a] + (0.5f * dt) * B[a];
+                        rhs_of(comp_eval(F, U3, q, bc, s3.ci, s3.cf), s3.D);
+                        float inc[3], nn = 0.0f;
+                        for (int a = 0; a < 3; ++a) {
+                            inc[a] = k.dS[a] + dt * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
+                            nn += inc[a] * inc[a];
+                        }
+                        float rn = rsqrtf(nn);
+                        for (int a = 0; a < 3; ++a) {
+                            u[a] = inc[a] * rn;             // unit step direction: d|r_{n+1} - r_n|
+                            rb[a] += lenb * u[a];
+                        }
+                    }
+                    // r' = r + dt (v + (A + 2B)/6),  v' = v + (A + 4B + C)/6
+                    float Ab[3], Bb[3], Cb[3], rn_[3], vn_[3];
+                    for (int a = 0; a < 3; ++a) {
+                        Ab[a] = (dt * (1.0f / 6.0f)) * rb[a] + vb[a] * (1.0f / 6.0f);
+                        Bb[a] = (dt * (1.0f / 3.0f)) * rb[a] + vb[a] * (4.0f / 6.0f);
+                        Cb[a] = vb[a] * (1.0f / 6.0f);
+                        rn_[a] = rb[a];
+                        vn_[a] = vb[a] + dt * rb[a];
+                        dtb += rb[a] * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
+                    }
+                    float Db[3], pb[3] = {0, 0, 0};
+                    float4 Q = make_float4(0, 0, 0, 0);
+                    // C = dt D(p3),  p3 = S(n+1) + dr + dt dv + dt/2 B
+                    for (int a = 0; a < 3; ++a) {
+                        dtb += Cb[a] * s3.D[a];
+                        Db[a] = dt * Cb[a];
+                    }
+                    if (a_) rhs_adjoint(F, s3, Db, pb, Q);
+                    scatter_warp(sc_buf, a_, s3.ci, s3.cf, Q, acc, nx, nxy);
+                    for (int a = 0; a < 3; ++a) {
+                        rn_[a] += pb[a];
+                        vn_[a] += dt * pb[a];
+                        Bb[a] += (0.5f * dt) * pb[a];
+                        dtb += pb[a] * (dvv[a] + 0.5f * B[a]);
+                    }
+                    // B = dt D(p2),  p2 = S(n+1/2) + dr + dt/2 dv + dt/8 A
+                    for (int a = 0; a < 3; ++a) {
+                        dtb += Bb[a] * s2.D[a];
+                        Db[a] = dt * Bb[a];
+                    }
+                    if (a_) rhs_adjoint(F, s2, Db, pb, Q);
+                    scatter_warp(sc_buf, a_, s2.ci, s2.cf, Q, acc, nx, nxy);
+                    for (int a = 0; a < 3; ++a) {
+                        rn_[a] += pb[a];
+                        vn_[a] += (0.5f * dt) * pb[a];
+                        Ab[a] += (0.125f * dt) * pb[a];
+                        dtb += pb[a] * (0.5f * dvv[a] + 0.125f * A[a]);
+                    }
+                    // A = dt D(p1),  p1 = S(n) + dr
+                    for (int a = 0; a < 3; ++a) {
+                        dtb += Ab[a] * s1.D[a];
+                        Db[a] = dt * Ab[a];
+                    }
+                    if (a_) rhs_adjoint(F, s1, Db, pb, Q);
+                    scatter_warp(sc_buf, a_, s1.ci, s1.cf, Q, acc, nx, nxy);
+                    if (a_) {
+                        for (int a = 0; a < 3; ++a) {
+                            rb[a] = rn_[a] + pb[a] - lenb * u[a];
+                            vb[a] = vn_[a];
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            // ---- entry: v0 = eta_in d and dt = ell / (N eta_in), eta_in = 1 + deta(r_in)
+            int ci[3] = {0, 0, 0};
+            float cf[3] = {0, 0, 0};
+            if (act) {
+                etab -= (double)dtb * (double)dt / eta_in;
+                BrickCache bc = {kNoKey, 0u};
+                float zero[3] = {0, 0, 0};
+                comp_eval(F, st0.U, zero, bc, ci, cf);
+            }
+            scatter_warp(sc_buf, act, ci, cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), acc, nx, nxy);
+        }
+    }
+}
+
+// dL/dT per node: transpose of the difference stencil of grad eta, plus d L/d deta, times
+// d deta/dT = -K / T^2.
+__global__ void gradient_kernel(GridDev g, const float4* __restrict__ acc, const float* __restrict__ T,
+                                float* __restrict__ dLdT) {
+    const long long n = (long long)g.n[0] * g.n[1] * g.n[2];
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int idx[3] = {(int)(c % g.n[0]), (int)((c / g.n[0]) % g.n[1]), (int)(c / ((long long)g.n[0] * g.n[1]))};
+        const long long stride[3] = {1, g.n[0], (long long)g.n[0] * g.n[1]};
+        double tot = (double)acc[c].x;
+        for (int a = 0; a < 3; ++a) {
+            const int i = idx[a], na = g.n[a];
+            const double h = g.h[a], h2 = 2.0 * g.h[a];
+            auto gch = [&](long long m) {
+                float4 v = acc[m];
+                return (double)(a == 0 ? v.y : a == 1 ? v.z : v.w);
+            };
+            if (i - 1 >= 0) tot += gch(c - stride[a]) / (i - 1 == 0 ? h : h2);        // node i-1 reads i as hi
+            if (i + 1 <= na - 1) tot -= gch(c + stride[a]) / (i + 1 == na - 1 ? h : h2);  // node i+1 reads i as lo
+            if (i == 0) tot -= gch(c) / h;                                            // one-sided at the faces
+            if (i == na - 1) tot += gch(c) / h;
+        }
+        const double Tc = (double)T[c];
+        dLdT[c] = (float)(tot * (-g.K / (Tc * Tc)));
+    }
+}
+
+template <class E>
+static cudaError_t launch_adjoint_t(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
+                                    int num_sms, cudaStream_t st) {
+    size_t smem = (size_t)kAdjWarps * (ck.every * 6 * 32 + 32 * kScatterStride) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel<E>, kAdjWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    adjoint_kernel<E><<<num_sms * per_sm, kAdjWarps * 32, smem, st>>>(S, ck, adj, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(int mode, const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
+                            const float* T, float* dLdT, int num_sms, cudaStream_t st) {
+    if (ck.every > 64) return cudaErrorNotSupported;
+    cudaError_t e;
+    if (mode == 1) e = launch_adjoint_t<float4>(S, ck, adj, w, num_sms, st);
+    else if (mode == 2) e = launch_adjoint_t<uint2>(S, ck, adj, w, num_sms, st);
+    else return cudaErrorNotSupported;
+    if (e != cudaSuccess) return e;
+    gradient_kernel<<<num_sms * 8, 256, 0, st>>>(S.g, adj.acc, T, dLdT);
+    return cudaGetLastError();
+}
+
+}  // namespace bos

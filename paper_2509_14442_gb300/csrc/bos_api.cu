@@ -1,0 +1,451 @@
+// C ABI of the BOS library: argument validation, context-owned device memory and
+// kernel launches.  Declarations and contracts: include/bos.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/bos.h"
+#include "bos_internal.h"
+
+using namespace bos;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bos_status_t fail(bos_status_t s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+bos_status_t fail(bos_status_t s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+bos_status_t cuda_fail(cudaError_t e, const char* what) {
+    return fail(BOS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool finite3(const double* v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+double norm3(const double* v) { return sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+bool unit3(const double* v) { return finite3(v) && fabs(norm3(v) - 1.0) < 1e-9; }
+
+bos_status_t check_camera(const bos_camera_desc* c, const char* who) {
+    if (!c) return fail(BOS_ERR_INVALID_ARG, "%s: NULL camera", who);
+    if (!finite3(c->pos) || !unit3(c->fwd) || !unit3(c->up))
+        return fail(BOS_ERR_INVALID_ARG, "%s: pos must be finite, fwd and up unit vectors", who);
+    double dot = c->fwd[0] * c->up[0] + c->fwd[1] * c->up[1] + c->fwd[2] * c->up[2];
+    if (fabs(dot) > 1e-9) return fail(BOS_ERR_INVALID_ARG, "%s: fwd and up must be orthogonal", who);
+    if (!(c->fx > 0) || !(c->fy > 0) || !isfinite(c->fx) || !isfinite(c->fy) || !isfinite(c->cx) ||
+        !isfinite(c->cy))
+        return fail(BOS_ERR_INVALID_ARG, "%s: focal lengths must be > 0 and finite", who);
+    if (c->width <= 0 || c->height <= 0 || c->spp <= 0)
+        return fail(BOS_ERR_INVALID_ARG, "%s: width, height and spp must be > 0", who);
+    if ((long long)c->width * c->height * c->spp > (1LL << 40))
+        return fail(BOS_ERR_INVALID_ARG, "%s: too many rays", who);
+    return BOS_OK;
+}
+
+template <class T>
+void copy3(T* dst, const double* src) {
+    for (int a = 0; a < 3; ++a) dst[a] = src[a];
+}
+
+CamDev to_dev(const bos_camera_desc& c) {
+    CamDev d;
+    copy3(d.pos, c.pos);
+    copy3(d.fwd, c.fwd);
+    copy3(d.up, c.up);
+    d.fx = c.fx;
+    d.fy = c.fy;
+    d.cx = c.cx;
+    d.cy = c.cy;
+    d.width = c.width;
+    d.height = c.height;
+    d.spp = c.spp;
+    d.seed = c.seed;
+    return d;
+}
+
+size_t elem_bytes(int prec) { return prec == BOS_PREC_FP64 ? 32 : prec == BOS_PREC_BF16_COMP ? 8 : 16; }
+
+// Tracer variant of a precision (see the MODE switch of the render kernel).
+int mode_of(int prec) {
+    switch (prec) {
+        case BOS_PREC_FP32_COMP: return 1;
+        case BOS_PREC_BF16_COMP: return 2;
+        case BOS_PREC_FP32: return 3;
+        default: return 4;
+    }
+}
+
+}  // namespace
+
+struct bos_ctx {
+    int device = 0;
+    int num_sms = 1;
+    uint64_t mem_limit = 0;
+    uint64_t bytes = 0;
+
+    bool has_grid = false, has_geom = false;
+    bos_grid_desc grid{};
+    GridDev g{};
+    void* store = nullptr;
+    size_t store_bytes = 0;
+    const float* T = nullptr;
+
+    CamDev cam{};
+    WallDev wall{};
+    LightDev light{};
+    IntegDev integ{};
+
+    void* small = nullptr;          // tile counter, step counter, error word
+    int* tile_counter = nullptr;
+    unsigned long long* steps = nullptr;
+    int* err = nullptr;
+
+    float4* ckpt = nullptr;
+    size_t ckpt_bytes = 0;
+    float* excess = nullptr;
+    size_t excess_bytes = 0;
+    bool saved = false;
+    CkptDev saved_ck{};
+    int saved_mode = 0;
+
+    float4* acc = nullptr;
+    size_t acc_bytes = 0;
+};
+
+namespace {
+
+bos_status_t dev_alloc(bos_ctx* c, void** p, size_t* have, size_t want, const char* what) {
+    if (*have >= want && *p) return BOS_OK;
+    if (c->mem_limit && c->bytes - *have + want > c->mem_limit)
+        return fail(BOS_ERR_OOM, "%s: %zu bytes would exceed the context limit of %llu bytes", what, want,
+                    (unsigned long long)c->mem_limit);
+    if (*p) {
+        cudaError_t e = cudaFree(*p);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+        c->bytes -= *have;
+        *p = nullptr;
+        *have = 0;
+    }
+    cudaError_t e = cudaMalloc(p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(BOS_ERR_OOM, "%s: cudaMalloc(%zu) failed: %s", what, want, cudaGetErrorString(e));
+    }
+    *have = want;
+    c->bytes += want;
+    return BOS_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+SceneDev scene_of(const bos_ctx* c) {
+    SceneDev S;
+    S.g = c->g;
+    S.cam = c->cam;
+    S.w = c->wall;
+    S.L = c->light;
+    S.it = c->integ;
+    return S;
+}
+
+// Upper bound of N over all rays: fixed, or the box diagonal over the step length.
+int step_bound(const bos_ctx* c) {
+    if (c->integ.fixed_steps > 0) return c->integ.fixed_steps;
+    double hmin = fmin(c->g.h[0], fmin(c->g.h[1], c->g.h[2]));
+    double diag = norm3(c->g.extent);
+    double b = ceil(diag / (c->integ.max_step_vox * hmin)) + 2.0;
+    return b > 2e9 ? 2000000000 : (int)b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bos_error_string(bos_status_t s) {
+    switch (s) {
+        case BOS_OK: return "ok";
+        case BOS_ERR_INVALID_ARG: return "invalid argument";
+        case BOS_ERR_NOT_READY: return "not ready";
+        case BOS_ERR_OOM: return "out of device memory";
+        case BOS_ERR_ADMISSION: return "request exceeds the admission limit";
+        case BOS_ERR_CUDA: return "CUDA error";
+        case BOS_ERR_TIMEOUT: return "timed out";
+        case BOS_ERR_DEVICE_CHECK: return "device-side check failed";
+        case BOS_ERR_UNIMPLEMENTED: return "unimplemented";
+    }
+    return "unknown status";
+}
+
+const char* bos_last_error(void) { return g_last_error.c_str(); }
+
+bos_status_t bos_create(bos_ctx** out, int device, uint64_t mem_limit_bytes) {
+    if (!out) return fail(BOS_ERR_INVALID_ARG, "bos_create: NULL out");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "bos_create: cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(BOS_ERR_INVALID_ARG, "bos_create: no CUDA device %d", device);
+    DeviceGuard dg(device);
+    bos_ctx* c = new bos_ctx();
+    c->device = device;
+    c->mem_limit = mem_limit_bytes;
+    e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "bos_create: SM count");
+    }
+    size_t have = 0;
+    bos_status_t s = dev_alloc(c, &c->small, &have, 256, "bos_create");
+    if (s != BOS_OK) {
+        delete c;
+        return s;
+    }
+    e = cudaMemset(c->small, 0, 256);
+    if (e != cudaSuccess) {
+        cudaFree(c->small);
+        delete c;
+        return cuda_fail(e, "bos_create: memset");
+    }
+    c->tile_counter = (int*)c->small;
+    c->err = (int*)c->small + 1;
+    c->steps = (unsigned long long*)((char*)c->small + 64);
+    *out = c;
+    return BOS_OK;
+}
+
+bos_status_t bos_destroy(bos_ctx* c) {
+    if (!c) return BOS_OK;
+    DeviceGuard dg(c->device);
+    void* bufs[] = {c->store, c->small, c->ckpt, c->excess, c->acc};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    delete c;
+    return BOS_OK;
+}
+
+uint64_t bos_device_bytes(bos_ctx* c) { return c ? c->bytes : 0; }
+
+bos_status_t bos_set_grid(bos_ctx* c, const bos_grid_desc* d, const float* T_dev, void* stream) {
+    if (!c || !d || !T_dev) return fail(BOS_ERR_INVALID_ARG, "bos_set_grid: NULL argument");
+    if (d->nx < 2 || d->ny < 2 || d->nz < 2 || d->nx > 8192 || d->ny > 8192 || d->nz > 8192)
+        return fail(BOS_ERR_INVALID_ARG, "bos_set_grid: need 2 <= n <= 8192 cells per axis, got %d x %d x %d", d->nx,
+                    d->ny, d->nz);
+    if ((long long)d->nx * d->ny * d->nz >= (1LL << 31))
+        return fail(BOS_ERR_INVALID_ARG, "bos_set_grid: at most 2^31 - 1 cells");
+    if (!finite3(d->origin) || !finite3(d->extent) || !(d->extent[0] > 0) || !(d->extent[1] > 0) ||
+        !(d->extent[2] > 0))
+        return fail(BOS_ERR_INVALID_ARG, "bos_set_grid: origin must be finite and extent > 0");
+    if (!(d->T0 > 0) || !(d->rho0 > 0) || !(d->G > 0) || !isfinite(d->T0 * d->rho0 * d->G))
+        return fail(BOS_ERR_INVALID_ARG, "bos_set_grid: T0, rho0 and G must be > 0");
+    if (d->prec < BOS_PREC_FP64 || d->prec > BOS_PREC_BF16_COMP)
+        return fail(BOS_ERR_INVALID_ARG, "bos_set_grid: unknown precision %d", d->prec);
+    DeviceGuard dg(c->device);
+    GridDev g{};
+    int n[3] = {d->nx, d->ny, d->nz};
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = n[a];
+        g.nb[a] = (n[a] - 1 + kBrick - 1) / kBrick;
+        g.origin[a] = d->origin[a];
+        g.extent[a] = d->extent[a];
+        g.h[a] = d->extent[a] / (double)n[a];
+        g.inv_hf[a] = (float)(1.0 / g.h[a]);
+        g.hf[a] = (float)g.h[a];
+    }
+    g.K = d->rho0 * d->G * d->T0;
+    g.prec = d->prec;
+    size_t slots = (size_t)morton3(g.nb[0] - 1, g.nb[1] - 1, g.nb[2] - 1) + 1;
+    size_t want = slots * kBrickCells * elem_bytes(d->prec);
+    bos_status_t s = dev_alloc(c, &c->store, &c->store_bytes, want, "bos_set_grid: brick store");
+    if (s != BOS_OK) return s;
+    g.store = c->store;
+    cudaError_t e = launch_build_store(g, T_dev, c->store, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bos_set_grid: launch");
+    c->grid = *d;
+    c->g = g;
+    c->T = T_dev;
+    c->has_grid = true;
+    c->saved = false;
+    return BOS_OK;
+}
+
+bos_status_t bos_set_geometry(bos_ctx* c, const bos_camera_desc* cam, const bos_wall_desc* wall,
+                              const bos_light_desc* light, const float* pattern_dev, const bos_integrator_desc* it) {
+    if (!c || !wall || !light || !it) return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: NULL argument");
+    bos_status_t s = check_camera(cam, "bos_set_geometry: camera");
+    if (s != BOS_OK) return s;
+    if (!finite3(wall->origin) || !unit3(wall->eu) || !unit3(wall->ev) || !unit3(wall->normal) ||
+        !(wall->size_u > 0) || !(wall->size_v > 0))
+        return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: wall needs a finite origin, unit axes and sizes > 0");
+    if (light->mode != 0 && light->mode != 1) return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: light mode");
+    if (light->tw <= 0 || light->th <= 0 || !pattern_dev)
+        return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: pattern size must be > 0 and pattern non-NULL");
+    if (light->mode == 1) {
+        s = check_camera(&light->proj, "bos_set_geometry: projector");
+        if (s != BOS_OK) return s;
+    }
+    if (it->fixed_steps < 0 || it->fixed_steps > (1 << 24))
+        return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: fixed_steps out of range");
+    if (it->fixed_steps == 0 && !(it->max_step_vox > 1e-3 && it->max_step_vox < 1e6))
+        return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: max_step_vox out of range");
+    if (it->integrator != 0 && it->integrator != 1) return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: integrator");
+    if (it->ckpt_every < 1 || it->ckpt_every > 4096)
+        return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: ckpt_every must be in [1, 4096]");
+    c->cam = to_dev(*cam);
+    copy3(c->wall.origin, wall->origin);
+    copy3(c->wall.eu, wall->eu);
+    copy3(c->wall.ev, wall->ev);
+    copy3(c->wall.normal, wall->normal);
+    c->wall.size_u = wall->size_u;
+    c->wall.size_v = wall->size_v;
+    c->light.mode = light->mode;
+    c->light.proj = to_dev(light->proj);
+    c->light.tw = light->tw;
+    c->light.th = light->th;
+    c->light.pattern = pattern_dev;
+    c->integ.fixed_steps = it->fixed_steps;
+    c->integ.max_step_vox = it->max_step_vox;
+    c->integ.integrator = it->integrator;
+    c->integ.ckpt_every = it->ckpt_every;
+    c->has_geom = true;
+    c->saved = false;
+    return BOS_OK;
+}
+
+static bos_status_t render_impl(bos_ctx* c, int mode, float* I, float* disp, double* hit, int save, void* stream) {
+    if (!c || !I) return fail(BOS_ERR_INVALID_ARG, "bos_render: NULL context or I");
+    if (!c->has_grid || !c->has_geom) return fail(BOS_ERR_NOT_READY, "bos_render: set_grid and set_geometry first");
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->integ.max_steps = step_bound(c);
+    SceneDev S = scene_of(c);
+    CkptDev ck{};
+    ck.every = c->integ.ckpt_every;
+    {
+        TileShape ts = tile_shape(c->cam.width, c->cam.height, c->cam.spp);
+        ck.nrays = (long long)ts.tiles_x * ts.tiles_y * 32 * ts.samples_per_lane;
+    }
+    if (save) {
+        if (mode != 1 && mode != 2)
+            return fail(BOS_ERR_UNIMPLEMENTED, "bos_render: save_for_backward needs FP32_COMP or BF16_COMP");
+        if (c->integ.integrator != 0)
+            return fail(BOS_ERR_UNIMPLEMENTED, "bos_render: the adjoint supports the Sharma RKN integrator only");
+        ck.max_ckpt = (c->integ.max_steps + ck.every - 1) / ck.every;
+        size_t want = (size_t)ck.max_ckpt * 3 * (size_t)ck.nrays * sizeof(float4);
+        bos_status_t s = dev_alloc(c, (void**)&c->ckpt, &c->ckpt_bytes, want, "bos_render: checkpoints");
+        if (s != BOS_OK) return s;
+        s = dev_alloc(c, (void**)&c->excess, &c->excess_bytes, (size_t)ck.nrays * sizeof(float), "bos_render: excess");
+        if (s != BOS_OK) return s;
+        ck.state = c->ckpt;
+        ck.excess = c->excess;
+    }
+    cudaError_t e = cudaMemsetAsync(c->small, 0, 4, st);               // tile counter
+    if (e == cudaSuccess && mode != 0) e = cudaMemsetAsync(c->steps, 0, 8, st);   // the reference traces nothing
+    if (e != cudaSuccess) return cuda_fail(e, "bos_render: memset");
+    WorkDev w{c->tile_counter, c->steps, c->err};
+    RenderOut o{I, disp, hit};
+    e = launch_render(mode, S, o, w, ck, c->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(e, "bos_render: launch");
+    c->saved = save != 0;
+    c->saved_ck = ck;
+    c->saved_mode = mode;
+    return BOS_OK;
+}
+
+bos_status_t bos_render(bos_ctx* c, float* I, float* disp, double* hit, int save_for_backward, void* stream) {
+    if (!c) return fail(BOS_ERR_INVALID_ARG, "bos_render: NULL context");
+    return render_impl(c, mode_of(c->grid.prec), I, disp, hit, save_for_backward, stream);
+}
+
+bos_status_t bos_render_reference(bos_ctx* c, float* I, float* disp, double* hit, void* stream) {
+    return render_impl(c, 0, I, disp, hit, 0, stream);
+}
+
+bos_status_t bos_ray_steps(bos_ctx* c, int32_t* nsteps, void* stream) {
+    if (!c || !nsteps) return fail(BOS_ERR_INVALID_ARG, "bos_ray_steps: NULL argument");
+    if (!c->has_grid || !c->has_geom) return fail(BOS_ERR_NOT_READY, "bos_ray_steps: set_grid and set_geometry first");
+    DeviceGuard dg(c->device);
+    c->integ.max_steps = step_bound(c);
+    cudaError_t e = launch_ray_steps(scene_of(c), nsteps, c->num_sms, (cudaStream_t)stream);
+    return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_ray_steps");
+}
+
+bos_status_t bos_last_ray_steps(bos_ctx* c, uint64_t* out) {
+    if (!c || !out) return fail(BOS_ERR_INVALID_ARG, "bos_last_ray_steps: NULL argument");
+    DeviceGuard dg(c->device);
+    unsigned long long v = 0;
+    cudaError_t e = cudaMemcpy(&v, c->steps, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "bos_last_ray_steps");
+    *out = v;
+    return BOS_OK;
+}
+
+bos_status_t bos_loss_l2(const float* I, const float* target, int64_t n, double* loss, float* dLdI, void* stream) {
+    if (!I || !target || !loss || n < 0) return fail(BOS_ERR_INVALID_ARG, "bos_loss_l2: bad argument");
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = launch_loss_l2(I, target, n, loss, dLdI, sms, (cudaStream_t)stream);
+    return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_loss_l2");
+}
+
+bos_status_t bos_backward(bos_ctx* c, const float* dLdI, float* dLdT, void* stream) {
+    if (!c || !dLdI || !dLdT) return fail(BOS_ERR_INVALID_ARG, "bos_backward: NULL argument");
+    if (!c->saved) return fail(BOS_ERR_NOT_READY, "bos_backward: needs a bos_render with save_for_backward=1");
+    DeviceGuard dg(c->device);
+    size_t cells = (size_t)c->g.n[0] * c->g.n[1] * c->g.n[2];
+    bos_status_t s = dev_alloc(c, (void**)&c->acc, &c->acc_bytes, cells * sizeof(float4), "bos_backward: accumulators");
+    if (s != BOS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(c->acc, 0, cells * sizeof(float4), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->small, 0, 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "bos_backward: memset");
+    AdjDev adj{c->acc, dLdI, c->err};
+    WorkDev w{c->tile_counter, c->steps, c->err};
+    e = launch_backward(c->saved_mode, scene_of(c), c->saved_ck, adj, w, c->T, dLdT, c->num_sms, st);
+    if (e == cudaErrorNotSupported) return fail(BOS_ERR_UNIMPLEMENTED, "bos_backward: not available for this mode");
+    return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_backward: launch");
+}
+
+bos_status_t bos_export_nodes(bos_ctx* c, void* out, void* stream) {
+    if (!c || !out) return fail(BOS_ERR_INVALID_ARG, "bos_export_nodes: NULL argument");
+    if (!c->has_grid) return fail(BOS_ERR_NOT_READY, "bos_export_nodes: set_grid first");
+    DeviceGuard dg(c->device);
+    cudaError_t e = launch_export_nodes(c->g, out, c->num_sms, (cudaStream_t)stream);
+    return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_export_nodes");
+}
+
+bos_status_t bos_status(bos_ctx* c) {
+    if (!c) return fail(BOS_ERR_INVALID_ARG, "bos_status: NULL context");
+    DeviceGuard dg(c->device);
+    int err = 0;
+    cudaError_t e = cudaMemcpy(&err, c->err, sizeof err, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "bos_status");
+    switch (err) {
+        case DEV_OK: return BOS_OK;
+        case DEV_STEP_BUDGET: return fail(BOS_ERR_DEVICE_CHECK, "a ray needed more steps than the step bound");
+        case DEV_CKPT_OVERFLOW: return fail(BOS_ERR_DEVICE_CHECK, "a ray needed more checkpoints than allocated");
+        default: return fail(BOS_ERR_DEVICE_CHECK, "device error %d", err);
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,415 @@
+// Forward kernels of the BOS library for sm_103a:
+//   build_store   -- step a1: T -> (eta - 1, grad eta) bricks                 (Sec. 2.1)
+//   render        -- steps a2-a5: rays, Sharma RKN tracing, wall, radiance    (Eq. 1, Eq. 2)
+//   ray_steps     -- the integer step count of every ray (step a2)
+//   export_nodes  -- read the store back through the brick addressing
+//   loss_l2       -- L_BOS and its seed dL/dI                                 (Sec. 2.4)
+#include "bos_comp.cuh"
+#include "bos_device.cuh"
+#include "bos_internal.h"
+
+namespace bos {
+
+// ===================================================================== a1: field store
+
+template <class E>
+__device__ __forceinline__ void store_cell(E* dst, double de, double gx, double gy, double gz);
+
+template <>
+__device__ __forceinline__ void store_cell<float4>(float4* dst, double de, double gx, double gy, double gz) {
+    *dst = make_float4(__double2float_rn(de), __double2float_rn(gx), __double2float_rn(gy), __double2float_rn(gz));
+}
+
+template <>
+__device__ __forceinline__ void store_cell<uint2>(uint2* dst, double de, double gx, double gy, double gz) {
+    uint32_t a = __bfloat16_as_ushort(__double2bfloat16(de)), b = __bfloat16_as_ushort(__double2bfloat16(gx));
+    uint32_t c = __bfloat16_as_ushort(__double2bfloat16(gy)), d = __bfloat16_as_ushort(__double2bfloat16(gz));
+    *dst = make_uint2(a | (b << 16), c | (d << 16));
+}
+
+template <>
+__device__ __forceinline__ void store_cell<D4>(D4* dst, double de, double gx, double gy, double gz) {
+    double2* p = reinterpret_cast<double2*>(dst);
+    p[0] = make_double2(de, gx);
+    p[1] = make_double2(gy, gz);
+}
+
+__device__ __forceinline__ double deta_at(const GridDev& g, const float* T, int i, int j, int k) {
+    double t = (double)__ldg(T + ((size_t)k * g.n[1] + j) * g.n[0] + i);
+    return ddiv(g.K, t);
+}
+
+// One thread per stored cell: bricks of 9^3 cells (8 + apron) over base cells 0..n-2.
+template <class E>
+__global__ void build_store_kernel(GridDev g, const float* __restrict__ T, E* __restrict__ store, long long total) {
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= total) return;
+    int local = (int)(tid % kBrickCells);
+    long long b = tid / kBrickCells;
+    int bx = (int)(b % g.nb[0]);
+    int by = (int)((b / g.nb[0]) % g.nb[1]);
+    int bz = (int)(b / ((long long)g.nb[0] * g.nb[1]));
+    int lx = local % kBrickSide, ly = (local / kBrickSide) % kBrickSide, lz = local / (kBrickSide * kBrickSide);
+    int c[3] = {min(bx * kBrick + lx, g.n[0] - 1), min(by * kBrick + ly, g.n[1] - 1), min(bz * kBrick + lz, g.n[2] - 1)};
+    double de = deta_at(g, T, c[0], c[1], c[2]);
+    double gr[3];
+    for (int a = 0; a < 3; ++a) {
+        int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
+        double den = dmul(2.0, g.h[a]);
+        lo[a] = c[a] - 1;
+        hi[a] = c[a] + 1;
+        if (lo[a] < 0) {
+            lo[a] = c[a];
+            den = g.h[a];
+        }
+        if (hi[a] > g.n[a] - 1) {
+            hi[a] = c[a];
+            den = g.h[a];
+        }
+        double d = dsub(deta_at(g, T, hi[0], hi[1], hi[2]), deta_at(g, T, lo[0], lo[1], lo[2]));
+        gr[a] = ddiv(d, den);
+    }
+    uint32_t slot = morton3((uint32_t)bx, (uint32_t)by, (uint32_t)bz);
+    store_cell<E>(store + (size_t)slot * kBrickCells + local, de, gr[0], gr[1], gr[2]);
+}
+
+// ===================================================================== a3: integrators
+
+// ---- full-state integration in T = float (plain FP32) or double (FP64) ------------
+
+template <class T>
+struct FullField;
+
+template <>
+struct FullField<double> {
+    GridDev g;
+    __device__ __forceinline__ void rhs(const double x[3], double D[3]) const {
+        double eta, gr[3];
+        field_at(g, x, eta, gr);
+        for (int a = 0; a < 3; ++a) D[a] = eta * gr[a];
+    }
+    __device__ __forceinline__ double eta(const double x[3]) const {
+        double e, gr[3];
+        field_at(g, x, e, gr);
+        return e;
+    }
+};
+
+template <>
+struct FullField<float> {
+    GridDev g;
+    __device__ __forceinline__ float4 at(const float x[3]) const {
+        int i[3];
+        float f[3];
+        for (int a = 0; a < 3; ++a) {
+            float u = (x[a] - (float)g.origin[a]) * g.inv_hf[a] - 0.5f;
+            split_coord(u, g.n[a], i[a], f[a]);
+        }
+        return trilinear(static_cast<const float4*>(g.store), brick_offset(i[0], i[1], i[2]), f[0], f[1], f[2]);
+    }
+    __device__ __forceinline__ void rhs(const float x[3], float D[3]) const { rhs_of(at(x), D); }
+    __device__ __forceinline__ float eta(const float x[3]) const { return 1.0f + at(x).x; }
+};
+
+template <class T, int INTEG>
+__device__ __forceinline__ void full_step(const FullField<T>& F, T r[3], T v[3], T dt) {
+    if (INTEG == 0) {
+        T A[3], B[3], C[3], p[3], D[3];
+        F.rhs(r, D);
+        for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
+        for (int a = 0; a < 3; ++a) p[a] = r[a] + (dt * T(0.5)) * v[a] + (dt * T(0.125)) * A[a];
+        F.rhs(p, D);
+        for (int a = 0; a < 3; ++a) B[a] = dt * D[a];
+        for (int a = 0; a < 3; ++a) p[a] = r[a] + dt * v[a] + (dt * T(0.5)) * B[a];
+        F.rhs(p, D);
+        for (int a = 0; a < 3; ++a) C[a] = dt * D[a];
+        for (int a = 0; a < 3; ++a) {
+            r[a] = r[a] + dt * (v[a] + (A[a] + T(2) * B[a]) / T(6));
+            v[a] = v[a] + (A[a] + T(4) * B[a] + C[a]) / T(6);
+        }
+    } else {
+        T k1v[3], k2v[3], k3v[3], k4v[3], k2r[3], k3r[3], k4r[3], p[3];
+        F.rhs(r, k1v);
+        for (int a = 0; a < 3; ++a) {
+            k2r[a] = v[a] + (dt * T(0.5)) * k1v[a];
+            p[a] = r[a] + (dt * T(0.5)) * v[a];
+        }
+        F.rhs(p, k2v);
+        for (int a = 0; a < 3; ++a) {
+            k3r[a] = v[a] + (dt * T(0.5)) * k2v[a];
+            p[a] = r[a] + (dt * T(0.5)) * k2r[a];
+        }
+        F.rhs(p, k3v);
+        for (int a = 0; a < 3; ++a) {
+            k4r[a] = v[a] + dt * k3v[a];
+            p[a] = r[a] + dt * k3r[a];
+        }
+        F.rhs(p, k4v);
+        for (int a = 0; a < 3; ++a) {
+            r[a] = r[a] + dt / T(6) * (v[a] + T(2) * k2r[a] + T(2) * k3r[a] + k4r[a]);
+            v[a] = v[a] + dt / T(6) * (k1v[a] + T(2) * k2v[a] + T(2) * k3v[a] + k4v[a]);
+        }
+    }
+}
+
+// ===================================================================== a2-a5: render
+
+struct Sums {
+    double I, du, dv, hu, hv;
+};
+
+// Trace one ray of the comp path; optionally store checkpoints every K steps.
+template <class E, int INTEG>
+__device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const Ray& R, const CkptDev& ck,
+                                long long ray) {
+    CompState st;
+    CompConst k;
+    double eta_in, rin[3];
+    comp_setup(S, F, R, st, k, eta_in, rin);
+    BrickCache bc = {0xffffffffu, 0u};
+    const int K = ck.every;
+    for (int n = 0; n < R.N; ++n) {
+        if (ck.state != nullptr && n % K == 0) {
+            size_t c = (size_t)(n / K);
+            ck.state[(c * 3 + 0) * ck.nrays + ray] = make_float4(st.dr[0], st.dr[1], st.dr[2], st.cr[0]);
+            ck.state[(c * 3 + 1) * ck.nrays + ray] = make_float4(st.dv[0], st.dv[1], st.dv[2], st.cr[1]);
+            ck.state[(c * 3 + 2) * ck.nrays + ray] = make_float4(st.cv[0], st.cv[1], st.cv[2], st.cr[2]);
+        }
+        comp_step<E, INTEG>(F, st, k, bc);
+    }
+    if (ck.state != nullptr) ck.excess[ray] = st.excess;
+    double rN[3], vN[3];
+    for (int a = 0; a < 3; ++a) {
+        double dr = (double)st.dr[a] - (double)st.cr[a];
+        double dv = (double)st.dv[a] - (double)st.cv[a];
+        rN[a] = rin[a] + R.ell * R.d[a] + dr;
+        vN[a] = eta_in * R.d[a] + dv;
+    }
+    return wall_epilogue(S, S.cam.pos, R, rN, vN, R.t_in + R.ell + (double)st.excess);
+}
+
+template <class T, int INTEG>
+__device__ RayResult trace_full(const SceneDev& S, const FullField<T>& F, const Ray& R) {
+    T r[3], v[3];
+    double rin[3];
+    for (int a = 0; a < 3; ++a) {
+        rin[a] = S.cam.pos[a] + R.t_in * R.d[a];
+        r[a] = (T)rin[a];
+    }
+    T eta_in = F.eta(r);
+    for (int a = 0; a < 3; ++a) v[a] = eta_in * (T)R.d[a];
+    T dt = (T)R.ell / ((T)R.N * eta_in);
+    T lensum = 0;
+    for (int n = 0; n < R.N; ++n) {
+        T r0[3] = {r[0], r[1], r[2]};
+        full_step<T, INTEG>(F, r, v, dt);
+        T d0 = r[0] - r0[0], d1 = r[1] - r0[1], d2 = r[2] - r0[2];
+        lensum += sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    }
+    double rN[3] = {(double)r[0], (double)r[1], (double)r[2]};
+    double vN[3] = {(double)v[0], (double)v[1], (double)v[2]};
+    return wall_epilogue(S, S.cam.pos, R, rN, vN, R.t_in + (double)lensum);
+}
+
+template <int MODE>   // 0 straight, 1 comp fp32, 2 comp bf16, 3 full fp32, 4 full fp64
+struct Tracer;
+
+template <int MODE, int INTEG>
+__device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, const CkptDev& ck, long long ray) {
+    if (MODE == 1) {
+        CompField<float4> F = {static_cast<const float4*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
+                               {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
+        return trace_comp<float4, INTEG>(S, F, R, ck, ray);
+    } else if (MODE == 2) {
+        CompField<uint2> F = {static_cast<const uint2*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
+                              {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
+        return trace_comp<uint2, INTEG>(S, F, R, ck, ray);
+    } else if (MODE == 3) {
+        FullField<float> F = {S.g};
+        return trace_full<float, INTEG>(S, F, R);
+    } else {
+        FullField<double> F = {S.g};
+        return trace_full<double, INTEG>(S, F, R);
+    }
+}
+
+template <int MODE, int INTEG>
+__global__ void __launch_bounds__(128) render_kernel(SceneDev S, RenderOut out, WorkDev wk, CkptDev ck) {
+    const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
+    const TileShape ts = tile_shape(W, H, spp);
+    const int ntiles = ts.tiles_x * ts.tiles_y;
+    const int lane = threadIdx.x & 31;
+    unsigned long long my_steps = 0;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntiles) break;
+        const int tx = t % ts.tiles_x, ty = t / ts.tiles_x;
+        const int lp = lane / ts.G, sl = lane % ts.G;
+        const int px = tx * ts.TW + lp % ts.TW, py = ty * ts.TH + lp / ts.TW;
+        const bool valid = px < W && py < H;
+        Sums acc = {0, 0, 0, 0, 0};
+        if (valid) {
+            for (int q = 0; q < ts.samples_per_lane; ++q) {
+                const int s = ts.samples_per_lane == 1 ? sl : q;
+                const long long ray = ((long long)t * 32 + lane) * ts.samples_per_lane + q;   // checkpoint slot
+                Ray R = ray_setup(S, px, py, s);
+                if (!R.wall) continue;
+                if (R.N < 0) {
+                    flag_error(wk.err, DEV_STEP_BUDGET);
+                    continue;
+                }
+                RayResult r;
+                if (MODE == 0 || R.N == 0) {
+                    double zero3[3] = {S.cam.pos[0], S.cam.pos[1], S.cam.pos[2]};
+                    r = wall_epilogue(S, S.cam.pos, R, zero3, R.d, 0.0);
+                    if (R.N == 0 && ck.state != nullptr) ck.excess[ray] = 0.0f;
+                } else {
+                    r = trace_ray<MODE, INTEG>(S, R, ck, ray);
+                    my_steps += (unsigned long long)R.N;
+                }
+                acc.I += r.I;
+                acc.du += r.disp[0];
+                acc.dv += r.disp[1];
+                acc.hu += r.hit[0];
+                acc.hv += r.hit[1];
+            }
+        }
+        for (int m = 1; m < ts.G; m <<= 1) {
+            acc.I += __shfl_xor_sync(0xffffffffu, acc.I, m);
+            acc.du += __shfl_xor_sync(0xffffffffu, acc.du, m);
+            acc.dv += __shfl_xor_sync(0xffffffffu, acc.dv, m);
+            acc.hu += __shfl_xor_sync(0xffffffffu, acc.hu, m);
+            acc.hv += __shfl_xor_sync(0xffffffffu, acc.hv, m);
+        }
+        if (valid && sl == 0) {
+            const size_t p = (size_t)py * W + px;
+            const double inv = 1.0 / spp;
+            out.I[p] = (float)(acc.I * inv);
+            if (out.disp) {
+                out.disp[2 * p] = (float)(acc.du * inv);
+                out.disp[2 * p + 1] = (float)(acc.dv * inv);
+            }
+            if (out.hit) {
+                out.hit[2 * p] = acc.hu * inv;
+                out.hit[2 * p + 1] = acc.hv * inv;
+            }
+        }
+    }
+    for (int m = 16; m >= 1; m >>= 1) my_steps += __shfl_xor_sync(0xffffffffu, my_steps, m);
+    if (lane == 0 && my_steps) atomicAdd(wk.steps, my_steps);
+}
+
+// ===================================================================== small kernels
+
+__global__ void ray_steps_kernel(SceneDev S, int32_t* __restrict__ nsteps) {
+    const long long nrays = (long long)S.cam.width * S.cam.height * S.cam.spp;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrays;
+         r += (long long)gridDim.x * blockDim.x) {
+        long long pix = r / S.cam.spp;
+        int s = (int)(r % S.cam.spp);
+        Ray R = ray_setup(S, (int)(pix % S.cam.width), (int)(pix / S.cam.width), s);
+        nsteps[r] = R.wall ? R.N : 0;
+    }
+}
+
+template <class E>
+__global__ void export_nodes_kernel(GridDev g, E* __restrict__ out) {
+    const long long n = (long long)g.n[0] * g.n[1] * g.n[2];
+    const E* st = static_cast<const E*>(g.store);
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((long long)g.n[0] * g.n[1]));
+        // read node (i, j, k) as a corner of the cell whose base is clamped to n-2
+        int bi = min(i, g.n[0] - 2), bj = min(j, g.n[1] - 2), bk = min(k, g.n[2] - 2);
+        uint32_t o = brick_offset(bi, bj, bk) + (uint32_t)((k - bk) * 81 + (j - bj) * 9 + (i - bi));
+        out[c] = st[o];
+    }
+}
+
+__global__ void loss_l2_kernel(const float* __restrict__ I, const float* __restrict__ target, long long n,
+                               double* loss, float* __restrict__ dLdI) {
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float r = target[i] - I[i];
+        acc += (double)r * (double)r;
+        if (dLdI) dLdI[i] = -2.0f * r;
+    }
+    for (int m = 16; m >= 1; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+    __shared__ double part[32];
+    int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) part[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += part[i];
+        atomicAdd(loss, s);
+    }
+}
+
+// ===================================================================== launchers
+
+cudaError_t launch_build_store(const GridDev& g, const float* T, void* store, cudaStream_t st) {
+    long long total = (long long)g.nb[0] * g.nb[1] * g.nb[2] * kBrickCells;
+    int threads = 256;
+    long long blocks = (total + threads - 1) / threads;
+    switch (g.prec) {
+        case 0: build_store_kernel<D4><<<(unsigned)blocks, threads, 0, st>>>(g, T, (D4*)store, total); break;
+        case 3: build_store_kernel<uint2><<<(unsigned)blocks, threads, 0, st>>>(g, T, (uint2*)store, total); break;
+        default: build_store_kernel<float4><<<(unsigned)blocks, threads, 0, st>>>(g, T, (float4*)store, total); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int MODE, int INTEG>
+static cudaError_t launch_render_t(const SceneDev& S, const RenderOut& o, const WorkDev& w, const CkptDev& ck,
+                                   int num_sms, cudaStream_t st) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<MODE, INTEG>, 128, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    render_kernel<MODE, INTEG><<<num_sms * per_sm, 128, 0, st>>>(S, o, w, ck);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render(int mode, const SceneDev& S, const RenderOut& o, const WorkDev& w, const CkptDev& ck,
+                          int num_sms, cudaStream_t st) {
+    const int integ = S.it.integrator;
+#define BOS_CASE(M)                                                                        \
+    case M:                                                                                \
+        return integ == 1 ? launch_render_t<M, 1>(S, o, w, ck, num_sms, st)                \
+                          : launch_render_t<M, 0>(S, o, w, ck, num_sms, st);
+    switch (mode) {
+        BOS_CASE(0)
+        BOS_CASE(1)
+        BOS_CASE(2)
+        BOS_CASE(3)
+        BOS_CASE(4)
+        default: return cudaErrorInvalidValue;
+    }
+#undef BOS_CASE
+}
+
+cudaError_t launch_ray_steps(const SceneDev& S, int32_t* nsteps, int num_sms, cudaStream_t st) {
+    ray_steps_kernel<<<num_sms * 8, 256, 0, st>>>(S, nsteps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_nodes(const GridDev& g, void* out, int num_sms, cudaStream_t st) {
+    switch (g.prec) {
+        case 0: export_nodes_kernel<D4><<<num_sms * 8, 256, 0, st>>>(g, (D4*)out); break;
+        case 3: export_nodes_kernel<uint2><<<num_sms * 8, 256, 0, st>>>(g, (uint2*)out); break;
+        default: export_nodes_kernel<float4><<<num_sms * 8, 256, 0, st>>>(g, (float4*)out); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss_l2(const float* I, const float* target, long long n, double* loss, float* dLdI, int num_sms,
+                           cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    loss_l2_kernel<<<num_sms * 4, 256, 0, st>>>(I, target, n, loss, dLdI);
+    return cudaGetLastError();
+}
+
+}  // namespace bos

@@ -1,0 +1,51 @@
+// Host/device interface between the C-ABI layer and the kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bos_device.cuh"
+
+namespace bos {
+
+struct RenderOut {
+    float* I;
+    float* disp;
+    double* hit;
+};
+
+struct WorkDev {
+    int* tile_counter;              // warp tile queue (zeroed per launch)
+    unsigned long long* steps;      // sum of N over traced rays
+    int* err;                       // sticky device error word
+};
+
+// Ray state every K steps (float4 x3 per checkpoint: dr + cr.x, dv + cr.y, cv + cr.z),
+// index ((c * 3 + q) * nrays + slot), plus the path-length excess of every ray.  A ray's
+// slot is (tile * 32 + lane) * samples_per_lane + sample, so a warp's loads coalesce.
+struct CkptDev {
+    float4* state;                  // nullptr: do not save
+    float* excess;
+    long long nrays;                // number of slots (tiles * 32 * samples_per_lane)
+    int every;
+    int max_ckpt;
+};
+
+// Grid adjoint accumulators: per node (d L/d deta, d L/d grad eta) in float32.
+struct AdjDev {
+    float4* acc;
+    const float* dLdI;
+    int* err;
+};
+
+cudaError_t launch_build_store(const GridDev& g, const float* T, void* store, cudaStream_t st);
+cudaError_t launch_render(int mode, const SceneDev& S, const RenderOut& o, const WorkDev& w, const CkptDev& ck,
+                          int num_sms, cudaStream_t st);
+cudaError_t launch_ray_steps(const SceneDev& S, int32_t* nsteps, int num_sms, cudaStream_t st);
+cudaError_t launch_export_nodes(const GridDev& g, void* out, int num_sms, cudaStream_t st);
+cudaError_t launch_loss_l2(const float* I, const float* target, long long n, double* loss, float* dLdI, int num_sms,
+                           cudaStream_t st);
+cudaError_t launch_backward(int mode, const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
+                            const float* T, float* dLdT, int num_sms, cudaStream_t st);
+
+}  // namespace bos

@@ -1,0 +1,152 @@
+"""Parity of the CUDA adjoint (step a6) with the FP64 oracle's gradient and with oracle
+finite differences."""
+import numpy as np
+import pytest
+
+from paper_2509_14442_gb300 import scenes as S
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+# Gradient tolerance: relative L2 over the grid.  The CUDA path rounds the field store
+# to float32 (2^-24), integrates the ray deviation and its adjoint in float32 and sums
+# the per-node sensitivities with float32 atomics in arbitrary order; 1e-4 leaves a
+# margin of ~100 over those effects while a wrong term shows up at O(1).
+GRAD_REL_L2 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def bos():
+    from paper_2509_14442_gb300 import bos as B
+    B.lib()
+    return B
+
+
+def gpu_grad(bos, scene, w, prec=None):
+    prec = bos.BOS_PREC_FP32_COMP if prec is None else prec
+    ctx = bos.Context(0)
+    ctx.set_scene(scene, prec)
+    ctx.render(disp=False, save_for_backward=True)
+    dT = ctx.backward(torch.as_tensor(np.ascontiguousarray(w, dtype=np.float32), device="cuda"))
+    torch.cuda.synchronize()
+    ctx.status()
+    out = dT.cpu().numpy().astype(np.float64)
+    ctx.close()
+    return out
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def crop_scene():
+    big = S.room_adjoint()
+    k, j, i = np.unravel_index(np.argmax(big.T), big.T.shape)
+    lo = [int(np.clip(c - 16, 0, n - 32)) for c, n in zip((i, j, k), big.grid.n)]
+    return S.crop(big, lo, 32, 256, 256, 1)
+
+
+def test_loss_kernel_matches_torch(bos):
+    rng = np.random.default_rng(0)
+    I = torch.as_tensor(rng.random((37, 53)).astype(np.float32), device="cuda")
+    tgt = torch.as_tensor(rng.random((37, 53)).astype(np.float32), device="cuda")
+    loss, g = bos.loss_l2(I, tgt)
+    torch.cuda.synchronize()
+    ref = ((tgt.double() - I.double()) ** 2).sum()
+    assert abs(loss.item() - ref.item()) <= 1e-12 * ref.item()
+    assert torch.equal(g, -2.0 * (tgt - I))
+
+
+def test_adjoint_matches_oracle_on_32cube_crop(bos, orc):
+    sc = crop_scene()           # 32^3 crop of the 256x256x192 plume at the same spacing, 256^2 camera
+    w = np.random.default_rng(11).standard_normal((sc.camera.height, sc.camera.width))
+    g_orc = orc.grad(sc, w)
+    g_gpu = gpu_grad(bos, sc, w)
+    assert np.abs(g_orc).max() > 0
+    assert rel_l2(g_gpu, g_orc) <= GRAD_REL_L2
+
+
+@pytest.mark.parametrize("spp", [1, 2, 3])
+def test_adjoint_matches_oracle_small_room(bos, orc, spp):
+    sc = S.room((40, 40, 30), 61, 47, spp, 3100 + spp)
+    sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, ckpt_every=7))   # ragged segments
+    w = np.random.default_rng(spp).standard_normal((sc.camera.height, sc.camera.width))
+    assert rel_l2(gpu_grad(bos, sc, w), orc.grad(sc, w)) <= GRAD_REL_L2
+
+
+@pytest.mark.parametrize("K", [1, 16, 64])
+def test_adjoint_checkpoint_interval_does_not_change_the_gradient(bos, orc, K):
+    sc = S.room((32, 32, 24), 40, 36, 1, 3200)
+    sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, ckpt_every=K))
+    w = np.random.default_rng(5).standard_normal((36, 40))
+    assert rel_l2(gpu_grad(bos, sc, w), orc.grad(sc, w)) <= GRAD_REL_L2
+
+
+def test_autograd_function_loss_gradient(bos, orc):
+    from paper_2509_14442_gb300 import torch_ops
+
+    sc = S.room((48, 48, 36), 64, 56, 1, 3300)
+    target = orc.render(sc.replace(T=S.plume_field(sc.grid, 3301)))["I"]
+    ctx = bos.Context(0)
+    ctx.set_geometry(sc.camera, sc.wall, sc.light, sc.integ)
+    T = torch.as_tensor(sc.T, device="cuda").requires_grad_(True)
+    I = torch_ops.render(T, ctx, sc.grid)
+    loss = ((torch.as_tensor(target, device="cuda", dtype=torch.float32) - I) ** 2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    I_orc = orc.render(sc)["I"]
+    g_orc = orc.grad(sc, -2.0 * (target - I_orc))
+    assert rel_l2(T.grad.cpu().numpy().astype(np.float64), g_orc) <= GRAD_REL_L2
+    ctx.close()
+
+
+def _pixels_near(scene, center, margin):
+    """Pixels whose straight centre ray passes within `margin` (a box) of `center`."""
+    c = scene.camera
+    px, py = np.meshgrid(np.arange(c.width) + 0.5, np.arange(c.height) + 0.5, indexing="xy")
+    fwd, up = np.array(c.fwd), np.array(c.up)
+    right = np.cross(fwd, up)
+    d = ((px - c.cx) / c.fx)[..., None] * right - ((py - c.cy) / c.fy)[..., None] * up + fwd
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    lo, hi = np.asarray(center) - margin, np.asarray(center) + margin
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t0 = (lo - np.array(c.pos)) / d
+        t1 = (hi - np.array(c.pos)) / d
+    tmin = np.nanmax(np.minimum(t0, t1), axis=-1)
+    tmax = np.nanmin(np.maximum(t0, t1), axis=-1)
+    return np.flatnonzero((tmin <= tmax).reshape(-1))
+
+
+@pytest.mark.slow
+def test_adjoint_full_size_against_oracle_finite_differences(bos, orc):
+    # 256x256x192 plume, 2048^2 camera, 1 spp, checkpoints every 16 steps: the benchmarked
+    # launch.  L(T) = sum_j w_j I_j(T) with seeded w; dL/dT_v by central differences of the
+    # oracle (h = 0.01 K) at 64 seeded voxels in the plume, each over the pixels whose rays
+    # pass within 3 cells of the voxel (the only ones its value reaches).
+    sc = S.room_adjoint()
+    rng = np.random.default_rng(64)
+    w = rng.standard_normal((sc.camera.height, sc.camera.width))
+    g_gpu = gpu_grad(bos, sc, w)
+    hot = np.argwhere(sc.T > 300.0)
+    vox = hot[rng.choice(len(hot), 64, replace=False)]
+    hgrid = np.array(sc.grid.spacing())
+    eps = 1e-2
+    T64 = sc.T.astype(np.float64)
+    fd, gp = [], []
+    for k, j, i in vox:
+        center = np.array(sc.grid.origin) + (np.array([i, j, k]) + 0.5) * hgrid
+        pix = _pixels_near(sc, center, 3.0 * hgrid + 1e-3)
+        vals = []
+        for sgn in (1.0, -1.0):
+            T = T64.copy()
+            T[k, j, i] += sgn * eps
+            I = orc.render(sc.replace(T=T), pix=pix)["I"]
+            vals.append(float((w.reshape(-1)[pix] * I).sum()))
+        fd.append((vals[0] - vals[1]) / (2 * eps))
+        gp.append(g_gpu[k, j, i])
+    fd, gp = np.array(fd), np.array(gp)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    bad = np.abs(gp - fd) > 1e-3 * np.abs(fd) + 1e-3 * scale
+    assert bad.sum() == 0, (np.flatnonzero(bad), gp[bad], fd[bad])
