@@ -195,6 +195,12 @@ bos_status_t bos_backward(bos_ctx* ctx, const float* dLdI_dev, float* dLdT_dev, 
  * uint16 bit patterns, or float64), read through the brick addressing. */
 bos_status_t bos_export_nodes(bos_ctx* ctx, void* out_dev, void* stream);
 
+/* Measurement probe, no counterpart in the paper: read `bytes` (a multiple of 16, 16-byte
+ * aligned) of buf_dev `repeats` times with coalesced 16-byte loads that bypass L1, so that
+ * with a buffer smaller than L2 the caller can time the L2 read bandwidth that bounds
+ * the tracer's gathers.  sink_dev (1 float) is written only to keep the loads alive. */
+bos_status_t bos_probe_read(const void* buf_dev, uint64_t bytes, int repeats, float* sink_dev, void* stream);
+
 /* Sticky device-side status of the context (call after synchronising). */
 bos_status_t bos_status(bos_ctx* ctx);
 

@@ -286,11 +286,13 @@ void pinhole_dir(const orc_camera& cam, double x, double y, double d[3]) {
     double right[3] = {cam.fwd[1] * cam.up[2] - cam.fwd[2] * cam.up[1],
                        cam.fwd[2] * cam.up[0] - cam.fwd[0] * cam.up[2],
                        cam.fwd[0] * cam.up[1] - cam.fwd[1] * cam.up[0]};
-    double a = (x - cam.cx) / cam.fx;
-    double b = (y - cam.cy) / cam.fy;
+    double inv_fx = 1.0 / cam.fx, inv_fy = 1.0 / cam.fy;
+    double a = (x - cam.cx) * inv_fx;
+    double b = (y - cam.cy) * inv_fy;
     for (int i = 0; i < 3; ++i) d[i] = a * right[i] - b * cam.up[i] + cam.fwd[i];
     double n = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    for (int i = 0; i < 3; ++i) d[i] = d[i] / n;
+    double inv_n = 1.0 / n;
+    for (int i = 0; i < 3; ++i) d[i] = d[i] * inv_n;
 }
 
 struct RayGeom {
@@ -328,8 +330,9 @@ RayGeom ray_geometry(const orc_grid& g, const orc_wall& w, const orc_integ& it,
             if (rs[a] < lo || rs[a] > hi) inside = false;
             continue;
         }
-        double t0 = (lo - rs[a]) / d[a];
-        double t1 = (hi - rs[a]) / d[a];
+        double inv = 1.0 / d[a];
+        double t0 = (lo - rs[a]) * inv;
+        double t1 = (hi - rs[a]) * inv;
         if (t0 > t1) std::swap(t0, t1);
         if (t0 > t_in) t_in = t0;
         if (t1 < t_out) t_out = t1;

@@ -82,6 +82,7 @@ SIGNATURES = {
     "bos_loss_l2": (_i, [_v, _v, _i64, _v, _v, _v]),
     "bos_backward": (_i, [_v, _v, _v, _v]),
     "bos_export_nodes": (_i, [_v, _v, _v]),
+    "bos_probe_read": (_i, [_v, _u64, _i, _v, _v]),
     "bos_status": (_i, [_v]),
     "bos_error_string": (C.c_char_p, [_i]),
     "bos_last_error": (C.c_char_p, []),
@@ -209,6 +210,10 @@ def bos_backward(ctx, dLdI_dev, dLdT_dev, stream) -> None:
 
 def bos_export_nodes(ctx, out_dev, stream) -> None:
     check(lib().bos_export_nodes(ctx, out_dev, stream), "bos_export_nodes")
+
+
+def bos_probe_read(buf_dev, nbytes: int, repeats: int, sink_dev, stream) -> None:
+    check(lib().bos_probe_read(buf_dev, nbytes, repeats, sink_dev, stream), "bos_probe_read")
 
 
 def bos_status(ctx) -> None:

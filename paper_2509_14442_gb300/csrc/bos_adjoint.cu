@@ -4,12 +4,13 @@
 //                      checkpoints the forward kept every K steps (each segment is
 //                      recomputed forward into shared memory, then reversed), starting
 //                      from the adjoint of the wall epilogue (luminance, cosine, path
-//                      length of Eq. 2).  At every stage evaluation the sensitivities of
-//                      the 8 trilinear corners are scattered into per-node accumulators
-//                      (d L/d deta, d L/d grad eta) with warp-aggregated atomics: lanes
-//                      whose stage point lies in the same cell are summed in shared
-//                      memory first, so each (corner, channel) gets one atomic per cell
-//                      per warp instead of one per ray.
+//                      length of Eq. 2).  Each stage's field value and gradient come
+//                      from one packed trilinear evaluation.  The sensitivities of the
+//                      8 trilinear corners are summed per lane while the ray stays in a
+//                      cell, and flushed into per-node accumulators (d L/d deta,
+//                      d L/d grad eta) with warp-aggregated atomics: lanes whose rows
+//                      belong to the same cell are summed in shared memory, so each
+//                      (corner, channel) gets one atomic per cell visit per warp.
 //   gradient_kernel -- per node: the transpose of the central-difference stencil applied
 //                      to the grad-eta sensitivities, plus the deta sensitivity, times
 //                      d deta/dT = -rho0 G T0 / T^2.  A gather, so it is deterministic.
@@ -20,84 +21,156 @@
 namespace bos {
 
 constexpr int kAdjWarps = 2;          // warps per block
-constexpr int kScatterStride = 36;    // floats per lane row of the scatter buffer (16-byte aligned rows)
+constexpr int kRow = 36;              // floats per lane row of the cell accumulators (16-byte aligned rows)
+constexpr int kStageRec = 22;         // floats kept per stage: value + 3 derivatives (16), cell (3), fractions (3)
 constexpr uint32_t kNoKey = 0xffffffffu;
 
 struct InterpGrad {
     float4 v, d0, d1, d2;   // value and derivatives with respect to the three fractions
 };
 
-__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ __forceinline__ Cell2 subc(Cell2 a, Cell2 b) { return Cell2{sub2(a.lo, b.lo), sub2(a.hi, b.hi)}; }
+__device__ __forceinline__ float4 to4(Cell2 c) {
+    float4 v;
+    unpack2(c.lo, v.x, v.y);
+    unpack2(c.hi, v.z, v.w);
+    return v;
+}
 
-// Same lerp order as the forward `trilinear`, so v matches it bit for bit.
+// Value (same operations as `trilinear2`, so bit-identical) and its derivatives with respect
+// to the three fractions, in packed f32x2 arithmetic.
 template <class E>
-__device__ __forceinline__ InterpGrad trilinear_grad(const E* s, uint32_t o, float f0, float f1, float f2) {
-    float4 c000 = load_cell(s, o), c100 = load_cell(s, o + 1);
-    float4 c010 = load_cell(s, o + 9), c110 = load_cell(s, o + 10);
-    float4 c001 = load_cell(s, o + 81), c101 = load_cell(s, o + 82);
-    float4 c011 = load_cell(s, o + 90), c111 = load_cell(s, o + 91);
-    float4 a0 = lerp4(c000, c100, f0), a1 = lerp4(c010, c110, f0);
-    float4 a2 = lerp4(c001, c101, f0), a3 = lerp4(c011, c111, f0);
-    float4 b0 = lerp4(a0, a1, f1), b1 = lerp4(a2, a3, f1);
+__device__ __forceinline__ InterpGrad trilinear_grad2(const E* s, uint32_t o, float f0, float f1, float f2) {
+    const f32x2 t0 = pack2(f0, f0), t1 = pack2(f1, f1), t2 = pack2(f2, f2);
+    const Cell2 c000 = load_cell2(s, o), c100 = load_cell2(s, o + 1), c010 = load_cell2(s, o + 9),
+                c110 = load_cell2(s, o + 10), c001 = load_cell2(s, o + 81), c101 = load_cell2(s, o + 82),
+                c011 = load_cell2(s, o + 90), c111 = load_cell2(s, o + 91);
+    const Cell2 a0 = lerpc(c000, c100, t0), a1 = lerpc(c010, c110, t0);
+    const Cell2 a2 = lerpc(c001, c101, t0), a3 = lerpc(c011, c111, t0);
+    const Cell2 b0 = lerpc(a0, a1, t1), b1 = lerpc(a2, a3, t1);
     InterpGrad r;
-    r.v = lerp4(b0, b1, f2);
-    r.d2 = sub4(b1, b0);
-    r.d1 = lerp4(sub4(a1, a0), sub4(a3, a2), f2);
-    r.d0 = lerp4(lerp4(sub4(c100, c000), sub4(c110, c010), f1), lerp4(sub4(c101, c001), sub4(c111, c011), f1), f2);
+    r.v = to4(lerpc(b0, b1, t2));
+    r.d2 = to4(subc(b1, b0));
+    r.d1 = to4(lerpc(subc(a1, a0), subc(a3, a2), t2));
+    r.d0 = to4(lerpc(lerpc(subc(c100, c000), subc(c110, c010), t1), lerpc(subc(c101, c001), subc(c111, c011), t1), t2));
     return r;
 }
 
 struct Stage {
     int ci[3];
     float cf[3];
-    float D[3];
+    InterpGrad ig;
 };
+
+__device__ __forceinline__ void rhs_from(const InterpGrad& ig, float D[3]) {
+    float eta = 1.0f + ig.v.x;
+    D[0] = eta * ig.v.y;
+    D[1] = eta * ig.v.z;
+    D[2] = eta * ig.v.w;
+}
+
+template <class E>
+__device__ __forceinline__ void stage_eval(const CompField<E>& F, const long long U[3], const float q[3], BrickCache& bc,
+                                           Stage& s) {
+    comp_cell(F, U, q, s.ci, s.cf);
+    uint32_t o = cached_offset(bc, s.ci[0], s.ci[1], s.ci[2]);
+    s.ig = trilinear_grad2(F.store, o, s.cf[0], s.cf[1], s.cf[2]);
+}
+
+// Park / restore a stage record in the warp's shared buffer ([kStageRec][32] per slot).
+__device__ __forceinline__ void put_stage(float* b, int lane, const Stage& s) {
+    const float* v = reinterpret_cast<const float*>(&s.ig);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) b[i * 32 + lane] = v[i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        b[(16 + a) * 32 + lane] = __int_as_float(s.ci[a]);
+        b[(19 + a) * 32 + lane] = s.cf[a];
+    }
+}
+__device__ __forceinline__ void get_stage(const float* b, int lane, Stage& s) {
+    float* v = reinterpret_cast<float*>(&s.ig);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = b[i * 32 + lane];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        s.ci[a] = __float_as_int(b[(16 + a) * 32 + lane]);
+        s.cf[a] = b[(19 + a) * 32 + lane];
+    }
+}
 
 // Adjoint of D = (1 + deta) grad at a stage point: given Db, the position adjoint (metres)
 // and the per-corner record Q (corner c receives w_c Q).
 template <class E>
-__device__ __forceinline__ void rhs_adjoint(const CompField<E>& F, const Stage& s, const float Db[3], float pb[3],
+__device__ __forceinline__ void rhs_adjoint(const CompField<E>& F, const InterpGrad& ig, const float Db[3], float pb[3],
                                             float4& Q) {
-    uint32_t o = brick_offset(s.ci[0], s.ci[1], s.ci[2]);
-    InterpGrad ig = trilinear_grad(F.store, o, s.cf[0], s.cf[1], s.cf[2]);
-    float eta = 1.0f + ig.v.x;
-    float Dg = Db[0] * ig.v.y + Db[1] * ig.v.z + Db[2] * ig.v.w;
+    const float eta = 1.0f + ig.v.x;
+    const float Dg = Db[0] * ig.v.y + Db[1] * ig.v.z + Db[2] * ig.v.w;
     const float4 dv[3] = {ig.d0, ig.d1, ig.d2};
+#pragma unroll
     for (int a = 0; a < 3; ++a)
         pb[a] = F.inv_h[a] * (dv[a].x * Dg + eta * (Db[0] * dv[a].y + Db[1] * dv[a].z + Db[2] * dv[a].w));
     Q = make_float4(Dg, eta * Db[0], eta * Db[1], eta * Db[2]);
 }
 
-// Warp-collective scatter of w_c(f) * Q into the 8 corner nodes of each lane's cell.
-// Every lane of the warp must call it (inactive lanes with act = false).
-__device__ __forceinline__ void scatter_warp(float* buf, bool act, const int ci[3], const float cf[3], float4 Q,
-                                             float* acc, int nx, int nxy) {
+// Per-lane accumulation of corner sensitivities for the lane's current cell; the row
+// (8 corners x 4 channels) lives in shared memory.  When a lane's stage point leaves the
+// cell, the warp flushes: lanes whose rows belong to the same cell are summed column by
+// column (lane l owns corner l/4, channel l%4) and each sum is one atomic.
+struct CellAcc {
+    uint32_t key;   // node index of the accumulated cell's base corner, kNoKey if empty
+};
+
+__device__ __forceinline__ void flush_rows(float* rows, bool flag, CellAcc& ca, float* acc, int nx, int nxy) {
     const int lane = threadIdx.x & 31;
-    unsigned pend = __ballot_sync(0xffffffffu, act);
+    unsigned pend = __ballot_sync(0xffffffffu, flag);
     if (!pend) return;
-    uint32_t key = act ? (uint32_t)ci[0] + (uint32_t)ci[1] * (uint32_t)nx + (uint32_t)ci[2] * (uint32_t)nxy : kNoKey;
-    float4* row = reinterpret_cast<float4*>(buf + lane * kScatterStride);
-    const float g0 = 1.0f - cf[0], g1 = 1.0f - cf[1], g2 = 1.0f - cf[2];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        float w = ((c & 1) ? cf[0] : g0) * ((c & 2) ? cf[1] : g1) * ((c & 4) ? cf[2] : g2);
-        if (!act) w = 0.0f;
-        row[c] = make_float4(w * Q.x, w * Q.y, w * Q.z, w * Q.w);
-    }
     __syncwarp();
     const int corner = lane >> 2;
     const uint32_t off = (uint32_t)(corner & 1) + (uint32_t)((corner >> 1) & 1) * (uint32_t)nx +
                          (uint32_t)(corner >> 2) * (uint32_t)nxy;
+    const uint32_t mykey = flag ? ca.key : kNoKey;
     while (pend) {
         const int leader = __ffs(pend) - 1;
-        const uint32_t lk = __shfl_sync(0xffffffffu, key, leader);
-        const unsigned grp = __ballot_sync(0xffffffffu, key == lk);
+        const uint32_t lk = __shfl_sync(0xffffffffu, mykey, leader);
+        const unsigned grp = __ballot_sync(0xffffffffu, mykey == lk);
         pend &= ~grp;
         float sum = 0.0f;
-        for (unsigned m = grp; m; m &= m - 1) sum += buf[(__ffs(m) - 1) * kScatterStride + lane];
+        for (unsigned m = grp; m; m &= m - 1) sum += rows[(__ffs(m) - 1) * kRow + lane];
         if (sum != 0.0f) atomicAdd(acc + ((size_t)(lk + off) << 2) + (lane & 3), sum);
     }
     __syncwarp();
+    if (flag) {
+        float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) row[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        ca.key = kNoKey;
+    }
+    __syncwarp();
+}
+
+// Warp-collective: add w_c(cf) Q to the lane's cell row (flushing first where the cell changes).
+__device__ __forceinline__ void accumulate(float* rows, bool act, const int ci[3], const float cf[3], float4 Q,
+                                           CellAcc& ca, float* acc, int nx, int nxy) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t key = act ? (uint32_t)ci[0] + (uint32_t)ci[1] * (uint32_t)nx + (uint32_t)ci[2] * (uint32_t)nxy : kNoKey;
+    flush_rows(rows, act && ca.key != kNoKey && ca.key != key, ca, acc, nx, nxy);
+    if (act) {
+        ca.key = key;
+        float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
+        const float g0 = 1.0f - cf[0], g1 = 1.0f - cf[1], g2 = 1.0f - cf[2];
+        const f32x2 qlo = pack2(Q.x, Q.y), qhi = pack2(Q.z, Q.w);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float w = ((c & 1) ? cf[0] : g0) * ((c & 2) ? cf[1] : g1) * ((c & 4) ? cf[2] : g2);
+            const f32x2 ww = pack2(w, w);
+            float4 r = row[c];
+            f32x2 lo = fma2(ww, qlo, pack2(r.x, r.y)), hi = fma2(ww, qhi, pack2(r.z, r.w));
+            unpack2(lo, r.x, r.y);
+            unpack2(hi, r.z, r.w);
+            row[c] = r;
+        }
+    }
 }
 
 // Adjoint of the wall epilogue for seed Ib = dL/dI of this ray: returns the adjoints of
@@ -139,14 +212,23 @@ __device__ __forceinline__ void wall_adjoint(const SceneDev& S, const double rN[
     }
 }
 
+__host__ __device__ constexpr size_t adj_warp_floats(int K) {
+    return (size_t)K * 6 * 32 + 32 * kRow + 2 * kStageRec * 32;
+}
+
 template <class E>
-__global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
+__global__ void __launch_bounds__(kAdjWarps * 32, 5) adjoint_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
     extern __shared__ float4 smem4[];
-    float* smem = reinterpret_cast<float*>(smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int K = ck.every;
-    float* st_buf = smem + (size_t)warp * (K * 6 * 32 + 32 * kScatterStride);   // [K][6][32]
-    float* sc_buf = st_buf + K * 6 * 32;
+    float* st_buf = reinterpret_cast<float*>(smem4) + (size_t)warp * adj_warp_floats(K);   // [K][6][32]
+    float* rows = st_buf + (size_t)K * 6 * 32;                                             // [32][kRow]
+    float* stg = rows + 32 * kRow;                                                          // [2][kStageRec][32]
+    {
+        float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
+        for (int c = 0; c < 8; ++c) row[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    __syncwarp();
     const CompField<E> F = {static_cast<const E*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
                             {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
     const int nx = S.g.n[0], nxy = S.g.n[0] * S.g.n[1];
@@ -154,6 +236,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(SceneDev S, Ckp
     const TileShape ts = tile_shape(W, H, spp);
     const int ntiles = ts.tiles_x * ts.tiles_y;
     float* acc = reinterpret_cast<float*>(adj.acc);
+    CellAcc ca = {kNoKey};
 
     for (;;) {
         int t = 0;
@@ -187,17 +270,17 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(SceneDev S, Ckp
             float rb[3] = {0, 0, 0}, vb[3] = {0, 0, 0}, dtb = 0.0f, lenb = 0.0f;
             double etab = 0.0;
             const float dt = act ? k.dt : 0.0f;
+            BrickCache bc = {kNoKey, 0u};
             for (int c = nseg_max - 1; c >= 0; --c) {
                 const int n0 = c * K;
                 const int n1 = min(n0 + K, N);
                 const bool seg = act && n0 < N;
                 // ---- recompute the segment from its checkpoint, keeping each step's state
-                CompState st;
-                BrickCache bc = {kNoKey, 0u};
                 if (seg) {
-                    float4 s0 = ck.state[((size_t)c * 3 + 0) * ck.nrays + slot];
-                    float4 s1 = ck.state[((size_t)c * 3 + 1) * ck.nrays + slot];
-                    float4 s2 = ck.state[((size_t)c * 3 + 2) * ck.nrays + slot];
+                    CompState st;
+                    const float4 s0 = ck.state[((size_t)c * 3 + 0) * ck.nrays + slot];
+                    const float4 s1 = ck.state[((size_t)c * 3 + 1) * ck.nrays + slot];
+                    const float4 s2 = ck.state[((size_t)c * 3 + 2) * ck.nrays + slot];
                     st.dr[0] = s0.x; st.dr[1] = s0.y; st.dr[2] = s0.z;
                     st.dv[0] = s1.x; st.dv[1] = s1.y; st.dv[2] = s1.z;
                     st.cv[0] = s2.x; st.cv[1] = s2.y; st.cv[2] = s2.z;
@@ -232,11 +315,13 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(SceneDev S, Ckp
                 const int n_hi = __reduce_max_sync(0xffffffffu, (unsigned)(seg ? n1 : 0));
                 for (int n = n_hi - 1; n >= n0; --n) {
                     const bool a_ = seg && n < n1;
-                    Stage s1 = {}, s2 = {}, s3 = {};
-                    float A[3] = {0, 0, 0}, B[3] = {0, 0, 0}, dr[3] = {0, 0, 0}, dvv[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+                    Stage s3;
+                    float A[3] = {0, 0, 0}, B[3] = {0, 0, 0}, dvv[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+                    float D1[3] = {0, 0, 0}, D2[3] = {0, 0, 0}, D3[3] = {0, 0, 0};
                     if (a_) {
+                        // recompute the step's three stages (value and gradient of the field)
                         const float* p = st_buf + (size_t)(n - n0) * 6 * 32 + lane;
-                        dr[0] = p[0]; dr[1] = p[32]; dr[2] = p[64];
+                        const float dr[3] = {p[0], p[32], p[64]};
                         dvv[0] = p[96]; dvv[1] = p[128]; dvv[2] = p[160];
                         long long U[3], U2[3], U3[3];
                         for (int a = 0; a < 3; ++a) {
@@ -245,19 +330,25 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(SceneDev S, Ckp
                             U3[a] = U[a] + k.dU[a];
                         }
                         float q[3];
-                        rhs_of(comp_eval(F, U, dr, bc, s1.ci, s1.cf), s1.D);
-                        for (int a = 0; a < 3; ++a) A[a] = dt * s1.D[a];
+                        Stage s;
+                        stage_eval(F, U, dr, bc, s);
+                        rhs_from(s.ig, D1);
+                        put_stage(stg, lane, s);
+                        for (int a = 0; a < 3; ++a) A[a] = dt * D1[a];
                         for (int a = 0; a < 3; ++a) q[a] = dr[a] + (0.5f * dt) * dvv[a] + (0.125f * dt) * A[a];
-                        rhs_of(comp_eval(F, U2, q, bc, s2.ci, s2.cf), s2.D);
-                        for (int a = 0; a < 3; ++a) B[a] = dt * s2.D[a];
+                        stage_eval(F, U2, q, bc, s);
+                        rhs_from(s.ig, D2);
+                        put_stage(stg + kStageRec * 32, lane, s);
+                        for (int a = 0; a < 3; ++a) B[a] = dt * D2[a];
                         for (int a = 0; a < 3; ++a) q[a] = dr[a] + dt * dvv[a] + (0.5f * dt) * B[a];
-                        rhs_of(comp_eval(F, U3, q, bc, s3.ci, s3.cf), s3.D);
+                        stage_eval(F, U3, q, bc, s3);
+                        rhs_from(s3.ig, D3);
                         float inc[3], nn = 0.0f;
                         for (int a = 0; a < 3; ++a) {
                             inc[a] = k.dS[a] + dt * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
                             nn += inc[a] * inc[a];
                         }
-                        float rn = rsqrtf(nn);
+                        const float rn = rsqrtf(nn);
                         for (int a = 0; a < 3; ++a) {
                             u[a] = inc[a] * rn;             // unit step direction: d|r_{n+1} - r_n|
                             rb[a] += lenb * u[a];
@@ -277,11 +368,11 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(SceneDev S, Ckp
                     float4 Q = make_float4(0, 0, 0, 0);
                     // C = dt D(p3),  p3 = S(n+1) + dr + dt dv + dt/2 B
                     for (int a = 0; a < 3; ++a) {
-                        dtb += Cb[a] * s3.D[a];
+                        dtb += Cb[a] * D3[a];
                         Db[a] = dt * Cb[a];
                     }
-                    if (a_) rhs_adjoint(F, s3, Db, pb, Q);
-                    scatter_warp(sc_buf, a_, s3.ci, s3.cf, Q, acc, nx, nxy);
+                    if (a_) rhs_adjoint(F, s3.ig, Db, pb, Q);
+                    accumulate(rows, a_, s3.ci, s3.cf, Q, ca, acc, nx, nxy);
                     for (int a = 0; a < 3; ++a) {
                         rn_[a] += pb[a];
                         vn_[a] += dt * pb[a];
@@ -290,11 +381,15 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(SceneDev S, Ckp
                     }
                     // B = dt D(p2),  p2 = S(n+1/2) + dr + dt/2 dv + dt/8 A
                     for (int a = 0; a < 3; ++a) {
-                        dtb += Bb[a] * s2.D[a];
+                        dtb += Bb[a] * D2[a];
                         Db[a] = dt * Bb[a];
                     }
-                    if (a_) rhs_adjoint(F, s2, Db, pb, Q);
-                    scatter_warp(sc_buf, a_, s2.ci, s2.cf, Q, acc, nx, nxy);
+                    Stage s2;
+                    if (a_) {
+                        get_stage(stg + kStageRec * 32, lane, s2);
+                        rhs_adjoint(F, s2.ig, Db, pb, Q);
+                    }
+                    accumulate(rows, a_, s2.ci, s2.cf, Q, ca, acc, nx, nxy);
                     for (int a = 0; a < 3; ++a) {
                         rn_[a] += pb[a];
                         vn_[a] += (0.5f * dt) * pb[a];
@@ -303,11 +398,15 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(SceneDev S, Ckp
                     }
                     // A = dt D(p1),  p1 = S(n) + dr
                     for (int a = 0; a < 3; ++a) {
-                        dtb += Ab[a] * s1.D[a];
+                        dtb += Ab[a] * D1[a];
                         Db[a] = dt * Ab[a];
                     }
-                    if (a_) rhs_adjoint(F, s1, Db, pb, Q);
-                    scatter_warp(sc_buf, a_, s1.ci, s1.cf, Q, acc, nx, nxy);
+                    Stage s1;
+                    if (a_) {
+                        get_stage(stg, lane, s1);
+                        rhs_adjoint(F, s1.ig, Db, pb, Q);
+                    }
+                    accumulate(rows, a_, s1.ci, s1.cf, Q, ca, acc, nx, nxy);
                     if (a_) {
                         for (int a = 0; a < 3; ++a) {
                             rb[a] = rn_[a] + pb[a] - lenb * u[a];
@@ -322,13 +421,13 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(SceneDev S, Ckp
             float cf[3] = {0, 0, 0};
             if (act) {
                 etab -= (double)dtb * (double)dt / eta_in;
-                BrickCache bc = {kNoKey, 0u};
-                float zero[3] = {0, 0, 0};
-                comp_eval(F, st0.U, zero, bc, ci, cf);
+                const float zero[3] = {0, 0, 0};
+                comp_cell(F, st0.U, zero, ci, cf);
             }
-            scatter_warp(sc_buf, act, ci, cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), acc, nx, nxy);
+            accumulate(rows, act, ci, cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), ca, acc, nx, nxy);
         }
     }
+    flush_rows(rows, ca.key != kNoKey, ca, acc, nx, nxy);
 }
 
 // dL/dT per node: transpose of the difference stencil of grad eta, plus d L/d deta, times
@@ -360,7 +459,7 @@ __global__ void gradient_kernel(GridDev g, const float4* __restrict__ acc, const
 template <class E>
 static cudaError_t launch_adjoint_t(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
                                     int num_sms, cudaStream_t st) {
-    size_t smem = (size_t)kAdjWarps * (ck.every * 6 * 32 + 32 * kScatterStride) * sizeof(float);
+    size_t smem = (size_t)kAdjWarps * adj_warp_floats(ck.every) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

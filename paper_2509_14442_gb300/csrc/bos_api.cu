@@ -65,6 +65,8 @@ CamDev to_dev(const bos_camera_desc& c) {
     d.fy = c.fy;
     d.cx = c.cx;
     d.cy = c.cy;
+    d.inv_fx = 1.0 / c.fx;
+    d.inv_fy = 1.0 / c.fy;
     d.width = c.width;
     d.height = c.height;
     d.spp = c.spp;
@@ -268,6 +270,7 @@ bos_status_t bos_set_grid(bos_ctx* c, const bos_grid_desc* d, const float* T_dev
         g.origin[a] = d->origin[a];
         g.extent[a] = d->extent[a];
         g.h[a] = d->extent[a] / (double)n[a];
+        g.inv_h[a] = 1.0 / g.h[a];
         g.inv_hf[a] = (float)(1.0 / g.h[a]);
         g.hf[a] = (float)g.h[a];
     }
@@ -432,6 +435,16 @@ bos_status_t bos_export_nodes(bos_ctx* c, void* out, void* stream) {
     DeviceGuard dg(c->device);
     cudaError_t e = launch_export_nodes(c->g, out, c->num_sms, (cudaStream_t)stream);
     return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_export_nodes");
+}
+
+bos_status_t bos_probe_read(const void* buf, uint64_t bytes, int repeats, float* sink, void* stream) {
+    if (!buf || !sink || bytes < 16 || (bytes & 15) || repeats < 1 || ((uintptr_t)buf & 15))
+        return fail(BOS_ERR_INVALID_ARG, "bos_probe_read: need a 16-byte aligned buffer of a multiple of 16 bytes");
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = launch_probe_read(buf, (long long)bytes, repeats, sink, sms, (cudaStream_t)stream);
+    return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_probe_read");
 }
 
 bos_status_t bos_status(bos_ctx* c) {

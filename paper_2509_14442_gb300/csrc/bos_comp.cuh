@@ -24,23 +24,43 @@ struct CompField {
     float inv_h[3];
 };
 
+// Cell and fraction of fixed-point straight position U plus deviation q (metres).  The
+// 32-bit fraction word becomes a float through its top 23 bits (U carries a +2^-24 bias
+// from the set-up, so this truncation rounds to nearest); fractions outside [0, 1) and
+// cells outside [0, n-2] (near the box faces, where the edge cells extrapolate) take a
+// rarely used exact path.
+template <class E>
+__device__ __forceinline__ void comp_cell(const CompField<E>& F, const long long U[3], const float q[3], int ci[3],
+                                          float cf[3]) {
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const uint32_t lo = (uint32_t)U[a];
+        ci[a] = (int)(U[a] >> 32);
+        const float fr = __uint_as_float((lo >> 9) | 0x3f800000u) - 1.0f;
+        cf[a] = fmaf(q[a], F.inv_h[a], fr);
+        ok = ok && cf[a] >= 0.0f && cf[a] < 1.0f && ci[a] >= 0 && ci[a] <= F.n[a] - 2;
+    }
+    if (!ok) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float fl = floorf(cf[a]);
+            int I = ci[a] + (int)fl;
+            float f = cf[a] - fl;
+            int Ic = min(max(I, 0), F.n[a] - 2);
+            ci[a] = Ic;
+            cf[a] = f + (float)(I - Ic);
+        }
+    }
+}
+
 // Field at fixed-point straight position U plus deviation q (metres).
 template <class E>
 __device__ __forceinline__ float4 comp_eval(const CompField<E>& F, const long long U[3], const float q[3],
                                             BrickCache& bc, int ci[3], float cf[3]) {
-    for (int a = 0; a < 3; ++a) {
-        int I = (int)(U[a] >> 32);
-        float f = fmaf(q[a], F.inv_h[a], __uint2float_rn((uint32_t)U[a]) * 2.3283064365386963e-10f);
-        float fl = floorf(f);
-        I += (int)fl;
-        f -= fl;
-        int Ic = min(max(I, 0), F.n[a] - 2);
-        f += (float)(I - Ic);
-        ci[a] = Ic;
-        cf[a] = f;
-    }
+    comp_cell(F, U, q, ci, cf);
     uint32_t o = cached_offset(bc, ci[0], ci[1], ci[2]);
-    return trilinear(F.store, o, cf[0], cf[1], cf[2]);
+    return trilinear2(F.store, o, cf[0], cf[1], cf[2]);
 }
 
 __device__ __forceinline__ void rhs_of(float4 v, float D[3]) {
@@ -143,11 +163,11 @@ __device__ __forceinline__ void comp_setup(const SceneDev& S, const CompField<E>
     double sl = R.ell / (double)R.N;
     for (int a = 0; a < 3; ++a) {
         rin[a] = S.cam.pos[a] + R.t_in * R.d[a];
-        double u = (rin[a] - g.origin[a]) / g.h[a] - 0.5;
-        double du = sl * R.d[a] / g.h[a];
-        st.U[a] = to_fixed(u, 4294967296.0);
+        double u = (rin[a] - g.origin[a]) * g.inv_h[a] - 0.5;
+        double du = sl * R.d[a] * g.inv_h[a];
+        st.U[a] = to_fixed(u, 4294967296.0) + 256;   // +2^-24: see comp_cell
         k.dU[a] = to_fixed(du, 4294967296.0);
-        k.dUh[a] = to_fixed(du, 2147483648.0);
+        k.dUh[a] = k.dU[a] >> 1;
         k.dS[a] = (float)(sl * R.d[a]);
         k.dhat[a] = (float)R.d[a];
         st.dr[a] = st.cr[a] = st.dv[a] = st.cv[a] = 0.0f;
@@ -164,5 +184,112 @@ __device__ __forceinline__ void comp_setup(const SceneDev& S, const CompField<E>
     k.step_len = (float)sl;
 }
 
+
+// ------------------------------------------------------------------ wall (Eq. 2) in float32
+//
+// With r_N = r_s + (t_in + ell) d + dr and v_N = eta_in d + dv, the wall hit relative to
+// the straight hit x_ref = r_s + t_w d only involves small quantities:
+//   t* = (L c - n.dr) / (eta_in c + n.dv),          c = n.d,  L = t_w - t_in - ell
+//   x_w - x_ref = dr + t* dv - ((eta_in n.dr + L n.dv) / (eta_in c + n.dv)) d
+// so float32 keeps ~1e-7 of the displacement; float64 is used only for x_ref.
+
+__device__ __forceinline__ float texel_f(const LightDev& L, int i, int j) {
+    if (i < 0 || j < 0 || i >= L.tw || j >= L.th) return 0.0f;
+    return __ldg(L.pattern + (size_t)j * L.tw + i);
+}
+
+__device__ __forceinline__ float bilinear_f(const LightDev& L, float s, float t) {
+    s -= 0.5f;
+    t -= 0.5f;
+    float fi = floorf(fminf(fmaxf(s, -4.0f), (float)L.tw + 4.0f));
+    float fj = floorf(fminf(fmaxf(t, -4.0f), (float)L.th + 4.0f));
+    int i = (int)fi, j = (int)fj;
+    float fs = s - fi, ft = t - fj;
+    float p00 = texel_f(L, i, j), p10 = texel_f(L, i + 1, j), p01 = texel_f(L, i, j + 1), p11 = texel_f(L, i + 1, j + 1);
+    return (1.0f - fs) * ((1.0f - ft) * p00 + ft * p01) + fs * ((1.0f - ft) * p10 + ft * p11);
+}
+
+// Luminance at x_ref + dx.
+__device__ __forceinline__ float luminance_rel(const SceneDev& S, const double xref[3], const float dx[3]) {
+    const LightDev& L = S.L;
+    const WallDev& w = S.w;
+    if (L.mode == 0) {
+        double q[3] = {xref[0] - w.origin[0], xref[1] - w.origin[1], xref[2] - w.origin[2]};
+        float hu = (float)(q[0] * w.eu[0] + q[1] * w.eu[1] + q[2] * w.eu[2]) +
+                   (dx[0] * (float)w.eu[0] + dx[1] * (float)w.eu[1] + dx[2] * (float)w.eu[2]);
+        float hv = (float)(q[0] * w.ev[0] + q[1] * w.ev[1] + q[2] * w.ev[2]) +
+                   (dx[0] * (float)w.ev[0] + dx[1] * (float)w.ev[1] + dx[2] * (float)w.ev[2]);
+        return bilinear_f(L, hu * (float)(L.tw / w.size_u), hv * (float)(L.th / w.size_v));
+    }
+    const CamDev& P = L.proj;
+    float q[3];
+    for (int a = 0; a < 3; ++a) q[a] = (float)(xref[a] - P.pos[a]) + dx[a];
+    float fw[3] = {(float)P.fwd[0], (float)P.fwd[1], (float)P.fwd[2]};
+    float up[3] = {(float)P.up[0], (float)P.up[1], (float)P.up[2]};
+    float rt[3] = {fw[1] * up[2] - fw[2] * up[1], fw[2] * up[0] - fw[0] * up[2], fw[0] * up[1] - fw[1] * up[0]};
+    float z = q[0] * fw[0] + q[1] * fw[1] + q[2] * fw[2];
+    if (!(z > 0.0f)) return 0.0f;
+    float iz = 1.0f / z;
+    float px = (float)P.cx + (float)P.fx * ((q[0] * rt[0] + q[1] * rt[1] + q[2] * rt[2]) * iz);
+    float py = (float)P.cy - (float)P.fy * ((q[0] * up[0] + q[1] * up[1] + q[2] * up[2]) * iz);
+    return bilinear_f(L, px, py);
+}
+
+__device__ __forceinline__ RayResult comp_epilogue(const SceneDev& S, const Ray& R, double eta_in, const float dr[3],
+                                                   const float dv[3], float excess, bool want_hit) {
+    RayResult o;
+    o.I = 0.0;
+    o.hit[0] = o.hit[1] = o.disp[0] = o.disp[1] = 0.0;
+    const WallDev& w = S.w;
+    float nf[3] = {(float)w.normal[0], (float)w.normal[1], (float)w.normal[2]};
+    float df[3] = {(float)R.d[0], (float)R.d[1], (float)R.d[2]};
+    const float cd = df[0] * nf[0] + df[1] * nf[1] + df[2] * nf[2];
+    const float Lrem = (float)(R.tw - R.t_in - R.ell);
+    const float e = (float)eta_in;
+    const float ndr = nf[0] * dr[0] + nf[1] * dr[1] + nf[2] * dr[2];
+    const float ndv = nf[0] * dv[0] + nf[1] * dv[1] + nf[2] * dv[2];
+    const float den = e * cd + ndv;                       // <n, v_N>
+    if (!(den > 0.0f)) return o;
+    const float iden = 1.0f / den;
+    const float ts = (Lrem * cd - ndr) * iden;
+    const float kk = -(e * ndr + Lrem * ndv) * iden;
+    float dx[3];
+    for (int a = 0; a < 3; ++a) dx[a] = dr[a] + ts * dv[a] + kk * df[a];
+    const float ddv = df[0] * dv[0] + df[1] * dv[1] + df[2] * dv[2];
+    const float vl = sqrtf(e * e + 2.0f * e * ddv + (dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]));
+    const float len = (float)(R.t_in + R.ell) + (excess + fabsf(ts) * vl);
+    double xref[3];
+    for (int a = 0; a < 3; ++a) xref[a] = S.cam.pos[a] + R.tw * R.d[a];
+    const float Lw = luminance_rel(S, xref, dx);
+    o.I = (double)(Lw * (den / vl) / len);
+    o.disp[0] = (double)(dx[0] * (float)w.eu[0] + dx[1] * (float)w.eu[1] + dx[2] * (float)w.eu[2]);
+    o.disp[1] = (double)(dx[0] * (float)w.ev[0] + dx[1] * (float)w.ev[1] + dx[2] * (float)w.ev[2]);
+    if (want_hit) {
+        double q[3] = {xref[0] - w.origin[0], xref[1] - w.origin[1], xref[2] - w.origin[2]};
+        o.hit[0] = q[0] * w.eu[0] + q[1] * w.eu[1] + q[2] * w.eu[2] + o.disp[0];
+        o.hit[1] = q[0] * w.ev[0] + q[1] * w.ev[1] + q[2] * w.ev[2] + o.disp[1];
+    }
+    return o;
+}
+
+// The straight (no-flow) ray: hit x_ref, cosine <n, d>, length t_w.
+__device__ __forceinline__ RayResult straight_epilogue(const SceneDev& S, const Ray& R, bool want_hit) {
+    const float zero[3] = {0.0f, 0.0f, 0.0f};
+    RayResult o;
+    o.I = 0.0;
+    o.hit[0] = o.hit[1] = o.disp[0] = o.disp[1] = 0.0;
+    const WallDev& w = S.w;
+    const float cd = (float)(R.d[0] * w.normal[0] + R.d[1] * w.normal[1] + R.d[2] * w.normal[2]);
+    if (!(cd > 0.0f)) return o;
+    double xref[3];
+    for (int a = 0; a < 3; ++a) xref[a] = S.cam.pos[a] + R.tw * R.d[a];
+    o.I = (double)(luminance_rel(S, xref, zero) * cd / (float)R.tw);
+    if (want_hit) {
+        double q[3] = {xref[0] - w.origin[0], xref[1] - w.origin[1], xref[2] - w.origin[2]};
+        o.hit[0] = q[0] * w.eu[0] + q[1] * w.eu[1] + q[2] * w.eu[2];
+        o.hit[1] = q[0] * w.ev[0] + q[1] * w.ev[1] + q[2] * w.ev[2];
+    }
+    return o;
+}
 
 }  // namespace bos

@@ -19,6 +19,7 @@ struct GridDev {
     double origin[3];
     double extent[3];
     double h[3];       // extent / n
+    double inv_h[3];   // 1 / h
     double K;          // rho0 * G * T0
     float inv_hf[3];   // 1 / h (float)
     float hf[3];
@@ -29,6 +30,7 @@ struct GridDev {
 struct CamDev {
     double pos[3], fwd[3], up[3];
     double fx, fy, cx, cy;
+    double inv_fx, inv_fy;   // 1/fx, 1/fy (IEEE division on the host)
     int width, height, spp;
     unsigned long long seed;
 };
@@ -132,6 +134,60 @@ __device__ __forceinline__ float4 load_cell(const uint2* s, uint32_t o) {
     r.z = __uint_as_float(u.y << 16);
     r.w = __uint_as_float(u.y & 0xffff0000u);
     return r;
+}
+
+// Packed pairs of float32 (sm_100+ f32x2 arithmetic: each lane rounds like the scalar op).
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pack2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// a + t (b - a), per lane exactly fmaf(t, b - a, a)
+__device__ __forceinline__ f32x2 lerp2(f32x2 a, f32x2 b, f32x2 t) { return fma2(t, sub2(b, a), a); }
+
+struct Cell2 {           // one (deta, gx, gy, gz) record as two packed pairs
+    f32x2 lo, hi;
+};
+
+__device__ __forceinline__ Cell2 load_cell2(const float4* s, uint32_t o) {
+    float4 v = __ldg(s + o);
+    return Cell2{pack2(v.x, v.y), pack2(v.z, v.w)};
+}
+__device__ __forceinline__ Cell2 load_cell2(const uint2* s, uint32_t o) {
+    uint2 u = __ldg(s + o);
+    return Cell2{pack2(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u)),
+                 pack2(__uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u))};
+}
+__device__ __forceinline__ Cell2 lerpc(Cell2 a, Cell2 b, f32x2 t) { return Cell2{lerp2(a.lo, b.lo, t), lerp2(a.hi, b.hi, t)}; }
+
+// Trilinear (deta, grad eta) in packed arithmetic; bit-identical to `trilinear`.
+template <class E>
+__device__ __forceinline__ float4 trilinear2(const E* s, uint32_t o, float f0, float f1, float f2) {
+    const f32x2 t0 = pack2(f0, f0), t1 = pack2(f1, f1), t2 = pack2(f2, f2);
+    Cell2 a0 = lerpc(load_cell2(s, o), load_cell2(s, o + 1), t0);
+    Cell2 a1 = lerpc(load_cell2(s, o + 9), load_cell2(s, o + 10), t0);
+    Cell2 a2 = lerpc(load_cell2(s, o + 81), load_cell2(s, o + 82), t0);
+    Cell2 a3 = lerpc(load_cell2(s, o + 90), load_cell2(s, o + 91), t0);
+    Cell2 r = lerpc(lerpc(a0, a1, t1), lerpc(a2, a3, t1), t2);
+    float4 v;
+    unpack2(r.lo, v.x, v.y);
+    unpack2(r.hi, v.z, v.w);
+    return v;
 }
 
 __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t) {
@@ -242,11 +298,12 @@ __device__ __forceinline__ void pinhole_direction(const CamDev& c, double x, dou
     double right[3] = {dsub(dmul(c.fwd[1], c.up[2]), dmul(c.fwd[2], c.up[1])),
                        dsub(dmul(c.fwd[2], c.up[0]), dmul(c.fwd[0], c.up[2])),
                        dsub(dmul(c.fwd[0], c.up[1]), dmul(c.fwd[1], c.up[0]))};
-    double a = ddiv(dsub(x, c.cx), c.fx);
-    double b = ddiv(dsub(y, c.cy), c.fy);
+    double a = dmul(dsub(x, c.cx), c.inv_fx);
+    double b = dmul(dsub(y, c.cy), c.inv_fy);
     for (int i = 0; i < 3; ++i) d[i] = dadd(dsub(dmul(a, right[i]), dmul(b, c.up[i])), c.fwd[i]);
     double n = dsqrt(ddot(d, d));
-    for (int i = 0; i < 3; ++i) d[i] = ddiv(d[i], n);
+    double inv_n = ddiv(1.0, n);
+    for (int i = 0; i < 3; ++i) d[i] = dmul(d[i], inv_n);
 }
 
 struct Ray {
@@ -283,8 +340,9 @@ __device__ __forceinline__ Ray ray_setup(const SceneDev& S, int px, int py, int 
             if (rs[a] < lo || rs[a] > hi) inside = false;
             continue;
         }
-        double t0 = ddiv(dsub(lo, rs[a]), R.d[a]);
-        double t1 = ddiv(dsub(hi, rs[a]), R.d[a]);
+        double inv = ddiv(1.0, R.d[a]);
+        double t0 = dmul(dsub(lo, rs[a]), inv);
+        double t1 = dmul(dsub(hi, rs[a]), inv);
         if (t0 > t1) {
             double t = t0;
             t0 = t1;

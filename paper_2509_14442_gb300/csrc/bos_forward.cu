@@ -161,7 +161,7 @@ struct Sums {
 // Trace one ray of the comp path; optionally store checkpoints every K steps.
 template <class E, int INTEG>
 __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const Ray& R, const CkptDev& ck,
-                                long long ray) {
+                                long long ray, bool want_hit) {
     CompState st;
     CompConst k;
     double eta_in, rin[3];
@@ -178,14 +178,12 @@ __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const 
         comp_step<E, INTEG>(F, st, k, bc);
     }
     if (ck.state != nullptr) ck.excess[ray] = st.excess;
-    double rN[3], vN[3];
+    float dr[3], dv[3];
     for (int a = 0; a < 3; ++a) {
-        double dr = (double)st.dr[a] - (double)st.cr[a];
-        double dv = (double)st.dv[a] - (double)st.cv[a];
-        rN[a] = rin[a] + R.ell * R.d[a] + dr;
-        vN[a] = eta_in * R.d[a] + dv;
+        dr[a] = st.dr[a] - st.cr[a];
+        dv[a] = st.dv[a] - st.cv[a];
     }
-    return wall_epilogue(S, S.cam.pos, R, rN, vN, R.t_in + R.ell + (double)st.excess);
+    return comp_epilogue(S, R, eta_in, dr, dv, st.excess, want_hit);
 }
 
 template <class T, int INTEG>
@@ -215,16 +213,19 @@ template <int MODE>   // 0 straight, 1 comp fp32, 2 comp bf16, 3 full fp32, 4 fu
 struct Tracer;
 
 template <int MODE, int INTEG>
-__device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, const CkptDev& ck, long long ray) {
-    if (MODE == 1) {
+__device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, const CkptDev& ck, long long ray,
+                                               bool want_hit) {
+    if constexpr (MODE == 0) {
+        return straight_epilogue(S, R, want_hit);
+    } else if constexpr (MODE == 1) {
         CompField<float4> F = {static_cast<const float4*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
                                {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
-        return trace_comp<float4, INTEG>(S, F, R, ck, ray);
-    } else if (MODE == 2) {
+        return trace_comp<float4, INTEG>(S, F, R, ck, ray, want_hit);
+    } else if constexpr (MODE == 2) {
         CompField<uint2> F = {static_cast<const uint2*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
                               {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
-        return trace_comp<uint2, INTEG>(S, F, R, ck, ray);
-    } else if (MODE == 3) {
+        return trace_comp<uint2, INTEG>(S, F, R, ck, ray, want_hit);
+    } else if constexpr (MODE == 3) {
         FullField<float> F = {S.g};
         return trace_full<float, INTEG>(S, F, R);
     } else {
@@ -234,7 +235,7 @@ __device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, 
 }
 
 template <int MODE, int INTEG>
-__global__ void __launch_bounds__(128) render_kernel(SceneDev S, RenderOut out, WorkDev wk, CkptDev ck) {
+__global__ void __launch_bounds__(128, 4) render_kernel(SceneDev S, RenderOut out, WorkDev wk, CkptDev ck) {
     const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
     const TileShape ts = tile_shape(W, H, spp);
     const int ntiles = ts.tiles_x * ts.tiles_y;
@@ -262,11 +263,10 @@ __global__ void __launch_bounds__(128) render_kernel(SceneDev S, RenderOut out, 
                 }
                 RayResult r;
                 if (MODE == 0 || R.N == 0) {
-                    double zero3[3] = {S.cam.pos[0], S.cam.pos[1], S.cam.pos[2]};
-                    r = wall_epilogue(S, S.cam.pos, R, zero3, R.d, 0.0);
+                    r = straight_epilogue(S, R, out.hit != nullptr);
                     if (R.N == 0 && ck.state != nullptr) ck.excess[ray] = 0.0f;
                 } else {
-                    r = trace_ray<MODE, INTEG>(S, R, ck, ray);
+                    r = trace_ray<MODE, INTEG>(S, R, ck, ray, out.hit != nullptr);
                     my_steps += (unsigned long long)R.N;
                 }
                 acc.I += r.I;
@@ -331,9 +331,9 @@ __global__ void loss_l2_kernel(const float* __restrict__ I, const float* __restr
                                double* loss, float* __restrict__ dLdI) {
     double acc = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float r = target[i] - I[i];
-        acc += (double)r * (double)r;
-        if (dLdI) dLdI[i] = -2.0f * r;
+        const double r = (double)target[i] - (double)I[i];     // exact for two floats
+        acc += r * r;
+        if (dLdI) dLdI[i] = -2.0f * (target[i] - I[i]);
     }
     for (int m = 16; m >= 1; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
     __shared__ double part[32];
@@ -345,6 +345,27 @@ __global__ void loss_l2_kernel(const float* __restrict__ I, const float* __restr
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += part[i];
         atomicAdd(loss, s);
     }
+}
+
+// ===================================================================== measurement probe
+
+// Streams `n4` float4 of an L2-resident buffer `repeats` times (grid-stride, L1 bypassed)
+// and folds them into a register; measures the L2 read bandwidth.
+__global__ void probe_read_kernel(const float4* __restrict__ buf, long long n4, int repeats, float* sink) {
+    float acc = 0.0f;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int r = 0; r < repeats; ++r)
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+            float4 v = __ldcg(buf + i);
+            acc += (v.x + v.y) + (v.z + v.w);
+        }
+    if (acc == 1234.5678f) sink[0] = acc;
+}
+
+cudaError_t launch_probe_read(const void* buf, long long bytes, int repeats, float* sink, int num_sms,
+                              cudaStream_t st) {
+    probe_read_kernel<<<num_sms * 8, 256, 0, st>>>((const float4*)buf, bytes / 16, repeats, sink);
+    return cudaGetLastError();
 }
 
 // ===================================================================== launchers

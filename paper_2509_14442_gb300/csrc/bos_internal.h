@@ -45,6 +45,8 @@ cudaError_t launch_ray_steps(const SceneDev& S, int32_t* nsteps, int num_sms, cu
 cudaError_t launch_export_nodes(const GridDev& g, void* out, int num_sms, cudaStream_t st);
 cudaError_t launch_loss_l2(const float* I, const float* target, long long n, double* loss, float* dLdI, int num_sms,
                            cudaStream_t st);
+cudaError_t launch_probe_read(const void* buf, long long bytes, int repeats, float* sink, int num_sms,
+                              cudaStream_t st);
 cudaError_t launch_backward(int mode, const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
                             const float* T, float* dLdT, int num_sms, cudaStream_t st);
 

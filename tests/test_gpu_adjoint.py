@@ -53,8 +53,8 @@ def test_loss_kernel_matches_torch(bos):
     tgt = torch.as_tensor(rng.random((37, 53)).astype(np.float32), device="cuda")
     loss, g = bos.loss_l2(I, tgt)
     torch.cuda.synchronize()
-    ref = ((tgt.double() - I.double()) ** 2).sum()
-    assert abs(loss.item() - ref.item()) <= 1e-12 * ref.item()
+    ref = ((tgt.double() - I.double()) ** 2).sum()          # each difference exact in float64
+    assert abs(loss.item() - ref.item()) <= 1e-13 * ref.item()
     assert torch.equal(g, -2.0 * (tgt - I))
 
 
@@ -87,7 +87,10 @@ def test_autograd_function_loss_gradient(bos, orc):
     from paper_2509_14442_gb300 import torch_ops
 
     sc = S.room((48, 48, 36), 64, 56, 1, 3300)
-    target = orc.render(sc.replace(T=S.plume_field(sc.grid, 3301)))["I"]
+    # target: the same room lit with another speckle, so that target - I = O(I) and the
+    # seed -2 (target - I) is not dominated by the ~1e-6 intensity rounding of either side
+    other = S.Light(1, S.speckle(512, 512, 3301), sc.light.proj)
+    target = orc.render(sc.replace(light=other))["I"]
     ctx = bos.Context(0)
     ctx.set_geometry(sc.camera, sc.wall, sc.light, sc.integ)
     T = torch.as_tensor(sc.T, device="cuda").requires_grad_(True)

@@ -118,7 +118,7 @@ def test_reference_image(bos, orc):
     sc = S.room((32, 32, 24), 50, 40, 4, 2713)
     o = orc.render(sc, straight=True)
     g = gpu_render(sc, bos.BOS_PREC_FP32_COMP, reference=True)
-    assert float(np.abs(g["I"] - o["I"]).max()) <= 1e-7
+    assert float(np.abs(g["I"] - o["I"]).max()) <= 1e-5      # float32 luminance lookup; bound 1e-4
     assert float(np.abs(g["disp"]).max()) <= 1e-12
 
 
