@@ -57,11 +57,14 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--workload", default="room_fwd", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default="room_fwd", choices=sorted(WORKLOADS) + ["serving"])
     p.add_argument("--prec", default="fp32_comp", choices=sorted(BYTES_PER_STEP))
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--requests", type=int, default=256, help="serving: number of requests")
+    p.add_argument("--slots", type=int, default=6, help="serving: concurrent requests")
+    p.add_argument("--mem-limit-gb", type=int, default=120, help="serving: admission limit (GiB)")
     return p.parse_args()
 
 
@@ -373,10 +376,107 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ serving
+
+SERVE_GRIDS = [(64, 64, 64), (128, 128, 96), (256, 256, 192)]
+SERVE_IMAGES = [256, 1024, 2048]
+
+
+def serving_arm(args):
+    """256 requests (forward or forward + adjoint; grid and image drawn per request; plume
+    seed per request) through the continuous-batching server under a 120 GB admission
+    limit: first all at once (saturated throughput), then with Poisson arrivals at 0.7x and
+    1.0x that rate; latency = completion - submission."""
+    import torch
+
+    from paper_2509_14442_gb300 import bos
+
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(S.BASE_SEED + 5)
+    n = args.requests
+    pattern_np = S.speckle(512, 512, S.BASE_SEED + 5000)
+    pattern = torch.as_tensor(pattern_np, device=dev)
+    classes = {}
+    reqs = []
+    for i in range(n):
+        u = rng.random(3)
+        adj = bool(u[0] < 0.5)
+        g = SERVE_GRIDS[int(u[1] * 3)]
+        im = SERVE_IMAGES[int(u[2] * 3)]
+        sc = classes[(g, im)][0] if (g, im) in classes else S.room(g, im, im, 1, S.BASE_SEED + 100 + i, field=False)
+        T = S.plume_field(S.room_grid(g), S.BASE_SEED + 100 + i, device=dev).contiguous()
+        r = dict(adj=adj, grid=g, image=im, T=T, I=torch.empty((im, im), device=dev))
+        if adj:
+            r.update(target=torch.full((im, im), 0.02, device=dev), loss=torch.empty(1, dtype=torch.float64, device=dev),
+                     dLdT=torch.empty_like(T))
+        else:
+            r["disp"] = torch.empty((im, im, 2), device=dev)
+        if (g, im) not in classes:
+            ctx = bos.Context(0)
+            ctx.set_grid(sc.grid, T, bos.BOS_PREC_FP32_COMP)
+            ctx.set_geometry(sc.camera, sc.wall, sc.light, sc.integ, pattern=pattern)
+            steps = int(ctx.ray_steps().sum().item())
+            ctx.close()
+            classes[(g, im)] = (sc, steps)
+        r["scene"], r["steps"] = classes[(g, im)]
+        reqs.append(r)
+    torch.cuda.synchronize()
+
+    def req_of(r):
+        sc = r["scene"]
+        p = lambda k: r[k].data_ptr() if k in r else None
+        return bos.make_request(sc.grid, bos.BOS_PREC_FP32_COMP, r["T"].data_ptr(), sc.camera, sc.wall, sc.light,
+                                pattern.data_ptr(), sc.integ, p("I"), p("disp"), p("target"), p("loss"), p("dLdT"))
+
+    def run(rate):
+        srv = bos.Server(0, args.mem_limit_gb << 30, args.slots)
+        t0 = time.perf_counter()
+        gaps = np.random.default_rng(7).exponential(1.0 / rate, n) if rate else np.zeros(n)
+        due = t0 + np.cumsum(gaps) - gaps[0]
+        tickets = []
+        for r, d in zip(reqs, due):
+            while True:
+                w = d - time.perf_counter()
+                if w <= 0:
+                    break
+                time.sleep(min(w, 0.002))
+            tickets.append(srv.submit(req_of(r)))
+        for t in tickets:
+            st = srv.wait(t, 600.0)
+            if st != bos.BOS_OK:
+                raise RuntimeError(f"request {t} failed with status {st}")
+        infos = [srv.info(t) for t in tickets]
+        stats = srv.stats()
+        srv.close()
+        lat = np.array([(i["done_ns"] - i["submit_ns"]) * 1e-6 for i in infos])
+        span = (max(i["done_ns"] for i in infos) - min(i["submit_ns"] for i in infos)) * 1e-9
+        steps = sum(r["steps"] for r in reqs)
+        live = [sum(1 for j in infos if j["admit_ns"] <= i["admit_ns"] < j["done_ns"]) for i in infos]
+        return dict(req_per_s=n / span, ray_steps_per_s=steps / span, p50_ms=float(np.percentile(lat, 50)),
+                    p99_ms=float(np.percentile(lat, 99)), mean_concurrency=float(np.mean(live)),
+                    peak_arena_gb=stats["peak_used_bytes"] / 2 ** 30, makespan_s=span)
+
+    run(0)                                   # warm-up (module load, first launches)
+    sat = run(0)
+    at07 = run(0.7 * sat["req_per_s"])
+    at10 = run(1.0 * sat["req_per_s"])
+    print(json.dumps({
+        "metric": "serving p99 latency (ms), Poisson arrivals at 0.7x saturated throughput", "value": at07["p99_ms"],
+        "unit": "ms", "n_gpus": 1, "steps": n, "warmup": n, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded plume fields and speckle patterns)",
+        "config": {"workload": "serving", "requests": n, "slots": args.slots, "admission_limit_gb": args.mem_limit_gb,
+                   "mix": "fwd | fwd+adjoint x grids {64^3,128^2x96,256^2x192} x images {256^2,1024^2,2048^2}, 1 spp"},
+        "latency_ms": {"p50": at07["p50_ms"], "p99": at07["p99_ms"]},
+        "at_0.7x": at07, "at_1.0x": at10, "saturated": sat,
+    }))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "serving":
+        serving_arm(args)
     else:
         gpu_arm(args)
 

@@ -213,6 +213,74 @@ const char* bos_last_error(void);
 /* Bytes of device memory the context currently owns. */
 uint64_t bos_device_bytes(bos_ctx* ctx);
 
+/* ------------------------------------------------------------------ request server
+ *
+ * Continuous batching of renders on one GPU.  A request is one frame: a temperature
+ * field on the device plus geometry; it is a forward render, or with target_dev set a
+ * forward + adjoint render (L_BOS against target_dev, then dL/dT).  Requests queue in
+ * arrival order; the server admits the head when one of its slots is free and the
+ * request's exact device footprint (bos_request_footprint) fits in the unused part of
+ * the server's arena, one allocation of mem_limit_bytes made at creation.  Each admitted
+ * request runs on its slot's own stream, so the work of all admitted requests overlaps
+ * on the device; requests arriving meanwhile are admitted as slots and memory free up.
+ * All device buffers named in a request are caller-owned and must stay valid until the
+ * request is done.  The server never blocks without a bound: bos_wait and
+ * bos_server_destroy take timeouts and return BOS_ERR_TIMEOUT. */
+
+typedef struct bos_server bos_server;
+
+typedef struct {
+    bos_grid_desc grid;
+    const float* T_dev;            /* nz*ny*nx float32 */
+    bos_camera_desc cam;
+    bos_wall_desc wall;
+    bos_light_desc light;
+    const float* pattern_dev;      /* th*tw float32 */
+    bos_integrator_desc integ;
+    float* I_dev;                  /* out: height*width float32 */
+    float* disp_dev;               /* out, nullable: height*width*2 float32 */
+    const float* target_dev;       /* nullable: height*width float32; set -> forward + adjoint */
+    double* loss_dev;              /* out with target: 1 float64 */
+    float* dLdT_dev;               /* out with target: nz*ny*nx float32 */
+} bos_request;
+
+typedef struct {
+    uint64_t submit_ns, admit_ns, done_ns;   /* host steady-clock times (0 = not yet) */
+    uint64_t footprint_bytes;
+    int status;                              /* the request's bos_status_t once done */
+    int done;
+    int slot;
+} bos_ticket_info;
+
+/* Run the scheduler without touching a GPU: admitted requests "run" for a time
+ * proportional to their footprint.  For tests of admission and queueing. */
+#define BOS_SERVER_FAKE_EXECUTOR 1
+
+/* Device bytes the server reserves for this request while it runs. */
+bos_status_t bos_request_footprint(const bos_request* req, uint64_t* bytes);
+
+/* Create a server on `device` with an arena of mem_limit_bytes and `slots` concurrent
+ * requests (1..64).  BOS_ERR_OOM if the arena cannot be allocated. */
+bos_status_t bos_server_create(bos_server** out, int device, uint64_t mem_limit_bytes, int slots, int flags);
+
+/* Queue a request (descriptors are copied).  BOS_ERR_ADMISSION if its footprint exceeds
+ * the arena, BOS_ERR_INVALID_ARG for a malformed request. */
+bos_status_t bos_submit(bos_server* s, const bos_request* req, uint64_t* ticket);
+
+/* Wait up to timeout_ns for a request; returns its status, or BOS_ERR_TIMEOUT. */
+bos_status_t bos_wait(bos_server* s, uint64_t ticket, uint64_t timeout_ns);
+
+/* Times, footprint and status of a request. */
+bos_status_t bos_ticket(bos_server* s, uint64_t ticket, bos_ticket_info* info);
+
+/* Arena size, peak arena use, queued and running requests. */
+bos_status_t bos_server_stats(bos_server* s, uint64_t* arena_bytes, uint64_t* peak_used_bytes, int* queued,
+                              int* running);
+
+/* Stop accepting requests, wait up to timeout_ns for queued and running ones, then free
+ * everything.  BOS_ERR_TIMEOUT leaves the server running (call again). */
+bos_status_t bos_server_destroy(bos_server* s, uint64_t timeout_ns);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,20 @@ class bos_integrator_desc(C.Structure):
                 ("ckpt_every", C.c_int)]
 
 
+class bos_request(C.Structure):
+    _fields_ = [("grid", bos_grid_desc), ("T_dev", C.c_void_p), ("cam", bos_camera_desc), ("wall", bos_wall_desc),
+                ("light", bos_light_desc), ("pattern_dev", C.c_void_p), ("integ", bos_integrator_desc),
+                ("I_dev", C.c_void_p), ("disp_dev", C.c_void_p), ("target_dev", C.c_void_p),
+                ("loss_dev", C.c_void_p), ("dLdT_dev", C.c_void_p)]
+
+
+class bos_ticket_info(C.Structure):
+    _fields_ = [("submit_ns", C.c_uint64), ("admit_ns", C.c_uint64), ("done_ns", C.c_uint64),
+                ("footprint_bytes", C.c_uint64), ("status", C.c_int), ("done", C.c_int), ("slot", C.c_int)]
+
+
+BOS_SERVER_FAKE_EXECUTOR = 1
+
 # every exported symbol of include/bos.h: name -> (restype, argtypes)
 _v, _i, _u64, _i64, _d = C.c_void_p, C.c_int, C.c_uint64, C.c_int64, C.c_double
 _P = C.POINTER
@@ -87,6 +101,13 @@ SIGNATURES = {
     "bos_error_string": (C.c_char_p, [_i]),
     "bos_last_error": (C.c_char_p, []),
     "bos_device_bytes": (_u64, [_v]),
+    "bos_request_footprint": (_i, [_P(bos_request), _P(_u64)]),
+    "bos_server_create": (_i, [_P(_v), _i, _u64, _i, _i]),
+    "bos_submit": (_i, [_v, _P(bos_request), _P(_u64)]),
+    "bos_wait": (_i, [_v, _u64, _u64]),
+    "bos_ticket": (_i, [_v, _u64, _P(bos_ticket_info)]),
+    "bos_server_stats": (_i, [_v, _P(_u64), _P(_u64), _P(_i), _P(_i)]),
+    "bos_server_destroy": (_i, [_v, _u64]),
 }
 
 _lib = None
@@ -345,3 +366,63 @@ def loss_l2(I, target, stream=None):
     g = torch.empty_like(I)
     bos_loss_l2(I.data_ptr(), target.data_ptr(), I.numel(), loss.data_ptr(), g.data_ptr(), _stream(stream))
     return loss, g
+
+
+# ------------------------------------------------------------------ request server
+
+def make_request(grid, prec, T_dev, camera, wall, light, pattern_dev, integ, I_dev, disp_dev=None,
+                 target_dev=None, loss_dev=None, dLdT_dev=None) -> bos_request:
+    """A bos_request from scene descriptors and device pointers (ints or None)."""
+    return bos_request(grid_desc(grid, prec), T_dev, camera_desc(camera), wall_desc(wall), light_desc(light),
+                       pattern_dev, integ_desc(integ), I_dev, disp_dev, target_dev, loss_dev, dLdT_dev)
+
+
+def bos_request_footprint(req: bos_request) -> int:
+    v = C.c_uint64()
+    check(lib().bos_request_footprint(C.byref(req), C.byref(v)), "bos_request_footprint")
+    return v.value
+
+
+class Server:
+    """Continuous-batching request server (include/bos.h, request server section)."""
+
+    def __init__(self, device: int = 0, mem_limit_bytes: int = 120 << 30, slots: int = 4, fake: bool = False):
+        h = C.c_void_p()
+        flags = BOS_SERVER_FAKE_EXECUTOR if fake else 0
+        check(lib().bos_server_create(C.byref(h), device, mem_limit_bytes, slots, flags), "bos_server_create")
+        self.h = h.value
+        self.keep = {}          # ticket -> objects the request points into
+
+    def submit(self, req: bos_request, keep=None) -> int:
+        t = C.c_uint64()
+        check(lib().bos_submit(self.h, C.byref(req), C.byref(t)), "bos_submit")
+        if keep is not None:
+            self.keep[t.value] = keep
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> int:
+        """Status of the request (BOS_ERR_TIMEOUT if not done within the timeout)."""
+        return int(lib().bos_wait(self.h, ticket, int(timeout_s * 1e9)))
+
+    def info(self, ticket: int) -> dict:
+        i = bos_ticket_info()
+        check(lib().bos_ticket(self.h, ticket, C.byref(i)), "bos_ticket")
+        return {f: getattr(i, f) for f, _ in bos_ticket_info._fields_}
+
+    def stats(self) -> dict:
+        a, p = C.c_uint64(), C.c_uint64()
+        q, r = C.c_int(), C.c_int()
+        check(lib().bos_server_stats(self.h, C.byref(a), C.byref(p), C.byref(q), C.byref(r)), "bos_server_stats")
+        return dict(arena_bytes=a.value, peak_used_bytes=p.value, queued=q.value, running=r.value)
+
+    def close(self, timeout_s: float = 600.0) -> None:
+        if self.h:
+            check(lib().bos_server_destroy(self.h, int(timeout_s * 1e9)), "bos_server_destroy")
+            self.h = None
+            self.keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

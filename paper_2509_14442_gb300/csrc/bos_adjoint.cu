@@ -21,8 +21,11 @@
 namespace bos {
 
 constexpr int kAdjWarps = 2;          // warps per block
+#ifndef BOS_ADJ_MIN_BLOCKS
+#define BOS_ADJ_MIN_BLOCKS 6              // resident blocks per SM the register budget is cut for
+#endif
 constexpr int kRow = 36;              // floats per lane row of the cell accumulators (16-byte aligned rows)
-constexpr int kStageRec = 22;         // floats kept per stage: value + 3 derivatives (16), cell (3), fractions (3)
+constexpr int kStageStride = 28;      // floats per lane row of a parked stage (value + 3 derivatives, cell, fractions)
 constexpr uint32_t kNoKey = 0xffffffffu;
 
 struct InterpGrad {
@@ -77,7 +80,40 @@ __device__ __forceinline__ void stage_eval(const CompField<E>& F, const long lon
     s.ig = trilinear_grad2(F.store, o, s.cf[0], s.cf[1], s.cf[2]);
 }
 
-// Park / restore a stage record in the warp's shared buffer ([kStageRec][32] per slot).
+#ifndef BOS_ADJ_STAGE_F4
+#define BOS_ADJ_STAGE_F4 1                // parked stage records as float4 rows (1) or scalar columns (0)
+#endif
+
+#if BOS_ADJ_STAGE_F4
+// Park / restore a stage record in the warp's shared buffer: one row of kStageStride
+// floats per lane, accessed as float4 (the stride keeps 8 consecutive lanes on distinct
+// banks, so the 128-bit accesses are conflict-free).
+__device__ __forceinline__ void put_stage(float* b, int lane, const Stage& s) {
+    float4* row = reinterpret_cast<float4*>(b + lane * kStageStride);
+    row[0] = s.ig.v;
+    row[1] = s.ig.d0;
+    row[2] = s.ig.d1;
+    row[3] = s.ig.d2;
+    row[4] = make_float4(__int_as_float(s.ci[0]), __int_as_float(s.ci[1]), __int_as_float(s.ci[2]), s.cf[0]);
+    row[5] = make_float4(s.cf[1], s.cf[2], 0.0f, 0.0f);
+}
+__device__ __forceinline__ void get_stage(const float* b, int lane, Stage& s) {
+    const float4* row = reinterpret_cast<const float4*>(b + lane * kStageStride);
+    s.ig.v = row[0];
+    s.ig.d0 = row[1];
+    s.ig.d1 = row[2];
+    s.ig.d2 = row[3];
+    const float4 a = row[4], c = row[5];
+    s.ci[0] = __float_as_int(a.x);
+    s.ci[1] = __float_as_int(a.y);
+    s.ci[2] = __float_as_int(a.z);
+    s.cf[0] = a.w;
+    s.cf[1] = c.x;
+    s.cf[2] = c.y;
+}
+#else
+// Park / restore a stage record in the warp's shared buffer: column `lane` of a
+// [22][32] block (conflict-free scalar accesses).
 __device__ __forceinline__ void put_stage(float* b, int lane, const Stage& s) {
     const float* v = reinterpret_cast<const float*>(&s.ig);
 #pragma unroll
@@ -98,6 +134,7 @@ __device__ __forceinline__ void get_stage(const float* b, int lane, Stage& s) {
         s.cf[a] = b[(19 + a) * 32 + lane];
     }
 }
+#endif
 
 // Adjoint of D = (1 + deta) grad at a stage point: given Db, the position adjoint (metres)
 // and the per-corner record Q (corner c receives w_c Q).
@@ -213,22 +250,17 @@ __device__ __forceinline__ void wall_adjoint(const SceneDev& S, const double rN[
 }
 
 __host__ __device__ constexpr size_t adj_warp_floats(int K) {
-    return (size_t)K * 6 * 32 + 32 * kRow + 2 * kStageRec * 32;
+    return (size_t)K * 6 * 32 + 32 * kRow + 2 * 32 * kStageStride;
 }
 
 template <class E>
-__global__ void __launch_bounds__(kAdjWarps * 32, 5) adjoint_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
+__global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
     extern __shared__ float4 smem4[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int K = ck.every;
     float* st_buf = reinterpret_cast<float*>(smem4) + (size_t)warp * adj_warp_floats(K);   // [K][6][32]
     float* rows = st_buf + (size_t)K * 6 * 32;                                             // [32][kRow]
-    float* stg = rows + 32 * kRow;                                                          // [2][kStageRec][32]
-    {
-        float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
-        for (int c = 0; c < 8; ++c) row[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    }
-    __syncwarp();
+    float* stg = rows + 32 * kRow;                                                          // [2][32][kStageStride]
     const CompField<E> F = {static_cast<const E*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
                             {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
     const int nx = S.g.n[0], nxy = S.g.n[0] * S.g.n[1];
@@ -236,6 +268,11 @@ __global__ void __launch_bounds__(kAdjWarps * 32, 5) adjoint_kernel(SceneDev S, 
     const TileShape ts = tile_shape(W, H, spp);
     const int ntiles = ts.tiles_x * ts.tiles_y;
     float* acc = reinterpret_cast<float*>(adj.acc);
+    {
+        float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
+        for (int c = 0; c < 8; ++c) row[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    __syncwarp();
     CellAcc ca = {kNoKey};
 
     for (;;) {
@@ -338,7 +375,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, 5) adjoint_kernel(SceneDev S, 
                         for (int a = 0; a < 3; ++a) q[a] = dr[a] + (0.5f * dt) * dvv[a] + (0.125f * dt) * A[a];
                         stage_eval(F, U2, q, bc, s);
                         rhs_from(s.ig, D2);
-                        put_stage(stg + kStageRec * 32, lane, s);
+                        put_stage(stg + 32 * kStageStride, lane, s);
                         for (int a = 0; a < 3; ++a) B[a] = dt * D2[a];
                         for (int a = 0; a < 3; ++a) q[a] = dr[a] + dt * dvv[a] + (0.5f * dt) * B[a];
                         stage_eval(F, U3, q, bc, s3);
@@ -386,7 +423,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, 5) adjoint_kernel(SceneDev S, 
                     }
                     Stage s2;
                     if (a_) {
-                        get_stage(stg + kStageRec * 32, lane, s2);
+                        get_stage(stg + 32 * kStageStride, lane, s2);
                         rhs_adjoint(F, s2.ig, Db, pb, Q);
                     }
                     accumulate(rows, a_, s2.ci, s2.cf, Q, ca, acc, nx, nxy);

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "../../include/bos.h"
+#include "bos_ctx_internal.h"
 #include "bos_internal.h"
 
 using namespace bos;
@@ -121,12 +122,27 @@ struct bos_ctx {
 
     float4* acc = nullptr;
     size_t acc_bytes = 0;
+
+    // Optional caller-provided device arena: when set, buffers are carved from it and
+    // nothing is allocated or freed (used by the request server).
+    char* arena = nullptr;
+    size_t arena_size = 0, arena_used = 0;
 };
 
 namespace {
 
 bos_status_t dev_alloc(bos_ctx* c, void** p, size_t* have, size_t want, const char* what) {
     if (*have >= want && *p) return BOS_OK;
+    if (c->arena) {
+        size_t need = bos::align_up(want);
+        if (c->arena_used + need > c->arena_size)
+            return fail(BOS_ERR_OOM, "%s: %zu bytes do not fit the request's arena (%zu of %zu used)", what, want,
+                        c->arena_used, c->arena_size);
+        *p = c->arena + c->arena_used;
+        c->arena_used += need;
+        *have = want;
+        return BOS_OK;
+    }
     if (c->mem_limit && c->bytes - *have + want > c->mem_limit)
         return fail(BOS_ERR_OOM, "%s: %zu bytes would exceed the context limit of %llu bytes", what, want,
                     (unsigned long long)c->mem_limit);
@@ -180,6 +196,58 @@ int step_bound(const bos_ctx* c) {
 }
 
 }  // namespace
+
+namespace bos {
+
+// Bind a context to a device arena (nullptr: back to its own allocations).  Drops the
+// context's grid, geometry and saved render.
+void ctx_bind_arena(bos_ctx* c, void* base, size_t bytes, cudaStream_t stream) {
+    if (!c->arena) {
+        void* bufs[] = {c->store, c->ckpt, c->excess, c->acc};
+        for (void* p : bufs)
+            if (p) cudaFree(p);
+        c->bytes = 256;
+    }
+    c->store = nullptr;
+    c->ckpt = nullptr;
+    c->excess = nullptr;
+    c->acc = nullptr;
+    c->store_bytes = c->ckpt_bytes = c->excess_bytes = c->acc_bytes = 0;
+    c->arena = (char*)base;
+    c->arena_size = bytes;
+    c->arena_used = 0;
+    c->has_grid = c->has_geom = c->saved = false;
+    if (c->small) cudaMemsetAsync(c->small, 0, 256, stream);
+}
+
+// Device bytes a render (and, with adjoint != 0, its backward) needs, as carved from an
+// arena: the same sizes render_impl / bos_set_grid / bos_backward allocate.
+size_t request_bytes(const bos_grid_desc& g, const bos_camera_desc& cam, const bos_integrator_desc& it, int adjoint) {
+    uint32_t nb[3] = {(uint32_t)(g.nx - 1 + kBrick - 1) / kBrick, (uint32_t)(g.ny - 1 + kBrick - 1) / kBrick,
+                      (uint32_t)(g.nz - 1 + kBrick - 1) / kBrick};
+    size_t slots = (size_t)morton3(nb[0] - 1, nb[1] - 1, nb[2] - 1) + 1;
+    size_t bytes = align_up(slots * kBrickCells * elem_bytes(g.prec));
+    if (adjoint) {
+        TileShape ts = tile_shape(cam.width, cam.height, cam.spp);
+        size_t nslots = (size_t)ts.tiles_x * ts.tiles_y * 32 * ts.samples_per_lane;
+        int bound;
+        if (it.fixed_steps > 0) {
+            bound = it.fixed_steps;
+        } else {
+            double h[3] = {g.extent[0] / g.nx, g.extent[1] / g.ny, g.extent[2] / g.nz};
+            double hmin = fmin(h[0], fmin(h[1], h[2]));
+            double b = ceil(norm3(g.extent) / (it.max_step_vox * hmin)) + 2.0;
+            bound = b > 2e9 ? 2000000000 : (int)b;
+        }
+        size_t max_ckpt = (size_t)((bound + it.ckpt_every - 1) / it.ckpt_every);
+        bytes += align_up(max_ckpt * 3 * nslots * sizeof(float4));
+        bytes += align_up(nslots * sizeof(float));
+        bytes += align_up((size_t)g.nx * g.ny * g.nz * sizeof(float4));
+    }
+    return bytes;
+}
+
+}  // namespace bos
 
 extern "C" {
 
@@ -238,9 +306,12 @@ bos_status_t bos_create(bos_ctx** out, int device, uint64_t mem_limit_bytes) {
 bos_status_t bos_destroy(bos_ctx* c) {
     if (!c) return BOS_OK;
     DeviceGuard dg(c->device);
-    void* bufs[] = {c->store, c->small, c->ckpt, c->excess, c->acc};
-    for (void* p : bufs)
-        if (p) cudaFree(p);
+    if (c->small) cudaFree(c->small);
+    if (!c->arena) {
+        void* bufs[] = {c->store, c->ckpt, c->excess, c->acc};
+        for (void* p : bufs)
+            if (p) cudaFree(p);
+    }
     delete c;
     return BOS_OK;
 }

@@ -168,14 +168,79 @@ __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const 
     comp_setup(S, F, R, st, k, eta_in, rin);
     BrickCache bc = {0xffffffffu, 0u};
     const int K = ck.every;
-    for (int n = 0; n < R.N; ++n) {
-        if (ck.state != nullptr && n % K == 0) {
-            size_t c = (size_t)(n / K);
-            ck.state[(c * 3 + 0) * ck.nrays + ray] = make_float4(st.dr[0], st.dr[1], st.dr[2], st.cr[0]);
-            ck.state[(c * 3 + 1) * ck.nrays + ray] = make_float4(st.dv[0], st.dv[1], st.dv[2], st.cr[1]);
-            ck.state[(c * 3 + 2) * ck.nrays + ray] = make_float4(st.cv[0], st.cv[1], st.cv[2], st.cr[2]);
+#ifndef BOS_FWD_PIPELINE
+#define BOS_FWD_PIPELINE 1
+#endif
+    if (INTEG == 0 && BOS_FWD_PIPELINE) {
+        // Sharma steps, software-pipelined: the next step's first stage needs only the new
+        // position r' = r + dt (v + (A + 2B)/6), not C, so it is evaluated together with this
+        // step's third stage.  Same operations as comp_step, in a different order in time.
+        BrickCache bc1 = {0xffffffffu, 0u};
+        int ci[3];
+        float cf[3], A[3], D[3];
+        rhs_of(comp_eval(F, st.U, st.dr, bc1, ci, cf), D);
+        const float dt = k.dt;
+        for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
+        for (int n = 0; n < R.N; ++n) {
+            if (ck.state != nullptr && n % K == 0) {
+                size_t c = (size_t)(n / K);
+                ck.state[(c * 3 + 0) * ck.nrays + ray] = make_float4(st.dr[0], st.dr[1], st.dr[2], st.cr[0]);
+                ck.state[(c * 3 + 1) * ck.nrays + ray] = make_float4(st.dv[0], st.dv[1], st.dv[2], st.cr[1]);
+                ck.state[(c * 3 + 2) * ck.nrays + ray] = make_float4(st.cv[0], st.cv[1], st.cv[2], st.cr[2]);
+            }
+            float B[3], C[3], q[3], inc_r[3], inc_v[3];
+            long long U2[3], U3[3];
+            for (int a = 0; a < 3; ++a) {
+                q[a] = st.dr[a] + (0.5f * dt) * st.dv[a] + (0.125f * dt) * A[a];
+                U2[a] = st.U[a] + k.dUh[a];
+                U3[a] = st.U[a] + k.dU[a];
+            }
+            rhs_of(comp_eval(F, U2, q, bc, ci, cf), D);
+            for (int a = 0; a < 3; ++a) B[a] = dt * D[a];
+            for (int a = 0; a < 3; ++a) {
+                q[a] = st.dr[a] + dt * st.dv[a] + (0.5f * dt) * B[a];
+                inc_r[a] = dt * (st.dv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
+            }
+            float dr1[3], cr1[3];
+            for (int a = 0; a < 3; ++a) {
+                dr1[a] = st.dr[a];
+                cr1[a] = st.cr[a];
+                kahan_add(dr1[a], cr1[a], inc_r[a]);
+            }
+            // independent: stage 3 of this step and stage 1 of the next
+            float D1[3] = {0.0f, 0.0f, 0.0f};
+            rhs_of(comp_eval(F, U3, q, bc, ci, cf), D);
+            if (n + 1 < R.N) {
+                int ci1[3];
+                float cf1[3];
+                rhs_of(comp_eval(F, U3, dr1, bc1, ci1, cf1), D1);
+            }
+            for (int a = 0; a < 3; ++a) {
+                C[a] = dt * D[a];
+                inc_v[a] = (A[a] + 4.0f * B[a] + C[a]) * (1.0f / 6.0f);
+            }
+            float si = k.dS[0] * inc_r[0] + k.dS[1] * inc_r[1] + k.dS[2] * inc_r[2];
+            float ii = inc_r[0] * inc_r[0] + inc_r[1] * inc_r[1] + inc_r[2] * inc_r[2];
+            float di = k.dhat[0] * inc_r[0] + k.dhat[1] * inc_r[1] + k.dhat[2] * inc_r[2];
+            st.excess += (2.0f * si + ii) / (2.0f * k.step_len + di);
+            for (int a = 0; a < 3; ++a) {
+                st.dr[a] = dr1[a];
+                st.cr[a] = cr1[a];
+                kahan_add(st.dv[a], st.cv[a], inc_v[a]);
+                st.U[a] = U3[a];
+                A[a] = dt * D1[a];
+            }
         }
-        comp_step<E, INTEG>(F, st, k, bc);
+    } else {
+        for (int n = 0; n < R.N; ++n) {
+            if (ck.state != nullptr && n % K == 0) {
+                size_t c = (size_t)(n / K);
+                ck.state[(c * 3 + 0) * ck.nrays + ray] = make_float4(st.dr[0], st.dr[1], st.dr[2], st.cr[0]);
+                ck.state[(c * 3 + 1) * ck.nrays + ray] = make_float4(st.dv[0], st.dv[1], st.dv[2], st.cr[1]);
+                ck.state[(c * 3 + 2) * ck.nrays + ray] = make_float4(st.cv[0], st.cv[1], st.cv[2], st.cr[2]);
+            }
+            comp_step<E, INTEG>(F, st, k, bc);
+        }
     }
     if (ck.state != nullptr) ck.excess[ray] = st.excess;
     float dr[3], dv[3];

@@ -8,6 +8,9 @@
 
 namespace bos {
 
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
+
 struct RenderOut {
     float* I;
     float* disp;

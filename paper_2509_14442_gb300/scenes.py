@@ -168,14 +168,15 @@ def plume_params(seed: int) -> dict:
 
 
 def plume_field(grid: Grid, seed: int, t_inlet: float = 310.0, radius: float = 0.2,
-                noise_amp: float = 0.3, ambient: float = T_AMBIENT) -> np.ndarray:
+                noise_amp: float = 0.3, ambient: float = T_AMBIENT, device=None):
     """Buoyant plume from the side-wall inlet plus multi-octave sinusoidal noise.
 
     T = ambient + (t_inlet - ambient) * exp(-d^2 / (2 radius^2)) * exp(-s / lam) + noise,
     with d the distance to a seeded curved centreline (a quadratic Bezier that
     leaves the inlet along +x and bends upward), s the arc length of the closest
     centreline point and noise = sum_o a_o sin(2 pi 2^o (u_o . x) / 1 m + phi_o),
-    sum_o a_o = noise_amp.  Returns (nz, ny, nx) float32.
+    sum_o a_o = noise_amp.  Returns (nz, ny, nx) float32: a numpy array, or with `device`
+    a torch tensor computed on that device.
     """
     prm = plume_params(seed)
     m = 96
@@ -189,24 +190,25 @@ def plume_field(grid: Grid, seed: int, t_inlet: float = 310.0, radius: float = 0
     nx, ny, nz = grid.n
     amp = t_inlet - ambient
     amps = [noise_amp * 2.0 ** (-o) / 1.875 for o in range(4)]
-    tp = torch.from_numpy(pts)
-    tseg = torch.from_numpy(seg)
-    tlen = torch.from_numpy(seg_len)
-    ts_at = torch.from_numpy(s_at)
+    dev = torch.device("cpu") if device is None else torch.device(device)
+    tp = torch.from_numpy(pts).to(dev)
+    tseg = torch.from_numpy(seg).to(dev)
+    tlen = torch.from_numpy(seg_len).to(dev)
+    ts_at = torch.from_numpy(s_at).to(dev)
     pp = (tp ** 2).sum(1)
-    X = torch.from_numpy(xc)
-    Y = torch.from_numpy(yc)
-    out = np.empty((nz, ny, nx), dtype=np.float32)
+    X = torch.from_numpy(xc).to(dev)
+    Y = torch.from_numpy(yc).to(dev)
+    out = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
     slabs = max(1, (1 << 20) // (nx * ny))
     for k0 in range(0, nz, slabs):
         k1 = min(nz, k0 + slabs)
-        Z = torch.from_numpy(zc[k0:k1])
+        Z = torch.from_numpy(zc[k0:k1]).to(dev)
         P = torch.stack(torch.meshgrid(X, Y, Z, indexing="xy"), -1)        # (ny, nx, nk, 3)
         P = P.permute(2, 0, 1, 3).reshape(-1, 3)                          # z, y, x order
         d2 = (P ** 2).sum(1, keepdim=True) - 2.0 * (P @ tp.T) + pp[None, :]
         i = torch.argmin(d2, dim=1)
-        best = torch.full((P.shape[0],), float("inf"), dtype=torch.float64)
-        best_s = torch.zeros(P.shape[0], dtype=torch.float64)
+        best = torch.full((P.shape[0],), float("inf"), dtype=torch.float64, device=dev)
+        best_s = torch.zeros(P.shape[0], dtype=torch.float64, device=dev)
         for off in (-1, 0):                                      # the two segments at point i
             j = torch.clamp(i + off, 0, m - 2)
             a = tp[j]
@@ -219,11 +221,10 @@ def plume_field(grid: Grid, seed: int, t_inlet: float = 310.0, radius: float = 0
             best_s = torch.where(take, ts_at[j] + t * tlen[j], best_s)
         val = amp * torch.exp(-best / (2.0 * radius * radius)) * torch.exp(-best_s / prm["lam"])
         for o, (uvec, phi) in enumerate(prm["octaves"]):
-            proj = P @ torch.tensor(uvec, dtype=torch.float64)
+            proj = P @ torch.tensor(uvec, dtype=torch.float64, device=dev)
             val = val + amps[o] * torch.sin(2.0 * math.pi * (2.0 ** o) * proj + phi)
-        out[k0:k1] = (ambient + val).reshape(k1 - k0, ny, nx).numpy().astype(np.float32)
-    T = out
-    return T
+        out[k0:k1] = (ambient + val).reshape(k1 - k0, ny, nx).to(torch.float32)
+    return out if device is not None else out.numpy()
 
 
 def linear_field_T(grid: Grid, grad_deta, deta0: float) -> np.ndarray:
@@ -315,12 +316,13 @@ def blob_cube(seed: int = BASE_SEED + 0, n: int = 32, width: int = 64, height: i
 
 def room(n=(128, 128, 96), width: int = 1024, height: int = 1024, spp: int = 4,
          seed: int = BASE_SEED + 1, pattern_size: int = 512, integrator: int = 0,
-         ckpt_every: int = 16, name: str = "room") -> Scene:
+         ckpt_every: int = 16, name: str = "room", field: bool = True) -> Scene:
     """Room-scale scene: plume field on an n-cell grid over the 4x4x3 m room, a projector
     casting a binary speckle on the back wall, a pinhole camera with `spp` tent-jittered
-    rays per pixel and adaptive steps of at most half the smallest cell."""
+    rays per pixel and adaptive steps of at most half the smallest cell.  field=False
+    leaves T empty (geometry only)."""
     grid = room_grid(n)
-    T = plume_field(grid, seed)
+    T = plume_field(grid, seed) if field else None
     dist = ROOM_ORIGIN[1] + ROOM_EXTENT[1] - CAMERA_POS[1]
     cam = _pinhole(CAMERA_POS, width, height, CAMERA_HALF_VIEW, dist, spp=spp, seed=seed * 7919 + 17)
     proj = _pinhole(PROJECTOR_POS, pattern_size, pattern_size, PROJECTOR_HALF_VIEW,

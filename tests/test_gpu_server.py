@@ -1,0 +1,98 @@
+"""The request server on the GPU: every request's result is the same alone and in the
+concurrent mix, and matches the oracle."""
+import numpy as np
+import pytest
+
+from paper_2509_14442_gb300 import scenes as S
+from helpers import DISP_REL_TOL, I_ABS_TOL, errors
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module")
+def bos():
+    from paper_2509_14442_gb300 import bos as B
+    B.lib()
+    return B
+
+
+SPECS = [  # grid, image, spp, adjoint
+    ((32, 32, 24), (64, 48), 1, False), ((48, 48, 36), (96, 80), 2, True), ((40, 40, 30), (80, 64), 4, False),
+    ((32, 32, 24), (128, 96), 1, True), ((64, 64, 48), (64, 64), 1, True), ((24, 24, 18), (50, 30), 3, False),
+    ((48, 48, 36), (96, 96), 1, False), ((32, 32, 24), (72, 56), 1, True), ((56, 56, 42), (100, 100), 2, False),
+    ((40, 40, 30), (64, 64), 1, True),
+]
+
+
+def make(bos, i, spec):
+    n, (w, h), spp, adj = spec
+    sc = S.room(n, w, h, spp, 4000 + i, pattern_size=128)
+    dev = "cuda"
+    d = dict(scene=sc, T=torch.as_tensor(sc.T, device=dev),
+             pattern=torch.as_tensor(sc.light.pattern, device=dev),
+             I=torch.zeros((h, w), device=dev), disp=torch.zeros((h, w, 2), device=dev))
+    if adj:
+        d["target"] = torch.full((h, w), 0.02, device=dev)      # a flat image as the measurement
+        d["loss"] = torch.zeros((1,), dtype=torch.float64, device=dev)
+        d["dLdT"] = torch.zeros_like(d["T"])
+    return d
+
+
+def alone(bos, d):
+    sc = d["scene"]
+    ctx = bos.Context(0)
+    ctx.set_grid(sc.grid, d["T"], bos.BOS_PREC_FP32_COMP)
+    ctx.set_geometry(sc.camera, sc.wall, sc.light, sc.integ, pattern=d["pattern"])
+    adj = "target" in d
+    I, D, _ = ctx.render(disp=True, save_for_backward=adj)
+    out = dict(I=I.clone(), disp=D.clone())
+    if adj:
+        loss, g = bos.loss_l2(I, d["target"])
+        out["loss"] = loss.clone()
+        out["dLdT"] = ctx.backward(g).clone()
+    torch.cuda.synchronize()
+    ctx.status()
+    ctx.close()
+    return out
+
+
+def submit(bos, srv, d):
+    sc = d["scene"]
+    p = lambda k: d[k].data_ptr() if k in d else None
+    req = bos.make_request(sc.grid, bos.BOS_PREC_FP32_COMP, d["T"].data_ptr(), sc.camera, sc.wall, sc.light,
+                           d["pattern"].data_ptr(), sc.integ, p("I"), p("disp"), p("target"), p("loss"), p("dLdT"))
+    return srv.submit(req, keep=d)
+
+
+def test_results_alone_equal_results_in_the_mix(bos):
+    reqs = [make(bos, i, s) for i, s in enumerate(SPECS)]
+    ref = [alone(bos, d) for d in reqs]
+    srv = bos.Server(0, 2 << 30, 4)
+    tickets = [submit(bos, srv, d) for d in reqs]
+    for t in tickets:
+        assert srv.wait(t, 120.0) == bos.BOS_OK
+    torch.cuda.synchronize()
+    infos = [srv.info(t) for t in tickets]
+    srv.close()
+    # several requests were on the device at once
+    assert max(sum(1 for j in infos if j["admit_ns"] <= i["admit_ns"] < j["done_ns"]) for i in infos) > 1
+    for d, r in zip(reqs, ref):
+        assert torch.equal(d["I"], r["I"])            # the forward is deterministic
+        assert torch.equal(d["disp"], r["disp"])
+        if "dLdT" in d:
+            # float32 atomics sum in a different order: same tolerance as the gradient parity
+            assert torch.linalg.norm(d["dLdT"] - r["dLdT"]) <= 1e-5 * torch.linalg.norm(r["dLdT"])
+            assert abs(d["loss"].item() - r["loss"].item()) <= 1e-12 * abs(r["loss"].item())
+
+
+def test_server_result_matches_oracle(bos, orc):
+    d = make(bos, 0, ((48, 48, 36), (96, 80), 2, False))
+    srv = bos.Server(0, 1 << 30, 2)
+    t = submit(bos, srv, d)
+    assert srv.wait(t, 60.0) == bos.BOS_OK
+    srv.close()
+    o = orc.render(d["scene"])
+    e = errors(dict(I=d["I"].cpu().numpy().astype(np.float64), disp=d["disp"].cpu().numpy().astype(np.float64)), o)
+    assert e["I_abs"] <= I_ABS_TOL and e["disp_rel"] <= DISP_REL_TOL, e
