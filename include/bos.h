@@ -201,6 +201,25 @@ bos_status_t bos_export_nodes(bos_ctx* ctx, void* out_dev, void* stream);
  * the tracer's gathers.  sink_dev (1 float) is written only to keep the loads alive. */
 bos_status_t bos_probe_read(const void* buf_dev, uint64_t bytes, int repeats, float* sink_dev, void* stream);
 
+/* Forward render that allocates nothing, for callers that must not call cudaMalloc
+ * (a latency-critical loop, where allocation and freeing can synchronise the device, or
+ * a host whose device memory is already handed out by another allocator).  No
+ * counterpart in the paper: it runs the same field build and render as bos_set_grid +
+ * bos_render (no displacement-free shortcut, no checkpoints), with the field store and
+ * the work counters in one file-scope device array of 64 MiB that the library reserves
+ * on every GPU it is loaded on, until the process exits.  The caller passes the inputs
+ * (T_dev, pattern_dev) and outputs (I_dev, disp_dev nullable) as in bos_render.
+ * Grids whose field store exceeds the array (64 MiB - 256 B; e.g. 128x128x96 cells
+ * fit in float32, 256x256x192 do not) are rejected with BOS_ERR_INVALID_ARG and a
+ * message in bos_last_error().  The first call on a device looks up the array's
+ * address with that device current; make that first call before any stream capture.
+ * Every call shares the array: calls whose work overlaps on the GPU race and must be
+ * serialised by the caller.  Each call clears the counters and rebuilds the store, so
+ * leftovers of the previous call do not matter.  Asynchronous on `stream`. */
+bos_status_t bos_render_noalloc(const bos_grid_desc* grid, const float* T_dev, const bos_camera_desc* cam,
+                                const bos_wall_desc* wall, const bos_light_desc* light, const float* pattern_dev,
+                                const bos_integrator_desc* integ, float* I_dev, float* disp_dev, void* stream);
+
 /* Sticky device-side status of the context (call after synchronising). */
 bos_status_t bos_status(bos_ctx* ctx);
 

@@ -97,6 +97,8 @@ SIGNATURES = {
     "bos_backward": (_i, [_v, _v, _v, _v]),
     "bos_export_nodes": (_i, [_v, _v, _v]),
     "bos_probe_read": (_i, [_v, _u64, _i, _v, _v]),
+    "bos_render_noalloc": (_i, [_P(bos_grid_desc), _v, _P(bos_camera_desc), _P(bos_wall_desc), _P(bos_light_desc),
+                                _v, _P(bos_integrator_desc), _v, _v, _v]),
     "bos_status": (_i, [_v]),
     "bos_error_string": (C.c_char_p, [_i]),
     "bos_last_error": (C.c_char_p, []),
@@ -235,6 +237,12 @@ def bos_export_nodes(ctx, out_dev, stream) -> None:
 
 def bos_probe_read(buf_dev, nbytes: int, repeats: int, sink_dev, stream) -> None:
     check(lib().bos_probe_read(buf_dev, nbytes, repeats, sink_dev, stream), "bos_probe_read")
+
+
+def bos_render_noalloc(grid: bos_grid_desc, T_dev, cam: bos_camera_desc, wall: bos_wall_desc,
+                       light: bos_light_desc, pattern_dev, integ: bos_integrator_desc, I_dev, disp_dev, stream) -> None:
+    check(lib().bos_render_noalloc(C.byref(grid), T_dev, C.byref(cam), C.byref(wall), C.byref(light), pattern_dev,
+                                   C.byref(integ), I_dev, disp_dev, stream), "bos_render_noalloc")
 
 
 def bos_status(ctx) -> None:

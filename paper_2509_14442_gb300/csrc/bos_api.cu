@@ -199,6 +199,8 @@ int step_bound(const bos_ctx* c) {
 
 namespace bos {
 
+void set_last_error(const char* msg) { g_last_error = msg; }
+
 // Bind a context to a device arena (nullptr: back to its own allocations).  Drops the
 // context's grid, geometry and saved render.
 void ctx_bind_arena(bos_ctx* c, void* base, size_t bytes, cudaStream_t stream) {
