@@ -35,20 +35,35 @@ sys.path.insert(0, ROOT)
 
 from paper_2509_14442_gb300 import scenes as S  # noqa: E402
 
+def quasi(scene):
+    return scene.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=2,
+                                            ckpt_every=scene.integ.ckpt_every))
+
+
 WORKLOADS = {
     "room_adj": dict(desc="room 256x256x192 plume, 2048^2 camera, 1 spp, forward + adjoint (K=16)",
                      make=lambda seed: S.room_adjoint(seed), adjoint=True),
     "room_fwd": dict(desc="room 128x128x96 plume, 1024^2 camera, 4 jittered spp, forward + I_ref",
                      make=lambda seed: S.room_forward(seed), adjoint=False),
+    # the paper's quasi-linear tracer (Sec. 2.2) on the same scenes
+    "room_adj_quasi": dict(desc="room 256x256x192 plume, 2048^2 camera, 1 spp, quasi-linear forward + adjoint",
+                           make=lambda seed: quasi(S.room_adjoint(seed)), adjoint=True, fwd_bytes=256, adj_bytes=512),
+    "room_fwd_quasi": dict(desc="room 128x128x96 plume, 1024^2 camera, 4 jittered spp, quasi-linear forward + I_ref",
+                           make=lambda seed: quasi(S.room_forward(seed)), adjoint=False, fwd_bytes=256),
     # small case of the same kernels for profiler captures (not a benchmark line)
     "room_fwd_small": dict(desc="room 128x128x96 plume, 256^2 camera, 4 jittered spp, forward + I_ref",
                            make=lambda seed: S.room((128, 128, 96), 256, 256, 4, seed), adjoint=False),
     "room_adj_small": dict(desc="room 256x256x192 plume, 512^2 camera, 1 spp, forward + adjoint (K=16)",
                            make=lambda seed: S.room((256, 256, 192), 512, 512, 1, seed), adjoint=True),
 }
-# Algorithmic bytes of one Sharma ray-step of the float32 store: 3 field evaluations x 8
-# trilinear corners x one 16-byte (deta, grad eta) record.
+# Algorithmic bytes of one Sharma ray-step of the forward tracer: 3 field evaluations x 8
+# trilinear corners x one (deta, grad eta) record (16 B in float32).
 BYTES_PER_STEP = {"fp32_comp": 384, "fp32": 384, "bf16_comp": 192, "fp64": 768}
+# Adjoint, per ray-step: the segment recompute gathers 384 B, the reverse step gathers the
+# same 3 x 8 records again, and scatters 3 x 8 corner sensitivities of 16 B.  (Quasi-linear
+# tracing samples 2 new points per step: 256 B forward; its one-sweep adjoint gathers and
+# scatters those 2 points: 512 B.)
+ADJ_BYTES_PER_STEP = {"fp32_comp": 3 * 384, "bf16_comp": 2 * 192 + 384}
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -57,12 +72,13 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--workload", default="room_fwd", choices=sorted(WORKLOADS) + ["serving"])
+    p.add_argument("--workload", default="room_adj", choices=sorted(WORKLOADS) + ["serving", "precision"])
     p.add_argument("--prec", default="fp32_comp", choices=sorted(BYTES_PER_STEP))
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--requests", type=int, default=256, help="serving: number of requests")
+    p.add_argument("--sample-pixels", type=int, default=4000, help="precision: oracle-checked pixels")
     p.add_argument("--slots", type=int, default=6, help="serving: concurrent requests")
     p.add_argument("--mem-limit-gb", type=int, default=120, help="serving: admission limit (GiB)")
     return p.parse_args()
@@ -81,22 +97,24 @@ def oracle_rate(scene, adjoint: bool, seconds: float, seed: int = 0):
     rng = np.random.default_rng(seed)
     npix = scene.pixels
 
-    def run(pix):
+    def run(pix, with_adjoint):
         t0 = time.perf_counter()
         out = O.render(scene, field=field, pix=pix, threads=threads, nsteps=True)
         steps = int(out["nsteps"].sum())
-        if adjoint:
+        if with_adjoint:
             w = np.zeros((scene.camera.height, scene.camera.width))
             w.reshape(-1)[pix] = 1.0
             O.grad(scene, w, threads=threads)
         return steps, time.perf_counter() - t0
 
-    probe = np.sort(rng.choice(npix, min(npix, 2000), replace=False))
-    s0, t0 = run(probe)
-    per_pix = t0 / len(probe)
-    m = int(min(npix, max(len(probe), seconds / max(per_pix, 1e-9))))
+    # size the sample from the forward render's per-pixel time (the oracle's gradient
+    # re-traces every ray with a tape and then reverses it: about three renders' work, plus
+    # a fixed per-call cost), so that the sample takes about `seconds`
+    m0 = min(npix, 4000)
+    per_pix = run(np.sort(rng.choice(npix, m0, replace=False)), False)[1] / m0
+    m = int(min(npix, max(m0, seconds / (per_pix * (4.0 if adjoint else 1.0)))))
     pix = np.sort(rng.choice(npix, m, replace=False))
-    steps, t = run(pix)
+    steps, t = run(pix, adjoint)
     kind = "forward + adjoint" if adjoint else "forward"
     return steps / t, threads, f"{m} of {npix} pixels ({kind}), {steps} ray-steps in {t:.1f} s"
 
@@ -215,6 +233,21 @@ def l2_read_peak(torch, dev, bos):
     return nbytes * reps / (best * 1e-3) / 1e9
 
 
+def aggregate(my_ms: float, units_per_rank: int, dist=None, device=None):
+    """Whole-job rate of a weak-scaling run: every rank processed `units_per_rank` units in
+    `my_ms` of device time; the job took the slowest rank's time.  Returns (job_ms, units/s)."""
+    job_ms = my_ms
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+
+        world = dist.get_world_size()
+        t = torch.tensor([my_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        job_ms = float(t.item())
+    return job_ms, units_per_rank * world / (job_ms * 1e-3)
+
+
 def gpu_arm(args):
     import torch
     import torch.distributed as dist
@@ -255,7 +288,7 @@ def gpu_arm(args):
     dLdI = torch.empty_like(I)
     dLdT = torch.empty_like(T)
     flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
-    ev_r = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev_r = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     launches_per_step = 0
 
     def step(T_in, ev=None):
@@ -274,7 +307,11 @@ def gpu_arm(args):
         if wl["adjoint"]:
             bos.check(L.bos_loss_l2(I.data_ptr(), target.data_ptr(), I.numel(), loss.data_ptr(), dLdI.data_ptr(),
                                     sp), "loss")
+            if ev is not None:
+                ev[2].record(stream)
             bos.check(L.bos_backward(ctx.h, dLdI.data_ptr(), dLdT.data_ptr(), sp), "backward")
+            if ev is not None:
+                ev[3].record(stream)
             launches_per_step = 5          # build_store, render, loss_l2, adjoint, gradient
         else:
             bos.check(L.bos_render_reference(ctx.h, Iref.data_ptr(), None, None, sp), "render_ref")
@@ -291,7 +328,7 @@ def gpu_arm(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
-    step_ms, render_ms = [], []
+    step_ms, render_ms, back_ms = [], [], []
     with clocks:
         for _ in range(args.steps):
             flush.fill_(0.0)
@@ -302,17 +339,13 @@ def gpu_arm(args):
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             render_ms.append(ev_r[0].elapsed_time(ev_r[1]))
+            if wl["adjoint"]:
+                back_ms.append(ev_r[2].elapsed_time(ev_r[3]))
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ctx.status()
-    my_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([my_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        my_ms = float(t.item())
-    total_ms = my_ms
-    value = steps_per_frame * world * args.steps / (total_ms * 1e-3)
+    total_ms, value = aggregate(sum(step_ms), steps_per_frame * args.steps, dist if world > 1 else None, dev)
 
     # ---- end to end through the C ABI with host buffers: H2D inputs, D2H result
     e2e_ms = []
@@ -345,14 +378,27 @@ def gpu_arm(args):
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     l2_peak = l2_read_peak(torch, dev, bos)
     render_avg_ms = statistics.mean(render_ms)
-    achieved = BYTES_PER_STEP[args.prec] * steps_per_frame / (render_avg_ms * 1e-3) / 1e9
-    roofline = {"bound": "l2", "kernel": "render_kernel (tracer)", "achieved": achieved, "peak": l2_peak,
-                "unit": "GB/s", "frac": achieved / l2_peak, "traffic": None,
+    fwd_b = wl.get("fwd_bytes", BYTES_PER_STEP[args.prec])
+    adj_b = wl.get("adj_bytes", ADJ_BYTES_PER_STEP.get(args.prec, 0))
+    fwd_gbs = fwd_b * steps_per_frame / (render_avg_ms * 1e-3) / 1e9
+    kernels = {"render_kernel": {"ms": render_avg_ms, "bytes_per_ray_step": fwd_b,
+                                 "achieved_gbs": fwd_gbs, "frac": fwd_gbs / l2_peak}}
+    dominant = "render_kernel"
+    if wl["adjoint"]:
+        back_avg_ms = statistics.mean(back_ms)
+        adj_gbs = adj_b * steps_per_frame / (back_avg_ms * 1e-3) / 1e9
+        kernels["adjoint_kernel"] = {"ms": back_avg_ms, "bytes_per_ray_step": adj_b,
+                                     "achieved_gbs": adj_gbs, "frac": adj_gbs / l2_peak,
+                                     "timed": "bos_backward: accumulator clear + adjoint_kernel + gradient_kernel"}
+        dominant = "adjoint_kernel"
+    dk = kernels[dominant]
+    roofline = {"bound": "l2", "kernel": dominant, "achieved": dk["achieved_gbs"], "peak": l2_peak, "unit": "GB/s",
+                "frac": dk["frac"], "traffic": None,
                 "peak_source": "in-run L2 read probe (bos_probe_read, 24 MiB x 50 passes, best of 10)",
-                "bytes_per_ray_step": BYTES_PER_STEP[args.prec],
-                "render_ms": render_avg_ms,
-                "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                "hbm_algorithmic_gbs": (scene.grid.cells * 16 * 1.42 + scene.pixels * 4) / (render_avg_ms * 1e-3) / 1e9}
+                "bytes_per_ray_step": dk["bytes_per_ray_step"],
+                "note": ("gather roofline R = L2 read bandwidth / algorithmic bytes per ray-step; the gathers "
+                         "hit L1 (ncu: ~95 % forward, ~80 % adjoint), so a kernel can exceed R"),
+                "kernels": kernels, "hbm_peak_gbs": peaks.get("hbm_gbs")}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         r, threads, desc = oracle_rate(scene, wl["adjoint"], args.cpu_seconds)
@@ -471,12 +517,81 @@ def serving_arm(args):
     }))
 
 
+# ------------------------------------------------------------------ precision variants
+
+def bf16_round(x):
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.round(m * 256.0), e - 8)
+
+
+def precision_arm(args):
+    """The 256x256x192 / 2048^2 scene rendered by every precision: render time and, on a
+    seeded sample of pixels, displacement and intensity errors against the FP64 oracle
+    (and for BF16 also against the oracle run on the BF16-dequantised field)."""
+    import torch
+
+    from oracle import oracle as O
+    from paper_2509_14442_gb300 import bos
+
+    O.build()
+    dev = torch.device("cuda", 0)
+    scene = S.room_adjoint(S.BASE_SEED + 2)
+    T = torch.as_tensor(scene.T, device=dev)
+    pix = np.sort(np.random.default_rng(4).choice(scene.pixels, args.sample_pixels, replace=False))
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    orc = O.render(scene, pix=pix, threads=threads)
+    de = O.deta_from_T(scene.grid, scene.T.astype(np.float64))
+    gr = O.grad_from_deta(scene.grid, de)
+    orc_bf16 = O.render(scene, field=O.NodeField(bf16_round(de), bf16_round(gr)), pix=pix, threads=threads)
+    t_orc = time.perf_counter() - t0
+    dmax = float(np.abs(orc["disp"]).max())
+
+    def err(I, D, ref):
+        return {"disp_rel": float(np.abs(D.reshape(-1, 2)[pix] - ref["disp"]).max()) / dmax,
+                "I_abs": float(np.abs(I.reshape(-1)[pix] - ref["I"]).max())}
+
+    out = {}
+    for name in ("fp64", "fp32", "fp32_comp", "bf16_comp"):
+        ctx = bos.Context(0)
+        ctx.set_scene(scene, bos.PRECISIONS[name], T=T)
+        reps = 1 if name == "fp64" else 5
+        ms = []
+        for i in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            I, D, _ = ctx.render(disp=True)
+            e1.record()
+            e1.synchronize()
+            if i:
+                ms.append(e0.elapsed_time(e1))
+        ctx.status()
+        steps = ctx.last_ray_steps()
+        Ih, Dh = I.cpu().numpy().astype(np.float64), D.cpu().numpy().astype(np.float64)
+        r = {"render_ms": statistics.mean(ms), "ray_steps_per_s": steps / (statistics.mean(ms) * 1e-3),
+             "vs_fp64_oracle": err(Ih, Dh, orc)}
+        if name == "bf16_comp":
+            r["vs_oracle_on_bf16_field"] = err(Ih, Dh, orc_bf16)
+        out[name] = r
+        ctx.close()
+    print(json.dumps({
+        "metric": "ray-steps/s and errors per precision (forward render)", "value": out["fp32_comp"]["ray_steps_per_s"],
+        "unit": "ray-steps/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic (seeded plume fields and speckle patterns)",
+        "config": {"workload": "precision", "grid": list(scene.grid.n), "image": [scene.camera.width,
+                   scene.camera.height], "spp": scene.camera.spp, "sample_pixels": args.sample_pixels,
+                   "max_displacement_m": dmax, "oracle_seconds": t_orc, "oracle_threads": threads},
+        "precisions": out}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
     elif args.workload == "serving":
         serving_arm(args)
+    elif args.workload == "precision":
+        precision_arm(args)
     else:
         gpu_arm(args)
 

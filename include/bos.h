@@ -164,6 +164,16 @@ bos_status_t bos_set_geometry(bos_ctx* ctx, const bos_camera_desc* cam, const bo
 bos_status_t bos_render(bos_ctx* ctx, float* I_dev, float* disp_dev, double* hit_dev, int save_for_backward,
                         void* stream);
 
+/* Steps a2-a5 for a subset of the pixels (the paper's reconstruction draws 5000 random
+ * pixels of the BOS image per iteration, Sec. 3.2): pix_dev holds npix flat pixel indices
+ * y*width + x (any order, repeats allowed; indices outside the image are skipped and
+ * flagged in bos_status).  I_dev receives npix float32 values and disp_dev (nullable)
+ * npix*2, entry k belonging to pix_dev[k].  With save_for_backward, the next
+ * bos_backward takes dL/dI as npix values in the same order; pix_dev must stay valid
+ * until then. */
+bos_status_t bos_render_pixels(bos_ctx* ctx, const int32_t* pix_dev, int64_t npix, float* I_dev, float* disp_dev,
+                               int save_for_backward, void* stream);
+
 /* The reference image I_ref (Sec. 2.1: no flow): the same rays, straight, with
  * the ambient index.  Same outputs as bos_render. */
 bos_status_t bos_render_reference(bos_ctx* ctx, float* I_dev, float* disp_dev, double* hit_dev, void* stream);
@@ -181,8 +191,29 @@ bos_status_t bos_last_ray_steps(bos_ctx* ctx, uint64_t* out);
 bos_status_t bos_loss_l2(const float* I_dev, const float* target_dev, int64_t n, double* loss_dev,
                          float* dLdI_dev, void* stream);
 
-/* Step a6 (Sec. 2.4): given dL/dI (height*width float32) for the most recent
- * bos_render(save_for_backward=1), write dL/dT (nz*ny*nx float32).  Needs the
+/* L_BOS over a pixel minibatch (Sec. 2.4, Sec. 3.2), times a constant scale s > 0:
+ * loss_dev (1 float64) = s sum_k (target[pix_k] - I_k)^2 and dLdI_dev (npix float32,
+ * nullable) = -2 s (target[pix_k] - I_k), with I_dev from bos_render_pixels over pix_dev
+ * and target_dev a whole image.  The scale brings image-loss gradients (often 1e-10 per
+ * voxel, since I carries the 1/path-length weight) above an optimiser's epsilon. */
+bos_status_t bos_loss_l2_pixels(const float* I_dev, const float* target_dev, const int32_t* pix_dev, int64_t npix,
+                                float scale, double* loss_dev, float* dLdI_dev, void* stream);
+
+/* A minibatch of npix uniformly random pixel indices in [0, n_pixels) (with repeats):
+ * entry k is the splitmix64 output number draw*npix + k + 1 for `seed`, scaled to the range
+ * by a 64x64-bit multiply-high.  Used for the random BOS-pixel minibatches of Sec. 3.2. */
+bos_status_t bos_sample_pixels(int32_t* pix_dev, int64_t npix, int64_t n_pixels, uint64_t seed, uint64_t draw,
+                               void* stream);
+
+/* One AdaBelief step (the optimiser of Sec. 3.2; Zhuang et al., NeurIPS 2020) on n float32
+ * parameters: m = b1 m + (1-b1) g; s = b2 s + (1-b2) (g-m)^2 + eps;
+ * theta -= lr (m / (1 - b1^step)) / (sqrt(s / (1 - b2^step)) + eps).  step >= 1; m and s start at 0. */
+bos_status_t bos_adabelief_step(float* theta_dev, const float* grad_dev, float* m_dev, float* s_dev, int64_t n,
+                                float lr, float beta1, float beta2, float eps, int64_t step, void* stream);
+
+/* Step a6 (Sec. 2.4): given dL/dI (height*width float32, or npix values after
+ * bos_render_pixels) for the most recent render with save_for_backward=1, write dL/dT
+ * (nz*ny*nx float32).  Needs the
  * FP32_COMP or BF16_COMP precision, Sharma RKN and ckpt_every <= 64 (else
  * BOS_ERR_UNIMPLEMENTED).  dLdI_dev must not alias the accumulators.  Reverses the
  * Sharma steps of every ray from its checkpoints, scatters d L / d(deta, grad eta)

@@ -15,6 +15,8 @@
 //   trilinear eta and grad eta; D = eta * grad eta               [Eq. 1, right-hand side]
 //   Sharma's Runge-Kutta-Nystrom step for dr/dt = v, dv/dt = D   [Sec. 2.2, Eq. 1]
 //   classic RK4 on (r, v) as a cross-check integrator            [Eq. 1]
+//   quasi-linear tracing: the index field sampled on the straight line r_in + t v0
+//   drives the velocity equation, which drives the position equation  [Sec. 2.2]
 //   pinhole camera, tent (triangular) pixel filter sampled by its inverse CDF,
 //   Monte Carlo over the pixel, wall hit by straight extrapolation, textured or
 //   pinhole-projector wall luminance, weight <n_w, v_w> / path length  [Sec. 2.3, Eq. 2]
@@ -74,7 +76,7 @@ typedef struct {
 typedef struct {
     int fixed_steps;       // > 0: steps per ray; 0: ceil(ell / (max_step_vox * min h))
     double max_step_vox;
-    int integrator;        // 0: Sharma RKN, 1: classic RK4
+    int integrator;        // 0: Sharma RKN, 1: classic RK4, 2: quasi-linear (RKN weights, stages on the line)
 } orc_integ;
 
 // Field description.  kind 0: trilinear on node arrays deta (eta - 1) and grad (3 per
@@ -243,6 +245,31 @@ void step_rk4(const Field<S>& F, S r[3], S v[3], S dt) {
     for (int a = 0; a < 3; ++a) {
         r[a] = r[a] + dt / 6.0 * (k1r[a] + 2.0 * k2r[a] + 2.0 * k3r[a] + k4r[a]);
         v[a] = v[a] + dt / 6.0 * (k1v[a] + 2.0 * k2v[a] + 2.0 * k3v[a] + k4v[a]);
+    }
+}
+
+// One step of quasi-linear tracing (Sec. 2.2): the right-hand side of the velocity
+// equation is taken on the straight line r_lin(t) = r_in + t v0 instead of on the ray, so
+// the velocity no longer feeds back into where the field is sampled.  Step n covers
+// [n dt, (n+1) dt]; the stages sit at the start, middle and end of it on the line, with
+// Sharma's weights:
+//   A = dt D(r_lin(n dt)), B = dt D(r_lin((n+1/2) dt)), C = dt D(r_lin((n+1) dt))
+//   r <- r + dt (v + (A + 2B)/6),  v <- v + (A + 4B + C)/6
+template <class S>
+void step_quasi(const Field<S>& F, const S rin[3], const S v0[3], long n, S r[3], S v[3], S dt) {
+    S A[3], B[3], C[3], p[3], D[3];
+    for (int a = 0; a < 3; ++a) p[a] = rin[a] + ((double)n * dt) * v0[a];
+    rhs(F, p, D);
+    for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
+    for (int a = 0; a < 3; ++a) p[a] = rin[a] + (((double)n + 0.5) * dt) * v0[a];
+    rhs(F, p, D);
+    for (int a = 0; a < 3; ++a) B[a] = dt * D[a];
+    for (int a = 0; a < 3; ++a) p[a] = rin[a] + (((double)n + 1.0) * dt) * v0[a];
+    rhs(F, p, D);
+    for (int a = 0; a < 3; ++a) C[a] = dt * D[a];
+    for (int a = 0; a < 3; ++a) {
+        r[a] = r[a] + dt * (v[a] + (A[a] + 2.0 * B[a]) / 6.0);
+        v[a] = v[a] + (A[a] + 4.0 * B[a] + C[a]) / 6.0;
     }
 }
 
@@ -448,9 +475,11 @@ RayOut<S> trace_ray(const Scene& sc, const Field<S>& F, const RayGeom& R, bool s
         for (int a = 0; a < 3; ++a) { r[a] = rin[a]; v[a] = eta_in * R.d[a]; }
         S dt = R.ell / ((double)R.N * eta_in);
         S lensum = S(0.0);
+        const S v0[3] = {v[0], v[1], v[2]};
         for (long n = 0; n < R.N; ++n) {
             S r0[3] = {r[0], r[1], r[2]};
             if (sc.it->integrator == 1) step_rk4(F, r, v, dt);
+            else if (sc.it->integrator == 2) step_quasi(F, rin, v0, n, r, v, dt);
             else step_rkn(F, r, v, dt);
             S dr[3] = {r[0] - r0[0], r[1] - r0[1], r[2] - r0[2]};
             lensum += norm3(dr);
@@ -667,6 +696,41 @@ void step_rkn_adjoint(const Field<double>& F, const double r[3], const double v[
     }
 }
 
+// Reverse one quasi-linear step.  The stage points lie on the straight line
+// r_in + t v0 with t v0 = (n + c) ell/N d, which does not depend on the field, so no
+// position adjoint flows back through the field samples (their dt and v0 dependences
+// cancel exactly, and both are left out).
+void step_quasi_adjoint(const Field<double>& F, const double rin[3], const double v0[3], long n, const double v[3],
+                        double dt, double rb[3], double vb[3], double& dtb, NodeAdj& acc) {
+    double p1[3], p2[3], p3[3], D1[3], D2[3], D3[3], A[3], B[3];
+    for (int a = 0; a < 3; ++a) {
+        p1[a] = rin[a] + ((double)n * dt) * v0[a];
+        p2[a] = rin[a] + (((double)n + 0.5) * dt) * v0[a];
+        p3[a] = rin[a] + (((double)n + 1.0) * dt) * v0[a];
+    }
+    rhs(F, p1, D1);
+    rhs(F, p2, D2);
+    rhs(F, p3, D3);
+    for (int a = 0; a < 3; ++a) {
+        A[a] = dt * D1[a];
+        B[a] = dt * D2[a];
+    }
+    double Ab[3], Bb[3], Cb[3], Db[3], pb[3];
+    for (int a = 0; a < 3; ++a) {
+        Ab[a] = dt / 6.0 * rb[a] + vb[a] / 6.0;
+        Bb[a] = dt / 3.0 * rb[a] + 4.0 * vb[a] / 6.0;
+        Cb[a] = vb[a] / 6.0;
+        dtb += rb[a] * (v[a] + (A[a] + 2.0 * B[a]) / 6.0);
+    }
+    for (int a = 0; a < 3; ++a) { dtb += Cb[a] * D3[a]; Db[a] = dt * Cb[a]; }
+    rhs_adjoint(F, p3, Db, pb, acc);
+    for (int a = 0; a < 3; ++a) { dtb += Bb[a] * D2[a]; Db[a] = dt * Bb[a]; }
+    rhs_adjoint(F, p2, Db, pb, acc);
+    for (int a = 0; a < 3; ++a) { dtb += Ab[a] * D1[a]; Db[a] = dt * Ab[a]; }
+    rhs_adjoint(F, p1, Db, pb, acc);
+    for (int a = 0; a < 3; ++a) vb[a] = vb[a] + dt * rb[a];
+}
+
 // Adjoint of one traced ray with seed Ib = dL/dI_ray, accumulating node adjoints.
 void ray_adjoint(const Scene& sc, const Field<double>& F, const RayGeom& R, double Ib, NodeAdj& acc,
                  std::vector<double>& tape) {
@@ -683,9 +747,11 @@ void ray_adjoint(const Scene& sc, const Field<double>& F, const RayGeom& R, doub
     for (int a = 0; a < 3; ++a) { r[a] = rin[a]; v[a] = eta_in * R.d[a]; }
     for (int a = 0; a < 3; ++a) { tape[a] = r[a]; tape[3 + a] = v[a]; }
     double lensum = 0.0;
+    const double v0[3] = {v[0], v[1], v[2]};
     for (long n = 0; n < N; ++n) {
         double r0[3] = {r[0], r[1], r[2]};
-        step_rkn(F, r, v, dt);
+        if (sc.it->integrator == 2) step_quasi(F, rin, v0, n, r, v, dt);
+        else step_rkn(F, r, v, dt);
         double dr[3] = {r[0] - r0[0], r[1] - r0[1], r[2] - r0[2]};
         lensum += norm3(dr);
         for (int a = 0; a < 3; ++a) { tape[6 * (n + 1) + a] = r[a]; tape[6 * (n + 1) + 3 + a] = v[a]; }
@@ -727,7 +793,8 @@ void ray_adjoint(const Scene& sc, const Field<double>& F, const RayGeom& R, doub
         double dr[3] = {r1[0] - rn[0], r1[1] - rn[1], r1[2] - rn[2]};
         double l = norm3(dr);
         for (int a = 0; a < 3; ++a) rb[a] += lenb * dr[a] / l;            // |r_{n+1} - r_n| term
-        step_rkn_adjoint(F, rn, vn_, dt, rb, vb, dtb, acc);
+        if (sc.it->integrator == 2) step_quasi_adjoint(F, rin, v0, n, vn_, dt, rb, vb, dtb, acc);
+        else step_rkn_adjoint(F, rn, vn_, dt, rb, vb, dtb, acc);
         for (int a = 0; a < 3; ++a) rb[a] -= lenb * dr[a] / l;
     }
     // v0 = eta_in d, dt = ell / (N eta_in), eta_in = 1 + deta(r_in)
@@ -769,9 +836,11 @@ void orc_trace_segment(const orc_grid* g, const orc_field* f, const double* r_in
     double dt = ell / ((double)N * eta_in);
     double ls = 0.0;
     if (tape) for (int a = 0; a < 3; ++a) { tape[a] = r[a]; tape[3 + a] = v[a]; }
+    const double rin[3] = {r[0], r[1], r[2]}, v0[3] = {v[0], v[1], v[2]};
     for (long n = 0; n < N; ++n) {
         double r0[3] = {r[0], r[1], r[2]};
         if (integrator == 1) step_rk4(F, r, v, dt);
+        else if (integrator == 2) step_quasi(F, rin, v0, n, r, v, dt);
         else step_rkn(F, r, v, dt);
         double dr[3] = {r[0] - r0[0], r[1] - r0[1], r[2] - r0[2]};
         ls += norm3(dr);
@@ -868,7 +937,7 @@ void orc_render_cs(const orc_grid* g, const double* T, const double* dT, double 
 }
 
 // Gradient of sum_j w_j I_j with respect to the node fields (deta, grad) and to T, by a
-// discrete adjoint over a full tape of ray states (Sharma RKN only).  w = dL/dI per pixel
+// discrete adjoint over a full tape of ray states (Sharma RKN or quasi-linear).  w = dL/dI per pixel
 // (all pixels).  Node adjoints (may be NULL) receive the direct node sensitivities;
 // dLdT receives the total derivative with respect to T through the central differences
 // and d eta / d T = -rho0 G T0 / T^2.

@@ -91,10 +91,14 @@ SIGNATURES = {
                               _P(bos_integrator_desc)]),
     "bos_render": (_i, [_v, _v, _v, _v, _i, _v]),
     "bos_render_reference": (_i, [_v, _v, _v, _v, _v]),
+    "bos_render_pixels": (_i, [_v, _v, _i64, _v, _v, _i, _v]),
     "bos_ray_steps": (_i, [_v, _v, _v]),
     "bos_last_ray_steps": (_i, [_v, _P(_u64)]),
     "bos_loss_l2": (_i, [_v, _v, _i64, _v, _v, _v]),
     "bos_backward": (_i, [_v, _v, _v, _v]),
+    "bos_loss_l2_pixels": (_i, [_v, _v, _v, _i64, C.c_float, _v, _v, _v]),
+    "bos_sample_pixels": (_i, [_v, _i64, _i64, _u64, _u64, _v]),
+    "bos_adabelief_step": (_i, [_v, _v, _v, _v, _i64, C.c_float, C.c_float, C.c_float, C.c_float, _i64, _v]),
     "bos_export_nodes": (_i, [_v, _v, _v]),
     "bos_probe_read": (_i, [_v, _u64, _i, _v, _v]),
     "bos_render_noalloc": (_i, [_P(bos_grid_desc), _v, _P(bos_camera_desc), _P(bos_wall_desc), _P(bos_light_desc),
@@ -209,6 +213,11 @@ def bos_render(ctx, I_dev, disp_dev, hit_dev, save_for_backward: int, stream) ->
     check(lib().bos_render(ctx, I_dev, disp_dev, hit_dev, int(save_for_backward), stream), "bos_render")
 
 
+def bos_render_pixels(ctx, pix_dev, npix: int, I_dev, disp_dev, save_for_backward: int, stream) -> None:
+    check(lib().bos_render_pixels(ctx, pix_dev, npix, I_dev, disp_dev, int(save_for_backward), stream),
+          "bos_render_pixels")
+
+
 def bos_render_reference(ctx, I_dev, disp_dev, hit_dev, stream) -> None:
     check(lib().bos_render_reference(ctx, I_dev, disp_dev, hit_dev, stream), "bos_render_reference")
 
@@ -225,6 +234,21 @@ def bos_last_ray_steps(ctx) -> int:
 
 def bos_loss_l2(I_dev, target_dev, n: int, loss_dev, dLdI_dev, stream) -> None:
     check(lib().bos_loss_l2(I_dev, target_dev, n, loss_dev, dLdI_dev, stream), "bos_loss_l2")
+
+
+def bos_loss_l2_pixels(I_dev, target_dev, pix_dev, npix: int, loss_dev, dLdI_dev, stream, scale: float = 1.0) -> None:
+    check(lib().bos_loss_l2_pixels(I_dev, target_dev, pix_dev, npix, scale, loss_dev, dLdI_dev, stream),
+          "bos_loss_l2_pixels")
+
+
+def bos_sample_pixels(pix_dev, npix: int, n_pixels: int, seed: int, draw: int, stream) -> None:
+    check(lib().bos_sample_pixels(pix_dev, npix, n_pixels, seed, draw, stream), "bos_sample_pixels")
+
+
+def bos_adabelief_step(theta_dev, grad_dev, m_dev, s_dev, n: int, lr: float, beta1: float, beta2: float, eps: float,
+                       step: int, stream) -> None:
+    check(lib().bos_adabelief_step(theta_dev, grad_dev, m_dev, s_dev, n, lr, beta1, beta2, eps, step, stream),
+          "bos_adabelief_step")
 
 
 def bos_backward(ctx, dLdI_dev, dLdT_dev, stream) -> None:
@@ -327,6 +351,18 @@ class Context:
         I, D, X = out if out is not None else self._outputs(disp, hit)
         bos_render(self.h, _ptr(I), _ptr(D), _ptr(X), int(save_for_backward), _stream(stream))
         return I, D, X
+
+    def render_pixels(self, pix, disp: bool = False, save_for_backward: bool = False, stream=None):
+        """Render the pixels of the int32 device tensor `pix` (flat indices); returns (I, disp)."""
+        import torch
+
+        assert pix.is_cuda and pix.dtype == torch.int32 and pix.is_contiguous()
+        n = pix.numel()
+        I = torch.empty((n,), dtype=torch.float32, device=self.torch_device)
+        D = torch.empty((n, 2), dtype=torch.float32, device=self.torch_device) if disp else None
+        bos_render_pixels(self.h, pix.data_ptr(), n, I.data_ptr(), _ptr(D), int(save_for_backward), _stream(stream))
+        self._pix = pix
+        return I, D
 
     def render_reference(self, disp: bool = False, hit: bool = False, stream=None):
         I, D, X = self._outputs(disp, hit)

@@ -20,9 +20,15 @@
 
 namespace bos {
 
-constexpr int kAdjWarps = 2;          // warps per block
+#ifndef BOS_ADJ_WARPS
+#define BOS_ADJ_WARPS 2
+#endif
+constexpr int kAdjWarps = BOS_ADJ_WARPS;   // warps per block
+#ifndef BOS_ACC_SCALAR
+#define BOS_ACC_SCALAR 0                  // accumulate cell rows with scalar (1) or packed (0) FMAs
+#endif
 #ifndef BOS_ADJ_MIN_BLOCKS
-#define BOS_ADJ_MIN_BLOCKS 6              // resident blocks per SM the register budget is cut for
+#define BOS_ADJ_MIN_BLOCKS 4              // resident blocks per SM the register budget is cut for
 #endif
 constexpr int kRow = 36;              // floats per lane row of the cell accumulators (16-byte aligned rows)
 constexpr int kStageStride = 28;      // floats per lane row of a parked stage (value + 3 derivatives, cell, fractions)
@@ -196,6 +202,18 @@ __device__ __forceinline__ void accumulate(float* rows, bool act, const int ci[3
         ca.key = key;
         float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
         const float g0 = 1.0f - cf[0], g1 = 1.0f - cf[1], g2 = 1.0f - cf[2];
+#if BOS_ACC_SCALAR
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float w = ((c & 1) ? cf[0] : g0) * ((c & 2) ? cf[1] : g1) * ((c & 4) ? cf[2] : g2);
+            float4 r = row[c];
+            r.x = fmaf(w, Q.x, r.x);
+            r.y = fmaf(w, Q.y, r.y);
+            r.z = fmaf(w, Q.z, r.z);
+            r.w = fmaf(w, Q.w, r.w);
+            row[c] = r;
+        }
+#else
         const f32x2 qlo = pack2(Q.x, Q.y), qhi = pack2(Q.z, Q.w);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -207,6 +225,7 @@ __device__ __forceinline__ void accumulate(float* rows, bool act, const int ci[3
             unpack2(hi, r.z, r.w);
             row[c] = r;
         }
+#endif
     }
 }
 
@@ -266,7 +285,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
     const int nx = S.g.n[0], nxy = S.g.n[0] * S.g.n[1];
     const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
     const TileShape ts = tile_shape(W, H, spp);
-    const int ntiles = ts.tiles_x * ts.tiles_y;
+    const int ntiles = tile_count(S, ts);
     float* acc = reinterpret_cast<float*>(adj.acc);
     {
         float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
@@ -280,10 +299,10 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
         if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= ntiles) break;
-        const int tx = t % ts.tiles_x, ty = t / ts.tiles_x;
-        const int lp = lane / ts.G, sl = lane % ts.G;
-        const int px = tx * ts.TW + lp % ts.TW, py = ty * ts.TH + lp / ts.TW;
-        const bool valid = px < W && py < H;
+        const int sl = lane % ts.G;
+        const TilePix tp = tile_pixel(S, ts, t, lane);
+        const int px = tp.px, py = tp.py;
+        const bool valid = tp.valid;
         for (int qs = 0; qs < ts.samples_per_lane; ++qs) {
             const int s = ts.samples_per_lane == 1 ? sl : qs;
             const long long slot = ((long long)t * 32 + lane) * ts.samples_per_lane + qs;
@@ -294,7 +313,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
             double Ib = 0.0;
             if (act) {
                 R = ray_setup(S, px, py, s);
-                Ib = (double)adj.dLdI[(size_t)py * W + px] / spp;
+                Ib = (double)adj.dLdI[(size_t)tp.out] / spp;
             }
             act = act && R.wall && R.N > 0 && Ib != 0.0;
             CompState st0;
@@ -467,6 +486,165 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
     flush_rows(rows, ca.key != kNoKey, ca, acc, nx, nxy);
 }
 
+// Adjoint of quasi-linear tracing (Sec. 2.2).  The stage points lie on the straight
+// line, so the outputs are linear in the sampled D values and no position adjoint flows
+// back through them.  Reversing a step leaves the position adjoint unchanged and adds
+// dt (r_bar + len_bar u_n) to the velocity adjoint (u_n the unit direction of step n), so
+//   v_bar_{n+1} = v_bar_N + dt (N - n - 1) r_bar + dt len_bar sum_{m > n} u_m
+// is known from the final state and a running prefix of u: one sweep in forward order
+// recomputes the samples and scatters every stage's sensitivity (the end sample of a
+// step and the start sample of the next are one point and one scatter).
+template <class E>
+__global__ void __launch_bounds__(kAdjWarps * 32) adjoint_quasi_kernel(SceneDev S, CkptDev ck, AdjDev adj,
+                                                                       WorkDev wk) {
+    extern __shared__ float4 smem4[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* rows = reinterpret_cast<float*>(smem4) + (size_t)warp * 32 * kRow;
+    {
+        float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
+        for (int c = 0; c < 8; ++c) row[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    __syncwarp();
+    const CompField<E> F = {static_cast<const E*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
+                            {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
+    const int nx = S.g.n[0], nxy = S.g.n[0] * S.g.n[1];
+    const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
+    const TileShape ts = tile_shape(W, H, spp);
+    const int ntiles = tile_count(S, ts);
+    float* acc = reinterpret_cast<float*>(adj.acc);
+    CellAcc ca = {kNoKey};
+    const float zero[3] = {0.0f, 0.0f, 0.0f};
+
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntiles) break;
+        const int sl = lane % ts.G;
+        const TilePix tp = tile_pixel(S, ts, t, lane);
+        const int px = tp.px, py = tp.py;
+        const bool valid = tp.valid;
+        for (int qs = 0; qs < ts.samples_per_lane; ++qs) {
+            const int s = ts.samples_per_lane == 1 ? sl : qs;
+            const long long slot = ((long long)t * 32 + lane) * ts.samples_per_lane + qs;
+            bool act = valid;
+            Ray R;
+            R.N = 0;
+            R.wall = false;
+            double Ib = 0.0;
+            if (act) {
+                R = ray_setup(S, px, py, s);
+                Ib = (double)adj.dLdI[(size_t)tp.out] / spp;
+            }
+            act = act && R.wall && R.N > 0 && Ib != 0.0;
+            CompState st;
+            CompConst k;
+            double eta_in = 1.0, rin[3] = {0, 0, 0};
+            float rb[3] = {0, 0, 0}, vbN[3] = {0, 0, 0}, lenb = 0.0f, usum[3] = {0, 0, 0};
+            double etab = 0.0;
+            if (act) {
+                comp_setup(S, F, R, st, k, eta_in, rin);
+                const float4 s0 = ck.state[0 * ck.nrays + slot];
+                const float4 s1 = ck.state[1 * ck.nrays + slot];
+                const float4 s2 = ck.state[2 * ck.nrays + slot];
+                usum[0] = s1.w;
+                usum[1] = s2.x;
+                usum[2] = s2.y;
+                double rN[3], vN[3], drb[3], dvb[3], lb;
+                const float drN[3] = {s0.x, s0.y, s0.z}, dvN[3] = {s1.x, s1.y, s1.z};
+                for (int a = 0; a < 3; ++a) {
+                    rN[a] = rin[a] + R.ell * R.d[a] + (double)drN[a];
+                    vN[a] = eta_in * R.d[a] + (double)dvN[a];
+                }
+                wall_adjoint(S, rN, vN, R.t_in + R.ell + (double)s0.w, Ib, drb, dvb, lb);
+                for (int a = 0; a < 3; ++a) {
+                    rb[a] = (float)drb[a];
+                    vbN[a] = (float)dvb[a];
+                }
+                lenb = (float)lb;
+                etab = dvb[0] * R.d[0] + dvb[1] * R.d[1] + dvb[2] * R.d[2];
+            }
+            const int N = act ? R.N : 0;
+            const int n_max = __reduce_max_sync(0xffffffffu, (unsigned)N);
+            const float dt = act ? k.dt : 0.0f;
+            BrickCache bc = {kNoKey, 0u};
+            // the start sample of step 0
+            Stage p0 = {};
+            float A[3] = {0, 0, 0}, dv[3] = {0, 0, 0}, prefix[3] = {0, 0, 0}, carry[3] = {0, 0, 0}, dtb = 0.0f;
+            if (act) {
+                stage_eval(F, st.U, zero, bc, p0);
+                float D[3];
+                rhs_from(p0.ig, D);
+                for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
+            }
+            for (int n = 0; n < n_max; ++n) {
+                const bool a_ = act && n < N;
+                Stage pm = {}, pe = {};
+                float B[3] = {0, 0, 0}, C[3] = {0, 0, 0}, u[3] = {0, 0, 0}, Dm[3] = {0, 0, 0}, De[3] = {0, 0, 0};
+                float Db0[3] = {0, 0, 0}, Dbm[3] = {0, 0, 0};
+                if (a_) {
+                    long long U2[3], U3[3];
+                    for (int a = 0; a < 3; ++a) {
+                        U2[a] = st.U[a] + (long long)n * k.dU[a] + k.dUh[a];
+                        U3[a] = st.U[a] + (long long)(n + 1) * k.dU[a];
+                    }
+                    stage_eval(F, U2, zero, bc, pm);
+                    rhs_from(pm.ig, Dm);
+                    stage_eval(F, U3, zero, bc, pe);
+                    rhs_from(pe.ig, De);
+                    float inc[3], nn = 0.0f;
+                    for (int a = 0; a < 3; ++a) {
+                        B[a] = dt * Dm[a];
+                        C[a] = dt * De[a];
+                        inc[a] = dt * (dv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
+                        const float w = k.dS[a] + inc[a];
+                        u[a] = w;
+                        nn += w * w;
+                    }
+                    const float rn = rsqrtf(nn);
+                    const float rem = (float)(N - n - 1);
+                    for (int a = 0; a < 3; ++a) {
+                        u[a] *= rn;
+                        prefix[a] += u[a];
+                        const float rbp = rb[a] + lenb * u[a];                       // adjoint of r_{n+1}
+                        const float vb1 = vbN[a] + dt * rem * rb[a] + dt * lenb * (usum[a] - prefix[a]);
+                        const float Ab = (dt * (1.0f / 6.0f)) * rbp + vb1 * (1.0f / 6.0f);
+                        const float Bb = (dt * (1.0f / 3.0f)) * rbp + vb1 * (4.0f / 6.0f);
+                        const float Cb = vb1 * (1.0f / 6.0f);
+                        dtb += rbp * (dv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f)) + Ab * (A[a] / dt) + Bb * Dm[a] +
+                               Cb * De[a];
+                        Db0[a] = carry[a] + dt * Ab;      // start sample: this step's A and the previous C
+                        Dbm[a] = dt * Bb;
+                        carry[a] = dt * Cb;
+                        dv[a] += (A[a] + 4.0f * B[a] + C[a]) * (1.0f / 6.0f);
+                        A[a] = C[a];
+                    }
+                }
+                float pb[3];
+                float4 Q = make_float4(0, 0, 0, 0);
+                if (a_) rhs_adjoint(F, p0.ig, Db0, pb, Q);
+                accumulate(rows, a_, p0.ci, p0.cf, Q, ca, acc, nx, nxy);
+                if (a_) rhs_adjoint(F, pm.ig, Dbm, pb, Q);
+                accumulate(rows, a_, pm.ci, pm.cf, Q, ca, acc, nx, nxy);
+                if (a_) p0 = pe;
+            }
+            // the end sample of the last step, then eta_in = 1 + deta(r_in)
+            float pb[3];
+            float4 Q = make_float4(0, 0, 0, 0);
+            if (act) rhs_adjoint(F, p0.ig, carry, pb, Q);
+            accumulate(rows, act, p0.ci, p0.cf, Q, ca, acc, nx, nxy);
+            int ci[3] = {0, 0, 0};
+            float cf[3] = {0, 0, 0};
+            if (act) {
+                etab -= (double)dtb * (double)dt / eta_in;
+                comp_cell(F, st.U, zero, ci, cf);
+            }
+            accumulate(rows, act, ci, cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), ca, acc, nx, nxy);
+        }
+    }
+    flush_rows(rows, ca.key != kNoKey, ca, acc, nx, nxy);
+}
+
 // dL/dT per node: transpose of the difference stencil of grad eta, plus d L/d deta, times
 // d deta/dT = -K / T^2.
 __global__ void gradient_kernel(GridDev g, const float4* __restrict__ acc, const float* __restrict__ T,
@@ -478,18 +656,18 @@ __global__ void gradient_kernel(GridDev g, const float4* __restrict__ acc, const
         double tot = (double)acc[c].x;
         for (int a = 0; a < 3; ++a) {
             const int i = idx[a], na = g.n[a];
-            const double h = g.h[a], h2 = 2.0 * g.h[a];
+            const double ih = g.inv_h[a], ih2 = 0.5 * g.inv_h[a];
             auto gch = [&](long long m) {
                 float4 v = acc[m];
                 return (double)(a == 0 ? v.y : a == 1 ? v.z : v.w);
             };
-            if (i - 1 >= 0) tot += gch(c - stride[a]) / (i - 1 == 0 ? h : h2);        // node i-1 reads i as hi
-            if (i + 1 <= na - 1) tot -= gch(c + stride[a]) / (i + 1 == na - 1 ? h : h2);  // node i+1 reads i as lo
-            if (i == 0) tot -= gch(c) / h;                                            // one-sided at the faces
-            if (i == na - 1) tot += gch(c) / h;
+            if (i - 1 >= 0) tot += gch(c - stride[a]) * (i - 1 == 0 ? ih : ih2);        // node i-1 reads i as hi
+            if (i + 1 <= na - 1) tot -= gch(c + stride[a]) * (i + 1 == na - 1 ? ih : ih2);  // node i+1 reads i as lo
+            if (i == 0) tot -= gch(c) * ih;                                             // one-sided at the faces
+            if (i == na - 1) tot += gch(c) * ih;
         }
-        const double Tc = (double)T[c];
-        dLdT[c] = (float)(tot * (-g.K / (Tc * Tc)));
+        const float Tc = T[c];
+        dLdT[c] = (float)tot * (-(float)g.K / (Tc * Tc));
     }
 }
 
@@ -507,12 +685,27 @@ static cudaError_t launch_adjoint_t(const SceneDev& S, const CkptDev& ck, const 
     return cudaGetLastError();
 }
 
+template <class E>
+static cudaError_t launch_adjoint_quasi_t(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
+                                          int num_sms, cudaStream_t st) {
+    size_t smem = (size_t)kAdjWarps * 32 * kRow * sizeof(float);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_quasi_kernel<E>, kAdjWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    adjoint_quasi_kernel<E><<<num_sms * per_sm, kAdjWarps * 32, smem, st>>>(S, ck, adj, w);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_backward(int mode, const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
                             const float* T, float* dLdT, int num_sms, cudaStream_t st) {
-    if (ck.every > 64) return cudaErrorNotSupported;
+    const bool quasi = S.it.integrator == 2;
+    if (!quasi && ck.every > 64) return cudaErrorNotSupported;
     cudaError_t e;
-    if (mode == 1) e = launch_adjoint_t<float4>(S, ck, adj, w, num_sms, st);
-    else if (mode == 2) e = launch_adjoint_t<uint2>(S, ck, adj, w, num_sms, st);
+    if (mode == 1) e = quasi ? launch_adjoint_quasi_t<float4>(S, ck, adj, w, num_sms, st)
+                             : launch_adjoint_t<float4>(S, ck, adj, w, num_sms, st);
+    else if (mode == 2) e = quasi ? launch_adjoint_quasi_t<uint2>(S, ck, adj, w, num_sms, st)
+                                  : launch_adjoint_t<uint2>(S, ck, adj, w, num_sms, st);
     else return cudaErrorNotSupported;
     if (e != cudaSuccess) return e;
     gradient_kernel<<<num_sms * 8, 256, 0, st>>>(S.g, adj.acc, T, dLdT);

@@ -119,6 +119,8 @@ struct bos_ctx {
     bool saved = false;
     CkptDev saved_ck{};
     int saved_mode = 0;
+    const int32_t* saved_pix = nullptr;   // pixel list of the saved render (nullptr: whole image)
+    long long saved_npix = 0;
 
     float4* acc = nullptr;
     size_t acc_bytes = 0;
@@ -183,6 +185,8 @@ SceneDev scene_of(const bos_ctx* c) {
     S.w = c->wall;
     S.L = c->light;
     S.it = c->integ;
+    S.pix = nullptr;
+    S.npix = 0;
     return S;
 }
 
@@ -241,7 +245,7 @@ size_t request_bytes(const bos_grid_desc& g, const bos_camera_desc& cam, const b
             double b = ceil(norm3(g.extent) / (it.max_step_vox * hmin)) + 2.0;
             bound = b > 2e9 ? 2000000000 : (int)b;
         }
-        size_t max_ckpt = (size_t)((bound + it.ckpt_every - 1) / it.ckpt_every);
+        size_t max_ckpt = it.integrator == 2 ? 1 : (size_t)((bound + it.ckpt_every - 1) / it.ckpt_every);
         bytes += align_up(max_ckpt * 3 * nslots * sizeof(float4));
         bytes += align_up(nslots * sizeof(float));
         bytes += align_up((size_t)g.nx * g.ny * g.nz * sizeof(float4));
@@ -383,7 +387,7 @@ bos_status_t bos_set_geometry(bos_ctx* c, const bos_camera_desc* cam, const bos_
         return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: fixed_steps out of range");
     if (it->fixed_steps == 0 && !(it->max_step_vox > 1e-3 && it->max_step_vox < 1e6))
         return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: max_step_vox out of range");
-    if (it->integrator != 0 && it->integrator != 1) return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: integrator");
+    if (it->integrator < 0 || it->integrator > 2) return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: integrator");
     if (it->ckpt_every < 1 || it->ckpt_every > 4096)
         return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: ckpt_every must be in [1, 4096]");
     c->cam = to_dev(*cam);
@@ -407,25 +411,30 @@ bos_status_t bos_set_geometry(bos_ctx* c, const bos_camera_desc* cam, const bos_
     return BOS_OK;
 }
 
-static bos_status_t render_impl(bos_ctx* c, int mode, float* I, float* disp, double* hit, int save, void* stream) {
+static bos_status_t render_impl(bos_ctx* c, int mode, float* I, float* disp, double* hit, int save, void* stream,
+                                const int32_t* pix = nullptr, long long npix = 0) {
     if (!c || !I) return fail(BOS_ERR_INVALID_ARG, "bos_render: NULL context or I");
     if (!c->has_grid || !c->has_geom) return fail(BOS_ERR_NOT_READY, "bos_render: set_grid and set_geometry first");
     DeviceGuard dg(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     c->integ.max_steps = step_bound(c);
     SceneDev S = scene_of(c);
+    S.pix = pix;
+    S.npix = npix;
     CkptDev ck{};
     ck.every = c->integ.ckpt_every;
     {
         TileShape ts = tile_shape(c->cam.width, c->cam.height, c->cam.spp);
-        ck.nrays = (long long)ts.tiles_x * ts.tiles_y * 32 * ts.samples_per_lane;
+        long long tiles = pix ? (npix + (32 / ts.G) - 1) / (32 / ts.G) : (long long)ts.tiles_x * ts.tiles_y;
+        ck.nrays = tiles * 32 * ts.samples_per_lane;
     }
     if (save) {
         if (mode != 1 && mode != 2)
             return fail(BOS_ERR_UNIMPLEMENTED, "bos_render: save_for_backward needs FP32_COMP or BF16_COMP");
-        if (c->integ.integrator != 0)
-            return fail(BOS_ERR_UNIMPLEMENTED, "bos_render: the adjoint supports the Sharma RKN integrator only");
-        ck.max_ckpt = (c->integ.max_steps + ck.every - 1) / ck.every;
+        if (c->integ.integrator == 1)
+            return fail(BOS_ERR_UNIMPLEMENTED, "bos_render: no adjoint for the RK4 integrator");
+        // quasi-linear tracing keeps only the final state (one-sweep adjoint)
+        ck.max_ckpt = c->integ.integrator == 2 ? 1 : (c->integ.max_steps + ck.every - 1) / ck.every;
         size_t want = (size_t)ck.max_ckpt * 3 * (size_t)ck.nrays * sizeof(float4);
         bos_status_t s = dev_alloc(c, (void**)&c->ckpt, &c->ckpt_bytes, want, "bos_render: checkpoints");
         if (s != BOS_OK) return s;
@@ -444,12 +453,22 @@ static bos_status_t render_impl(bos_ctx* c, int mode, float* I, float* disp, dou
     c->saved = save != 0;
     c->saved_ck = ck;
     c->saved_mode = mode;
+    c->saved_pix = pix;
+    c->saved_npix = npix;
     return BOS_OK;
 }
 
 bos_status_t bos_render(bos_ctx* c, float* I, float* disp, double* hit, int save_for_backward, void* stream) {
     if (!c) return fail(BOS_ERR_INVALID_ARG, "bos_render: NULL context");
     return render_impl(c, mode_of(c->grid.prec), I, disp, hit, save_for_backward, stream);
+}
+
+bos_status_t bos_render_pixels(bos_ctx* c, const int32_t* pix, int64_t npix, float* I, float* disp,
+                               int save_for_backward, void* stream) {
+    if (!c) return fail(BOS_ERR_INVALID_ARG, "bos_render_pixels: NULL context");
+    if (!pix || npix <= 0 || npix > (1LL << 36))
+        return fail(BOS_ERR_INVALID_ARG, "bos_render_pixels: need a pixel list of 1 .. 2^36 entries");
+    return render_impl(c, mode_of(c->grid.prec), I, disp, nullptr, save_for_backward, stream, pix, npix);
 }
 
 bos_status_t bos_render_reference(bos_ctx* c, float* I, float* disp, double* hit, void* stream) {
@@ -497,7 +516,10 @@ bos_status_t bos_backward(bos_ctx* c, const float* dLdI, float* dLdT, void* stre
     if (e != cudaSuccess) return cuda_fail(e, "bos_backward: memset");
     AdjDev adj{c->acc, dLdI, c->err};
     WorkDev w{c->tile_counter, c->steps, c->err};
-    e = launch_backward(c->saved_mode, scene_of(c), c->saved_ck, adj, w, c->T, dLdT, c->num_sms, st);
+    SceneDev S = scene_of(c);
+    S.pix = c->saved_pix;
+    S.npix = c->saved_npix;
+    e = launch_backward(c->saved_mode, S, c->saved_ck, adj, w, c->T, dLdT, c->num_sms, st);
     if (e == cudaErrorNotSupported) return fail(BOS_ERR_UNIMPLEMENTED, "bos_backward: not available for this mode");
     return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_backward: launch");
 }
@@ -530,6 +552,7 @@ bos_status_t bos_status(bos_ctx* c) {
         case DEV_OK: return BOS_OK;
         case DEV_STEP_BUDGET: return fail(BOS_ERR_DEVICE_CHECK, "a ray needed more steps than the step bound");
         case DEV_CKPT_OVERFLOW: return fail(BOS_ERR_DEVICE_CHECK, "a ray needed more checkpoints than allocated");
+        case DEV_BAD_PIXEL: return fail(BOS_ERR_DEVICE_CHECK, "a pixel index of the list is outside the image");
         default: return fail(BOS_ERR_DEVICE_CHECK, "device error %d", err);
     }
 }

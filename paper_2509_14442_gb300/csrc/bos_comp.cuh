@@ -39,7 +39,9 @@ __device__ __forceinline__ void comp_cell(const CompField<E>& F, const long long
         ci[a] = (int)(U[a] >> 32);
         const float fr = __uint_as_float((lo >> 9) | 0x3f800000u) - 1.0f;
         cf[a] = fmaf(q[a], F.inv_h[a], fr);
-        ok = ok && cf[a] >= 0.0f && cf[a] < 1.0f && ci[a] >= 0 && ci[a] <= F.n[a] - 2;
+        // 0 <= f < 1 exactly when the bit pattern is below that of 1.0f (negatives have the
+        // sign bit set); 0 <= i <= n - 2 as one unsigned compare
+        ok = ok && __float_as_uint(cf[a]) < 0x3f800000u && (uint32_t)ci[a] <= (uint32_t)(F.n[a] - 2);
     }
     if (!ok) {
 #pragma unroll
@@ -98,7 +100,7 @@ __device__ __forceinline__ void comp_step(const CompField<E>& F, CompState& st, 
     float cf[3], D[3];
     float inc_r[3], inc_v[3];
     const float dt = k.dt;
-    if (INTEG == 0) {
+    if constexpr (INTEG != 1) {
         float A[3], B[3], C[3], q[3];
         long long U2[3], U3[3];
         rhs_of(comp_eval(F, st.U, st.dr, bc, ci, cf), D);

@@ -61,6 +61,8 @@ struct SceneDev {
     WallDev w;
     LightDev L;
     IntegDev it;
+    const int32_t* pix;   // nullptr: the whole image; else a list of flat pixel indices
+    long long npix;
 };
 
 struct D4 {            // float64 store element
@@ -482,8 +484,46 @@ __host__ __device__ __forceinline__ TileShape tile_shape(int width, int height, 
     return t;
 }
 
+// Pixel of a lane of warp tile t.  Whole image: TW x TH pixel tiles in row-major order,
+// outputs indexed by pixel.  Pixel list: P = 32/G consecutive list entries per tile,
+// outputs (and dL/dI seeds) indexed by list entry; out-of-range indices are skipped.
+struct TilePix {
+    int px, py;
+    long long out;
+    bool valid, bad;
+};
+
+__device__ __forceinline__ int tile_count(const SceneDev& S, const TileShape& ts) {
+    if (S.pix) return (int)((S.npix + (32 / ts.G) - 1) / (32 / ts.G));
+    return ts.tiles_x * ts.tiles_y;
+}
+
+__device__ __forceinline__ TilePix tile_pixel(const SceneDev& S, const TileShape& ts, int t, int lane) {
+    TilePix r;
+    const int lp = lane / ts.G;
+    r.bad = false;
+    if (S.pix) {
+        const long long e = (long long)t * (32 / ts.G) + lp;
+        const long long npx = (long long)S.cam.width * S.cam.height;
+        long long p = e < S.npix ? (long long)__ldg(S.pix + e) : -1;
+        r.bad = e < S.npix && (p < 0 || p >= npx);
+        r.valid = e < S.npix && !r.bad;
+        if (!r.valid) p = 0;
+        r.px = (int)(p % S.cam.width);
+        r.py = (int)(p / S.cam.width);
+        r.out = e;
+    } else {
+        const int tx = t % ts.tiles_x, ty = t / ts.tiles_x;
+        r.px = tx * ts.TW + lp % ts.TW;
+        r.py = ty * ts.TH + lp / ts.TW;
+        r.valid = r.px < S.cam.width && r.py < S.cam.height;
+        r.out = (long long)r.py * S.cam.width + r.px;
+    }
+    return r;
+}
+
 // Device-side error word: first error code wins.
-enum DeviceError : int { DEV_OK = 0, DEV_STEP_BUDGET = 1, DEV_CKPT_OVERFLOW = 2 };
+enum DeviceError : int { DEV_OK = 0, DEV_STEP_BUDGET = 1, DEV_CKPT_OVERFLOW = 2, DEV_BAD_PIXEL = 3 };
 
 __device__ __forceinline__ void flag_error(int* err, int code) {
     if (err) atomicCAS(err, 0, code);

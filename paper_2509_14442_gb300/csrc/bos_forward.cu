@@ -39,38 +39,51 @@ __device__ __forceinline__ double deta_at(const GridDev& g, const float* T, int 
     return ddiv(g.K, t);
 }
 
-// One thread per stored cell: bricks of 9^3 cells (8 + apron) over base cells 0..n-2.
+// One block per brick: deta = K / T is computed once for every cell of the brick's 9^3
+// records plus a one-cell halo (11^3 values in shared memory), then each record takes
+// its central or one-sided differences from there.  Bricks cover base cells 0..n-2;
+// coordinates beyond the grid are clamped (those records are never read).
+constexpr int kHalo = kBrickSide + 2;   // 11
+
 template <class E>
-__global__ void build_store_kernel(GridDev g, const float* __restrict__ T, E* __restrict__ store, long long total) {
-    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= total) return;
-    int local = (int)(tid % kBrickCells);
-    long long b = tid / kBrickCells;
-    int bx = (int)(b % g.nb[0]);
-    int by = (int)((b / g.nb[0]) % g.nb[1]);
-    int bz = (int)(b / ((long long)g.nb[0] * g.nb[1]));
-    int lx = local % kBrickSide, ly = (local / kBrickSide) % kBrickSide, lz = local / (kBrickSide * kBrickSide);
-    int c[3] = {min(bx * kBrick + lx, g.n[0] - 1), min(by * kBrick + ly, g.n[1] - 1), min(bz * kBrick + lz, g.n[2] - 1)};
-    double de = deta_at(g, T, c[0], c[1], c[2]);
-    double gr[3];
-    for (int a = 0; a < 3; ++a) {
-        int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
-        double den = dmul(2.0, g.h[a]);
-        lo[a] = c[a] - 1;
-        hi[a] = c[a] + 1;
-        if (lo[a] < 0) {
-            lo[a] = c[a];
-            den = g.h[a];
-        }
-        if (hi[a] > g.n[a] - 1) {
-            hi[a] = c[a];
-            den = g.h[a];
-        }
-        double d = dsub(deta_at(g, T, hi[0], hi[1], hi[2]), deta_at(g, T, lo[0], lo[1], lo[2]));
-        gr[a] = ddiv(d, den);
+__global__ void __launch_bounds__(256) build_store_kernel(GridDev g, const float* __restrict__ T,
+                                                          E* __restrict__ store) {
+    __shared__ double de[kHalo * kHalo * kHalo];
+    const int b = blockIdx.x;
+    const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
+    const int ox = bx * kBrick - 1, oy = by * kBrick - 1, oz = bz * kBrick - 1;
+    for (int t = threadIdx.x; t < kHalo * kHalo * kHalo; t += blockDim.x) {
+        const int hx = t % kHalo, hy = (t / kHalo) % kHalo, hz = t / (kHalo * kHalo);
+        const int i = min(max(ox + hx, 0), g.n[0] - 1), j = min(max(oy + hy, 0), g.n[1] - 1),
+                  k = min(max(oz + hz, 0), g.n[2] - 1);
+        de[t] = deta_at(g, T, i, j, k);
     }
-    uint32_t slot = morton3((uint32_t)bx, (uint32_t)by, (uint32_t)bz);
-    store_cell<E>(store + (size_t)slot * kBrickCells + local, de, gr[0], gr[1], gr[2]);
+    __syncthreads();
+    const uint32_t slot = morton3((uint32_t)bx, (uint32_t)by, (uint32_t)bz);
+    for (int local = threadIdx.x; local < kBrickCells; local += blockDim.x) {
+        const int lx = local % kBrickSide, ly = (local / kBrickSide) % kBrickSide, lz = local / (kBrickSide * kBrickSide);
+        const int c[3] = {min(bx * kBrick + lx, g.n[0] - 1), min(by * kBrick + ly, g.n[1] - 1),
+                          min(bz * kBrick + lz, g.n[2] - 1)};
+        // halo index of a (clamped) grid cell
+        auto at = [&](int i, int j, int k) { return de[((k - oz) * kHalo + (j - oy)) * kHalo + (i - ox)]; };
+        double gr[3];
+        for (int a = 0; a < 3; ++a) {
+            int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
+            double den = dmul(2.0, g.h[a]);
+            lo[a] = c[a] - 1;
+            hi[a] = c[a] + 1;
+            if (lo[a] < 0) {
+                lo[a] = c[a];
+                den = g.h[a];
+            }
+            if (hi[a] > g.n[a] - 1) {
+                hi[a] = c[a];
+                den = g.h[a];
+            }
+            gr[a] = ddiv(dsub(at(hi[0], hi[1], hi[2]), at(lo[0], lo[1], lo[2])), den);
+        }
+        store_cell<E>(store + (size_t)slot * kBrickCells + local, at(c[0], c[1], c[2]), gr[0], gr[1], gr[2]);
+    }
 }
 
 // ===================================================================== a3: integrators
@@ -171,7 +184,56 @@ __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const 
 #ifndef BOS_FWD_PIPELINE
 #define BOS_FWD_PIPELINE 1
 #endif
-    if (INTEG == 0 && BOS_FWD_PIPELINE) {
+    if constexpr (INTEG == 2) {
+        // Quasi-linear tracing (Sec. 2.2): the field is sampled on the straight line at the
+        // start, middle and end of every step (Sharma's weights); the end sample is the next
+        // step's start sample, so each step gathers twice, with no dependence on the ray.
+        const float zero[3] = {0.0f, 0.0f, 0.0f};
+        int ci[3];
+        float cf[3], A[3], B[3], C[3], D[3];
+        float usum[3] = {0.0f, 0.0f, 0.0f};
+        const float dt = k.dt;
+        rhs_of(comp_eval(F, st.U, zero, bc, ci, cf), D);
+        for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
+        for (int n = 0; n < R.N; ++n) {
+            long long U2[3], U3[3];
+            for (int a = 0; a < 3; ++a) {
+                U2[a] = st.U[a] + k.dUh[a];
+                U3[a] = st.U[a] + k.dU[a];
+            }
+            rhs_of(comp_eval(F, U2, zero, bc, ci, cf), D);
+            for (int a = 0; a < 3; ++a) B[a] = dt * D[a];
+            rhs_of(comp_eval(F, U3, zero, bc, ci, cf), D);
+            float inc_r[3], inc_v[3];
+            for (int a = 0; a < 3; ++a) {
+                C[a] = dt * D[a];
+                inc_r[a] = dt * (st.dv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
+                inc_v[a] = (A[a] + 4.0f * B[a] + C[a]) * (1.0f / 6.0f);
+            }
+            float si = k.dS[0] * inc_r[0] + k.dS[1] * inc_r[1] + k.dS[2] * inc_r[2];
+            float ii = inc_r[0] * inc_r[0] + inc_r[1] * inc_r[1] + inc_r[2] * inc_r[2];
+            float di = k.dhat[0] * inc_r[0] + k.dhat[1] * inc_r[1] + k.dhat[2] * inc_r[2];
+            st.excess += (2.0f * si + ii) / (2.0f * k.step_len + di);
+            if (ck.state != nullptr) {          // sum of the unit step directions, for the adjoint
+                float w[3] = {k.dS[0] + inc_r[0], k.dS[1] + inc_r[1], k.dS[2] + inc_r[2]};
+                float rn = rsqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+                for (int a = 0; a < 3; ++a) usum[a] += w[a] * rn;
+            }
+            for (int a = 0; a < 3; ++a) {
+                kahan_add(st.dr[a], st.cr[a], inc_r[a]);
+                kahan_add(st.dv[a], st.cv[a], inc_v[a]);
+                st.U[a] = U3[a];
+                A[a] = C[a];
+            }
+        }
+        if (ck.state != nullptr) {   // the final state, for the one-sweep adjoint
+            ck.state[0 * ck.nrays + ray] = make_float4(st.dr[0] - st.cr[0], st.dr[1] - st.cr[1], st.dr[2] - st.cr[2],
+                                                       st.excess);
+            ck.state[1 * ck.nrays + ray] = make_float4(st.dv[0] - st.cv[0], st.dv[1] - st.cv[1], st.dv[2] - st.cv[2],
+                                                       usum[0]);
+            ck.state[2 * ck.nrays + ray] = make_float4(usum[1], usum[2], 0.0f, 0.0f);
+        }
+    } else if constexpr (INTEG == 0 && BOS_FWD_PIPELINE) {
         // Sharma steps, software-pipelined: the next step's first stage needs only the new
         // position r' = r + dt (v + (A + 2B)/6), not C, so it is evaluated together with this
         // step's third stage.  Same operations as comp_step, in a different order in time.
@@ -263,9 +325,28 @@ __device__ RayResult trace_full(const SceneDev& S, const FullField<T>& F, const 
     for (int a = 0; a < 3; ++a) v[a] = eta_in * (T)R.d[a];
     T dt = (T)R.ell / ((T)R.N * eta_in);
     T lensum = 0;
+    const T rl[3] = {r[0], r[1], r[2]}, v0[3] = {v[0], v[1], v[2]};
     for (int n = 0; n < R.N; ++n) {
         T r0[3] = {r[0], r[1], r[2]};
-        full_step<T, INTEG>(F, r, v, dt);
+        if constexpr (INTEG == 2) {
+            // quasi-linear: the field on the straight line at the start, middle and end of the step
+            T A[3], B[3], C[3], p[3], D[3];
+            for (int a = 0; a < 3; ++a) p[a] = rl[a] + ((T)n * dt) * v0[a];
+            F.rhs(p, D);
+            for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
+            for (int a = 0; a < 3; ++a) p[a] = rl[a] + (((T)n + T(0.5)) * dt) * v0[a];
+            F.rhs(p, D);
+            for (int a = 0; a < 3; ++a) B[a] = dt * D[a];
+            for (int a = 0; a < 3; ++a) p[a] = rl[a] + (((T)n + T(1)) * dt) * v0[a];
+            F.rhs(p, D);
+            for (int a = 0; a < 3; ++a) C[a] = dt * D[a];
+            for (int a = 0; a < 3; ++a) {
+                r[a] = r[a] + dt * (v[a] + (A[a] + T(2) * B[a]) / T(6));
+                v[a] = v[a] + (A[a] + T(4) * B[a] + C[a]) / T(6);
+            }
+        } else {
+            full_step<T, INTEG>(F, r, v, dt);
+        }
         T d0 = r[0] - r0[0], d1 = r[1] - r0[1], d2 = r[2] - r0[2];
         lensum += sqrt(d0 * d0 + d1 * d1 + d2 * d2);
     }
@@ -300,10 +381,13 @@ __device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, 
 }
 
 template <int MODE, int INTEG>
-__global__ void __launch_bounds__(128, 4) render_kernel(SceneDev S, RenderOut out, WorkDev wk, CkptDev ck) {
+#ifndef BOS_FWD_MIN_BLOCKS
+#define BOS_FWD_MIN_BLOCKS 4              // resident 128-thread blocks per SM the register budget is cut for
+#endif
+__global__ void __launch_bounds__(128, BOS_FWD_MIN_BLOCKS) render_kernel(SceneDev S, RenderOut out, WorkDev wk, CkptDev ck) {
     const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
     const TileShape ts = tile_shape(W, H, spp);
-    const int ntiles = ts.tiles_x * ts.tiles_y;
+    const int ntiles = tile_count(S, ts);
     const int lane = threadIdx.x & 31;
     unsigned long long my_steps = 0;
     for (;;) {
@@ -311,10 +395,11 @@ __global__ void __launch_bounds__(128, 4) render_kernel(SceneDev S, RenderOut ou
         if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= ntiles) break;
-        const int tx = t % ts.tiles_x, ty = t / ts.tiles_x;
-        const int lp = lane / ts.G, sl = lane % ts.G;
-        const int px = tx * ts.TW + lp % ts.TW, py = ty * ts.TH + lp / ts.TW;
-        const bool valid = px < W && py < H;
+        const int sl = lane % ts.G;
+        const TilePix tp = tile_pixel(S, ts, t, lane);
+        if (tp.bad) flag_error(wk.err, DEV_BAD_PIXEL);
+        const int px = tp.px, py = tp.py;
+        const bool valid = tp.valid;
         Sums acc = {0, 0, 0, 0, 0};
         if (valid) {
             for (int q = 0; q < ts.samples_per_lane; ++q) {
@@ -349,7 +434,7 @@ __global__ void __launch_bounds__(128, 4) render_kernel(SceneDev S, RenderOut ou
             acc.hv += __shfl_xor_sync(0xffffffffu, acc.hv, m);
         }
         if (valid && sl == 0) {
-            const size_t p = (size_t)py * W + px;
+            const size_t p = (size_t)tp.out;
             const double inv = 1.0 / spp;
             out.I[p] = (float)(acc.I * inv);
             if (out.disp) {
@@ -436,13 +521,11 @@ cudaError_t launch_probe_read(const void* buf, long long bytes, int repeats, flo
 // ===================================================================== launchers
 
 cudaError_t launch_build_store(const GridDev& g, const float* T, void* store, cudaStream_t st) {
-    long long total = (long long)g.nb[0] * g.nb[1] * g.nb[2] * kBrickCells;
-    int threads = 256;
-    long long blocks = (total + threads - 1) / threads;
+    const unsigned blocks = (unsigned)g.nb[0] * g.nb[1] * g.nb[2];
     switch (g.prec) {
-        case 0: build_store_kernel<D4><<<(unsigned)blocks, threads, 0, st>>>(g, T, (D4*)store, total); break;
-        case 3: build_store_kernel<uint2><<<(unsigned)blocks, threads, 0, st>>>(g, T, (uint2*)store, total); break;
-        default: build_store_kernel<float4><<<(unsigned)blocks, threads, 0, st>>>(g, T, (float4*)store, total); break;
+        case 0: build_store_kernel<D4><<<blocks, 256, 0, st>>>(g, T, (D4*)store); break;
+        case 3: build_store_kernel<uint2><<<blocks, 256, 0, st>>>(g, T, (uint2*)store); break;
+        default: build_store_kernel<float4><<<blocks, 256, 0, st>>>(g, T, (float4*)store); break;
     }
     return cudaGetLastError();
 }
@@ -463,8 +546,9 @@ cudaError_t launch_render(int mode, const SceneDev& S, const RenderOut& o, const
     const int integ = S.it.integrator;
 #define BOS_CASE(M)                                                                        \
     case M:                                                                                \
-        return integ == 1 ? launch_render_t<M, 1>(S, o, w, ck, num_sms, st)                \
-                          : launch_render_t<M, 0>(S, o, w, ck, num_sms, st);
+        return integ == 1   ? launch_render_t<M, 1>(S, o, w, ck, num_sms, st)              \
+               : integ == 2 ? launch_render_t<M, 2>(S, o, w, ck, num_sms, st)              \
+                            : launch_render_t<M, 0>(S, o, w, ck, num_sms, st);
     switch (mode) {
         BOS_CASE(0)
         BOS_CASE(1)

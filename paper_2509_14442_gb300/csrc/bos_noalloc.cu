@@ -144,6 +144,8 @@ extern "C" bos_status_t bos_render_noalloc(const bos_grid_desc* grid, const floa
     if (e != cudaSuccess) return refuse(BOS_ERR_CUDA, "field build: %s", cudaGetErrorString(e));
 
     SceneDev S;
+    S.pix = nullptr;
+    S.npix = 0;
     S.g = g;
     S.cam = cam_dev(*cam);
     for (int a = 0; a < 3; ++a) {

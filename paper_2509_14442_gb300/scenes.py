@@ -98,7 +98,7 @@ class Light:
 class Integrator:
     fixed_steps: int = 0            # > 0: this many steps per ray; 0: adaptive
     max_step_vox: float = 0.5       # adaptive step bound in units of the smallest cell size
-    integrator: int = 0             # 0: Sharma RKN, 1: classic RK4
+    integrator: int = 0             # 0: Sharma RKN, 1: classic RK4, 2: quasi-linear (Sharma weights)
     ckpt_every: int = 16            # adjoint checkpoint interval (steps)
 
 

@@ -153,3 +153,20 @@ def test_adjoint_full_size_against_oracle_finite_differences(bos, orc):
     assert scale > 0
     bad = np.abs(gp - fd) > 1e-3 * np.abs(fd) + 1e-3 * scale
     assert bad.sum() == 0, (np.flatnonzero(bad), gp[bad], fd[bad])
+
+
+# ------------------------------------------------------------------ quasi-linear tracing (Sec. 2.2)
+
+@pytest.mark.parametrize("spp", [1, 3])
+def test_quasi_linear_adjoint_matches_oracle(bos, orc, spp):
+    sc = S.room((40, 40, 30), 61, 47, spp, 3400 + spp)
+    sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=2))
+    w = np.random.default_rng(20 + spp).standard_normal((sc.camera.height, sc.camera.width))
+    assert rel_l2(gpu_grad(bos, sc, w), orc.grad(sc, w)) <= GRAD_REL_L2
+
+
+def test_quasi_linear_adjoint_matches_oracle_on_32cube_crop(bos, orc):
+    sc = crop_scene()
+    sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=2))
+    w = np.random.default_rng(13).standard_normal((sc.camera.height, sc.camera.width))
+    assert rel_l2(gpu_grad(bos, sc, w), orc.grad(sc, w)) <= GRAD_REL_L2

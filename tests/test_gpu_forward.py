@@ -160,3 +160,27 @@ def test_room_adjoint_scene_full_size_sampled(bos, orc):
     o = orc.render(sc, pix=pix, nsteps=True)
     e = errors(g, o, pix)
     assert e["I_abs"] <= I_ABS_TOL and e["disp_rel"] <= DISP_REL_TOL, e
+
+
+# ------------------------------------------------------------------ quasi-linear tracing (Sec. 2.2)
+
+@pytest.mark.parametrize("prec", ["fp32_comp", "fp64", "bf16_comp"])
+def test_quasi_linear_parity(bos, orc, prec):
+    sc = S.room((96, 96, 72), 121, 97, 2, 2800)
+    sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=2))
+    if prec == "bf16_comp":
+        de = orc.deta_from_T(sc.grid, sc.T.astype(np.float64))
+        o = orc.render(sc, field=orc.NodeField(bf16_round(de), bf16_round(orc.grad_from_deta(sc.grid, de))))
+    else:
+        o = orc.render(sc)
+    _check(gpu_render(sc, bos.PRECISIONS[prec]), o, disp_tol=2e-7 if prec == "fp64" else DISP_REL_TOL)
+
+
+@pytest.mark.slow
+def test_quasi_linear_full_size_sampled(bos, orc):
+    sc = S.room_adjoint()
+    sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=2))
+    g = gpu_render(sc, bos.BOS_PREC_FP32_COMP)
+    pix = np.random.default_rng(3).choice(sc.pixels, 600, replace=False)
+    e = errors(g, orc.render(sc, pix=pix), pix)
+    assert e["I_abs"] <= I_ABS_TOL and e["disp_rel"] <= DISP_REL_TOL, e

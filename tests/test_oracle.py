@@ -432,3 +432,54 @@ def test_loss_gradient_single_voxel_central_difference(orc):
     Tm[k] -= eps
     fd = (loss(Tp) - loss(Tm)) / (2 * eps)
     assert gT[k] == pytest.approx(fd, rel=1e-5)
+
+
+# ----------------------------------------------------------------- quasi-linear tracing, Sec. 2.2
+
+def test_quasi_linear_closed_form_when_eta_is_linear(orc):
+    # on the straight line eta(r_in + t v0) = eta0 + (g.v0) t, so
+    #   v(t) = v0 + g (eta0 t + (g.v0) t^2 / 2),  r(t) = r0 + v0 t + g (eta0 t^2 / 2 + (g.v0) t^3 / 6)
+    # which Sharma's weights integrate exactly (the sampled right-hand side is linear in t)
+    gvec = np.array([0.05, 0.2, -0.1])
+    e0 = 1.0003
+    fld = orc.AnalyticField(2, [e0, *gvec])
+    g = unit_grid()
+    r0 = np.array([0.2, 0.0, 0.6])
+    d = np.array([0.1, 1.0, 0.05])
+    d /= np.linalg.norm(d)
+    ell, N = 1.2, 50
+    r, v, _ = orc.trace_segment(g, fld, r0, d, ell, N, 2)
+    eta0 = e0 + gvec @ r0
+    v0 = eta0 * d
+    t = ell / eta0
+    gv = gvec @ v0
+    np.testing.assert_allclose(v, v0 + gvec * (eta0 * t + gv * t * t / 2), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(r, r0 + v0 * t + gvec * (eta0 * t * t / 2 + gv * t ** 3 / 6), rtol=0, atol=1e-13)
+    # and differs from the fully coupled ray at second order in the bending
+    rn, _, _ = orc.trace_segment(g, fld, r0, d, ell, N, 0)
+    bend = np.linalg.norm(rn - (r0 + v0 * t))
+    assert 0 < np.linalg.norm(r - rn) < 0.2 * bend
+
+
+def test_quasi_linear_is_close_to_nonlinear_in_weak_fields(orc):
+    # the paper's premise (Sec. 2.2): for small index changes the quasi-linear path deviates
+    # little from the true one -- here the displacement differs at second order
+    sc = S.blob_cube()
+    on = orc.render(sc)
+    oq = orc.render(sc.replace(integ=S.Integrator(fixed_steps=128, integrator=2)))
+    dmax = np.abs(on["disp"]).max()
+    assert np.abs(oq["disp"] - on["disp"]).max() < 1e-2 * dmax
+    assert np.abs(oq["disp"] - on["disp"]).max() > 0
+
+
+def test_quasi_linear_adjoint_matches_complex_step(orc):
+    sc = _grad_scene()
+    sc = sc.replace(integ=S.Integrator(fixed_steps=40, integrator=2))
+    rng = np.random.default_rng(12)
+    w = rng.standard_normal((sc.camera.height, sc.camera.width))
+    gT = orc.grad(sc, w)
+    for _ in range(2):
+        dT = rng.standard_normal(sc.T.shape)
+        dI, _ = orc.render_cs(sc, dT)
+        lhs, rhs = float((gT * dT).sum()), float((w * dI).sum())
+        assert abs(lhs - rhs) <= 1e-9 * abs(rhs), (lhs, rhs)

@@ -38,6 +38,10 @@ def test_footprint_counts_every_buffer(bos):
     ck = -(-n_max // 16) * 48 * rays
     expect = fwd + ck + rays * 4 + 64 ** 3 * 16 + rays * 4
     assert adj == expect
+    # quasi-linear tracing keeps only the final state per ray
+    q = request(bos, (64, 64, 64), adjoint=True)
+    q.integ.integrator = 2
+    assert bos.bos_request_footprint(q) == fwd + 48 * rays + rays * 4 + 64 ** 3 * 16 + rays * 4
     # bigger grids and images need more
     assert bos.bos_request_footprint(request(bos, (128, 128, 96))) > fwd
     assert bos.bos_request_footprint(request(bos, img=(512, 512), adjoint=True)) > adj
