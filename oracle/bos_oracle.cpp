@@ -489,9 +489,10 @@ RayOut<S> trace_ray(const Scene& sc, const Field<S>& F, const RayGeom& R, bool s
         S q[3] = {w.origin[0] - r[0], w.origin[1] - r[1], w.origin[2] - r[2]};
         S tstar = (q[0] * w.normal[0] + q[1] * w.normal[1] + q[2] * w.normal[2]) / vn;
         for (int a = 0; a < 3; ++a) { xw[a] = r[a] + tstar * v[a]; vN[a] = v[a]; }
+        // path length to the wall: entry distance, traced polyline, and the straight
+        // continuation from r_N, signed (t* < 0 when the traced segment ends behind the wall)
         S seg_in[3] = {rin[0] - R.rs[0], rin[1] - R.rs[1], rin[2] - R.rs[2]};
-        S seg_out[3] = {xw[0] - r[0], xw[1] - r[1], xw[2] - r[2]};
-        len = norm3(seg_in) + lensum + norm3(seg_out);
+        len = norm3(seg_in) + lensum + tstar * norm3(v);
         o.N = R.N;
     }
     S cosw = (vN[0] * w.normal[0] + vN[1] * w.normal[1] + vN[2] * w.normal[2]) / norm3(vN);
@@ -760,12 +761,11 @@ void ray_adjoint(const Scene& sc, const Field<double>& F, const RayGeom& R, doub
     if (!(vn > 0.0)) return;
     double q[3] = {w.origin[0] - r[0], w.origin[1] - r[1], w.origin[2] - r[2]};
     double tstar = (q[0] * w.normal[0] + q[1] * w.normal[1] + q[2] * w.normal[2]) / vn;
-    double xw[3], so[3];
-    for (int a = 0; a < 3; ++a) { xw[a] = r[a] + tstar * v[a]; so[a] = xw[a] - r[a]; }
+    double xw[3];
+    for (int a = 0; a < 3; ++a) xw[a] = r[a] + tstar * v[a];
     double si[3] = {rin[0] - R.rs[0], rin[1] - R.rs[1], rin[2] - R.rs[2]};
-    double lout = norm3(so);
-    double len = norm3(si) + lensum + lout;
     double vlen = norm3(v);
+    double len = norm3(si) + lensum + tstar * vlen;   // signed continuation, as in trace_ray
     double cosw = vn / vlen;
     double Lw = luminance<double>(*sc.L, w, xw);
 
@@ -773,10 +773,13 @@ void ray_adjoint(const Scene& sc, const Field<double>& F, const RayGeom& R, doub
     double Lb = Ib * cosw / len, cb = Ib * Lw / len, lenb = -Ib * Lw * cosw / (len * len);
     double gL[3];
     luminance_grad(*sc.L, w, xw, gL);
+    // x_w - r_N = t* v, so the length of the continuation t* |v| has the adjoint
+    // lenb v / |v| on x_w and its negative on r_N (t* passed through x_w below).
     double xwb[3], rb[3], vb[3];
     for (int a = 0; a < 3; ++a) {
-        xwb[a] = Lb * gL[a] + lenb * so[a] / lout;   // luminance and |x_w - r_N|
-        rb[a] = -lenb * so[a] / lout;
+        double uo = v[a] / vlen;
+        xwb[a] = Lb * gL[a] + lenb * uo;   // luminance and t* |v|
+        rb[a] = -lenb * uo;
         vb[a] = cb * (w.normal[a] / vlen - vn * v[a] / (vlen * vlen * vlen));   // cosine
     }
     // x_w = r + t* v,  t* = ((o - r) . n) / (v . n)

@@ -241,14 +241,10 @@ __device__ __forceinline__ void wall_adjoint(const SceneDev& S, const double rN[
     if (!(vn > 0.0)) return;
     double q[3] = {w.origin[0] - rN[0], w.origin[1] - rN[1], w.origin[2] - rN[2]};
     double ts = (q[0] * w.normal[0] + q[1] * w.normal[1] + q[2] * w.normal[2]) / vn;
-    double xw[3], so[3];
-    for (int a = 0; a < 3; ++a) {
-        xw[a] = rN[a] + ts * vN[a];
-        so[a] = xw[a] - rN[a];
-    }
+    double xw[3];
+    for (int a = 0; a < 3; ++a) xw[a] = rN[a] + ts * vN[a];
     double vl = sqrt(vN[0] * vN[0] + vN[1] * vN[1] + vN[2] * vN[2]);
-    double lout = fabs(ts) * vl;
-    double len = len_before + lout;
+    double len = len_before + ts * vl;              // signed continuation x_w - r_N = t* v
     double cw = vn / vl;
     double gL[3];
     double Lw = wall_luminance(S.L, w, xw, gL);
@@ -256,7 +252,7 @@ __device__ __forceinline__ void wall_adjoint(const SceneDev& S, const double rN[
     lenb = -Ib * Lw * cw / (len * len);
     double xwb[3];
     for (int a = 0; a < 3; ++a) {
-        double u = lout > 0.0 ? so[a] / lout : 0.0;
+        double u = vN[a] / vl;                      // d(t* |v|) through x_w = r_N + t* v
         xwb[a] = Lb * gL[a] + lenb * u;
         rb[a] = -lenb * u;
         vb[a] = cb * (w.normal[a] / vl - vn * vN[a] / (vl * vl * vl));

@@ -259,7 +259,7 @@ __device__ __forceinline__ RayResult comp_epilogue(const SceneDev& S, const Ray&
     for (int a = 0; a < 3; ++a) dx[a] = dr[a] + ts * dv[a] + kk * df[a];
     const float ddv = df[0] * dv[0] + df[1] * dv[1] + df[2] * dv[2];
     const float vl = sqrtf(e * e + 2.0f * e * ddv + (dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]));
-    const float len = (float)(R.t_in + R.ell) + (excess + fabsf(ts) * vl);
+    const float len = (float)(R.t_in + R.ell) + (excess + ts * vl);   // signed continuation t* |v|
     double xref[3];
     for (int a = 0; a < 3; ++a) xref[a] = S.cam.pos[a] + R.tw * R.d[a];
     const float Lw = luminance_rel(S, xref, dx);

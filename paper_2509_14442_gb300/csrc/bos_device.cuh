@@ -448,7 +448,7 @@ __device__ __forceinline__ RayResult wall_epilogue(const SceneDev& S, const doub
     double xw[3], dx[3];
     for (int a = 0; a < 3; ++a) xw[a] = rN[a] + ts * vN[a];
     double vl = sqrt(vN[0] * vN[0] + vN[1] * vN[1] + vN[2] * vN[2]);
-    double len = len_before + fabs(ts) * vl;
+    double len = len_before + ts * vl;   // signed: t* < 0 when r_N lies behind the wall
     double cw = vn / vl;
     o.I = wall_luminance(S.L, w, xw) * cw / len;
     for (int a = 0; a < 3; ++a) {

@@ -434,6 +434,25 @@ def test_loss_gradient_single_voxel_central_difference(orc):
     assert gT[k] == pytest.approx(fd, rel=1e-5)
 
 
+def test_adjoint_at_a_uniform_medium_matches_central_differences(orc):
+    # In a uniform medium whose box ends at the back wall, rays end on the wall
+    # (x_w = r_N) and |x_w - r_N| has a kink there; the adjoint takes its zero
+    # subgradient, which is what a central difference (symmetric in +/- eps) sees.
+    sc = S.room((12, 12, 9), 24, 18, 1, 23, pattern_size=32)
+    sc = sc.replace(T=np.full(sc.T.shape, S.T_AMBIENT))
+    rng = np.random.default_rng(8)
+    w = rng.standard_normal((18, 24))
+    gT = orc.grad(sc, w)
+    assert np.isfinite(gT).all() and np.abs(gT).max() > 0
+    dT = rng.standard_normal(sc.T.shape)
+    eps = 1e-3
+    Ip = orc.render(sc.replace(T=sc.T + eps * dT))["I"]
+    Im = orc.render(sc.replace(T=sc.T - eps * dT))["I"]
+    rhs = float((w * (Ip - Im)).sum()) / (2 * eps)
+    lhs = float((gT * dT).sum())
+    assert abs(lhs - rhs) <= 1e-6 * abs(rhs), (lhs, rhs)
+
+
 # ----------------------------------------------------------------- quasi-linear tracing, Sec. 2.2
 
 def test_quasi_linear_closed_form_when_eta_is_linear(orc):
