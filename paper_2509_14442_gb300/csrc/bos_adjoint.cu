@@ -178,8 +178,23 @@ __device__ __forceinline__ void flush_rows(float* rows, bool flag, CellAcc& ca, 
         const uint32_t lk = __shfl_sync(0xffffffffu, mykey, leader);
         const unsigned grp = __ballot_sync(0xffffffffu, mykey == lk);
         pend &= ~grp;
+        // column sum over the group's rows, sixteen rows at a time with independent loads
+        // and a pairwise tree (warp tiles are coherent, so a group is often the whole warp)
         float sum = 0.0f;
-        for (unsigned m = grp; m; m &= m - 1) sum += rows[(__ffs(m) - 1) * kRow + lane];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const unsigned part = (grp >> (16 * q)) & 0xffffu;
+            if (part) {
+                float v[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = (part >> i) & 1u ? rows[(16 * q + i) * kRow + lane] : 0.0f;
+#pragma unroll
+                for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                    for (int i = 0; i < w; ++i) v[i] += v[i + w];
+                sum += v[0];
+            }
+        }
         if (sum != 0.0f) atomicAdd(acc + ((size_t)(lk + off) << 2) + (lane & 3), sum);
     }
     __syncwarp();

@@ -185,6 +185,7 @@ SceneDev scene_of(const bos_ctx* c) {
     S.w = c->wall;
     S.L = c->light;
     S.it = c->integ;
+    S.rc = bos::ray_const_of(S);
     S.pix = nullptr;
     S.npix = 0;
     return S;
@@ -204,6 +205,28 @@ int step_bound(const bos_ctx* c) {
 namespace bos {
 
 void set_last_error(const char* msg) { g_last_error = msg; }
+
+// Host IEEE double (this file is built without FMA contraction), in the order the
+// per-ray device code used for the same terms.
+RayConst ray_const_of(const SceneDev& S) {
+    RayConst rc;
+    const double* f = S.cam.fwd;
+    const double* u = S.cam.up;
+    const double* p = S.cam.pos;
+    rc.right[0] = f[1] * u[2] - f[2] * u[1];
+    rc.right[1] = f[2] * u[0] - f[0] * u[2];
+    rc.right[2] = f[0] * u[1] - f[1] * u[0];
+    for (int a = 0; a < 3; ++a) {
+        rc.lo_m[a] = S.g.origin[a] - p[a];
+        rc.hi_m[a] = (S.g.origin[a] + S.g.extent[a]) - p[a];
+    }
+    const double q[3] = {S.w.origin[0] - p[0], S.w.origin[1] - p[1], S.w.origin[2] - p[2]};
+    rc.qn = (q[0] * S.w.normal[0] + q[1] * S.w.normal[1]) + q[2] * S.w.normal[2];
+    double hmin = S.g.h[0] < S.g.h[1] ? S.g.h[0] : S.g.h[1];
+    hmin = S.g.h[2] < hmin ? S.g.h[2] : hmin;
+    rc.step = S.it.max_step_vox * hmin;
+    return rc;
+}
 
 // Bind a context to a device arena (nullptr: back to its own allocations).  Drops the
 // context's grid, geometry and saved render.

@@ -147,7 +147,7 @@ __device__ __forceinline__ void comp_step(const CompField<E>& F, CompState& st, 
     float si = k.dS[0] * inc_r[0] + k.dS[1] * inc_r[1] + k.dS[2] * inc_r[2];
     float ii = inc_r[0] * inc_r[0] + inc_r[1] * inc_r[1] + inc_r[2] * inc_r[2];
     float di = k.dhat[0] * inc_r[0] + k.dhat[1] * inc_r[1] + k.dhat[2] * inc_r[2];
-    st.excess += (2.0f * si + ii) / (2.0f * k.step_len + di);
+    st.excess += __fdividef(2.0f * si + ii, 2.0f * k.step_len + di);
     for (int a = 0; a < 3; ++a) {
         kahan_add(st.dr[a], st.cr[a], inc_r[a]);
         kahan_add(st.dv[a], st.cv[a], inc_v[a]);

@@ -55,12 +55,23 @@ struct IntegDev {
     int max_steps;     // bound on N for any ray of this grid/camera (sizes checkpoints)
 };
 
+// Ray-independent float64 terms of the ray set-up, formed on the host with the same IEEE
+// operations (and order) the per-ray code would apply, so every ray sees the same bits.
+struct RayConst {
+    double right[3];       // fwd x up
+    double lo_m[3];        // grid origin - camera position
+    double hi_m[3];        // (grid origin + extent) - camera position
+    double qn;             // (wall origin - camera position) . wall normal
+    double step;           // max_step_vox * min(h)
+};
+
 struct SceneDev {
     GridDev g;
     CamDev cam;
     WallDev w;
     LightDev L;
     IntegDev it;
+    RayConst rc;
     const int32_t* pix;   // nullptr: the whole image; else a list of flat pixel indices
     long long npix;
 };
@@ -296,10 +307,8 @@ __device__ __forceinline__ void image_point(const CamDev& c, int px, int py, int
     y = dadd(dadd((double)py, 0.5), t2);
 }
 
-__device__ __forceinline__ void pinhole_direction(const CamDev& c, double x, double y, double d[3]) {
-    double right[3] = {dsub(dmul(c.fwd[1], c.up[2]), dmul(c.fwd[2], c.up[1])),
-                       dsub(dmul(c.fwd[2], c.up[0]), dmul(c.fwd[0], c.up[2])),
-                       dsub(dmul(c.fwd[0], c.up[1]), dmul(c.fwd[1], c.up[0]))};
+__device__ __forceinline__ void pinhole_direction(const CamDev& c, const double right[3], double x, double y,
+                                                  double d[3]) {
     double a = dmul(dsub(x, c.cx), c.inv_fx);
     double b = dmul(dsub(y, c.cy), c.inv_fy);
     for (int i = 0; i < 3; ++i) d[i] = dadd(dsub(dmul(a, right[i]), dmul(b, c.up[i])), c.fwd[i]);
@@ -323,7 +332,7 @@ __device__ __forceinline__ Ray ray_setup(const SceneDev& S, int px, int py, int 
     Ray R;
     double x, y;
     image_point(S.cam, px, py, s, x, y);
-    pinhole_direction(S.cam, x, y, R.d);
+    pinhole_direction(S.cam, S.rc.right, x, y, R.d);
     const double* rs = S.cam.pos;
     R.N = 0;
     R.t_in = 0.0;
@@ -332,19 +341,17 @@ __device__ __forceinline__ Ray ray_setup(const SceneDev& S, int px, int py, int 
     double den = ddot(R.d, S.w.normal);
     R.wall = den > 0.0;
     if (!R.wall) return R;
-    double q[3] = {dsub(S.w.origin[0], rs[0]), dsub(S.w.origin[1], rs[1]), dsub(S.w.origin[2], rs[2])};
-    R.tw = ddiv(ddot(q, S.w.normal), den);
+    R.tw = ddiv(S.rc.qn, den);
     double t_in = 0.0, t_out = __longlong_as_double(0x7ff0000000000000LL);
     bool inside = true;
     for (int a = 0; a < 3; ++a) {
-        double lo = S.g.origin[a], hi = dadd(S.g.origin[a], S.g.extent[a]);
         if (R.d[a] == 0.0) {
-            if (rs[a] < lo || rs[a] > hi) inside = false;
+            if (rs[a] < S.g.origin[a] || rs[a] > dadd(S.g.origin[a], S.g.extent[a])) inside = false;
             continue;
         }
         double inv = ddiv(1.0, R.d[a]);
-        double t0 = dmul(dsub(lo, rs[a]), inv);
-        double t1 = dmul(dsub(hi, rs[a]), inv);
+        double t0 = dmul(S.rc.lo_m[a], inv);
+        double t1 = dmul(S.rc.hi_m[a], inv);
         if (t0 > t1) {
             double t = t0;
             t0 = t1;
@@ -360,10 +367,7 @@ __device__ __forceinline__ Ray ray_setup(const SceneDev& S, int px, int py, int 
     if (S.it.fixed_steps > 0) {
         R.N = S.it.fixed_steps;
     } else {
-        double hmin = S.g.h[0] < S.g.h[1] ? S.g.h[0] : S.g.h[1];
-        hmin = S.g.h[2] < hmin ? S.g.h[2] : hmin;
-        double step = dmul(S.it.max_step_vox, hmin);
-        double nn = ceil(ddiv(R.ell, step));
+        double nn = ceil(ddiv(R.ell, S.rc.step));
         R.N = nn > (double)S.it.max_steps ? -1 : (int)nn;   // -1: over the step budget
     }
     return R;

@@ -213,7 +213,7 @@ __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const 
             float si = k.dS[0] * inc_r[0] + k.dS[1] * inc_r[1] + k.dS[2] * inc_r[2];
             float ii = inc_r[0] * inc_r[0] + inc_r[1] * inc_r[1] + inc_r[2] * inc_r[2];
             float di = k.dhat[0] * inc_r[0] + k.dhat[1] * inc_r[1] + k.dhat[2] * inc_r[2];
-            st.excess += (2.0f * si + ii) / (2.0f * k.step_len + di);
+            st.excess += __fdividef(2.0f * si + ii, 2.0f * k.step_len + di);
             if (ck.state != nullptr) {          // sum of the unit step directions, for the adjoint
                 float w[3] = {k.dS[0] + inc_r[0], k.dS[1] + inc_r[1], k.dS[2] + inc_r[2]};
                 float rn = rsqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
@@ -284,7 +284,7 @@ __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const 
             float si = k.dS[0] * inc_r[0] + k.dS[1] * inc_r[1] + k.dS[2] * inc_r[2];
             float ii = inc_r[0] * inc_r[0] + inc_r[1] * inc_r[1] + inc_r[2] * inc_r[2];
             float di = k.dhat[0] * inc_r[0] + k.dhat[1] * inc_r[1] + k.dhat[2] * inc_r[2];
-            st.excess += (2.0f * si + ii) / (2.0f * k.step_len + di);
+            st.excess += __fdividef(2.0f * si + ii, 2.0f * k.step_len + di);
             for (int a = 0; a < 3; ++a) {
                 st.dr[a] = dr1[a];
                 st.cr[a] = cr1[a];
@@ -382,7 +382,7 @@ __device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, 
 
 template <int MODE, int INTEG>
 #ifndef BOS_FWD_MIN_BLOCKS
-#define BOS_FWD_MIN_BLOCKS 4              // resident 128-thread blocks per SM the register budget is cut for
+#define BOS_FWD_MIN_BLOCKS 6              // resident 128-thread blocks per SM the register budget is cut for
 #endif
 __global__ void __launch_bounds__(128, BOS_FWD_MIN_BLOCKS) render_kernel(SceneDev S, RenderOut out, WorkDev wk, CkptDev ck) {
     const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;

@@ -44,6 +44,9 @@ struct AdjDev {
 // Message returned by bos_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
+// Ray-independent float64 set-up terms of a scene (S.g, S.cam, S.w and S.it filled in).
+RayConst ray_const_of(const SceneDev& S);
+
 cudaError_t launch_build_store(const GridDev& g, const float* T, void* store, cudaStream_t st);
 cudaError_t launch_render(int mode, const SceneDev& S, const RenderOut& o, const WorkDev& w, const CkptDev& ck,
                           int num_sms, cudaStream_t st);

@@ -173,6 +173,7 @@ extern "C" bos_status_t bos_render_noalloc(const bos_grid_desc* grid, const floa
         double b = ceil(diag / (integ->max_step_vox * hmin)) + 2.0;
         S.it.max_steps = b > 2e9 ? 2000000000 : (int)b;
     }
+    S.rc = ray_const_of(S);
     const int mode = grid->prec == BOS_PREC_FP32_COMP ? 1 : grid->prec == BOS_PREC_BF16_COMP ? 2
                      : grid->prec == BOS_PREC_FP32     ? 3
                                                        : 4;
