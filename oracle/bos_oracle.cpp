@@ -20,6 +20,9 @@
 //   pinhole camera, tent (triangular) pixel filter sampled by its inverse CDF,
 //   Monte Carlo over the pixel, wall hit by straight extrapolation, textured or
 //   pinhole-projector wall luminance, weight <n_w, v_w> / path length  [Sec. 2.3, Eq. 2]
+//   refracted projector connection: the projector point that lights wall point x_w is the
+//   one whose own ray, traced through the same field, lands on x_w; found by M rounds of
+//   aiming a_{k+1} = a_k + (x_w - y(a_k)) from a_0 = x_w                    [Sec. 2.3]
 //   L_BOS = sum_j (I_flow_j - I_j)^2 and its gradient with respect to T by a
 //   discrete adjoint over a full tape of ray states              [Sec. 2.4]
 //   complex-step directional derivatives (the same code run on std::complex<double>)
@@ -67,10 +70,13 @@ typedef struct {
 } orc_wall;
 
 typedef struct {
-    int mode;              // 0: luminance is a texture on the wall, 1: pinhole projector
-    orc_camera proj;       // projector pinhole (mode 1); width/height = pattern size
+    int mode;              // 0: luminance is a texture on the wall, 1: pinhole projector with a
+                           // straight projector-to-wall connection, 2: the projector's own rays
+                           // traced through the field too (refracted connection)
+    orc_camera proj;       // projector pinhole (modes 1, 2); width/height = pattern size
     int tw, th;            // texture / pattern size (texels)
     const float* pattern;  // th rows of tw values
+    int connect_iters;     // mode 2: projector rays traced per wall point (M >= 1)
 } orc_light;
 
 typedef struct {
@@ -448,6 +454,122 @@ void wall_coords(const orc_wall& w, const S x[3], S out[2]) {
     out[1] = q[0] * w.ev[0] + q[1] * w.ev[1] + q[2] * w.ev[2];
 }
 
+// ---------------------------------------------------------------- projector rays [Sec. 2.3]
+
+// Geometry of the projector ray aimed at wall point `aim`: unit direction from the
+// projector pinhole, the box segment [t_in, t_end] (t_end = min(box exit, wall plane)) and
+// its step count.  The same slab test as a camera ray, written for real or complex
+// arithmetic; branch decisions and N use the real parts.  in_axis / out_axis name the
+// slab face that fixes t_in / t_end (-1: t_in = 0 inside the box; out_axis = 3: the wall).
+template <class S>
+struct ProjGeom {
+    S q[3], nq, d[3];
+    bool wall, traced;
+    S tw, t_in, t_end, ell;
+    int in_axis, out_axis;
+    long N;
+};
+
+template <class S>
+ProjGeom<S> projector_geometry(const Scene& sc, const S aim[3]) {
+    const orc_grid& g = *sc.g;
+    const orc_wall& w = *sc.w;
+    const double* P = sc.L->proj.pos;
+    ProjGeom<S> G;
+    for (int a = 0; a < 3; ++a) G.q[a] = aim[a] - P[a];
+    G.nq = norm3(G.q);
+    S inv_n = 1.0 / G.nq;
+    for (int a = 0; a < 3; ++a) G.d[a] = G.q[a] * inv_n;
+    S den = G.d[0] * w.normal[0] + G.d[1] * w.normal[1] + G.d[2] * w.normal[2];
+    G.wall = re(den) > 0.0;
+    G.traced = false;
+    G.N = 0;
+    G.in_axis = -1;
+    G.out_axis = 3;
+    G.tw = G.t_in = G.t_end = G.ell = S(0.0);
+    if (!G.wall) return G;
+    double qw[3] = {w.origin[0] - P[0], w.origin[1] - P[1], w.origin[2] - P[2]};
+    G.tw = (qw[0] * w.normal[0] + qw[1] * w.normal[1] + qw[2] * w.normal[2]) / den;
+    S t_in = S(0.0), t_out = S(INFINITY);
+    int ia = -1, oa = -1;
+    bool inside = true;
+    for (int a = 0; a < 3; ++a) {
+        double lo = g.origin[a], hi = g.origin[a] + g.extent[a];
+        if (re(G.d[a]) == 0.0) {
+            if (P[a] < lo || P[a] > hi) inside = false;
+            continue;
+        }
+        S inv = 1.0 / G.d[a];
+        S t0 = (lo - P[a]) * inv, t1 = (hi - P[a]) * inv;
+        if (re(t0) > re(t1)) std::swap(t0, t1);
+        if (re(t0) > re(t_in)) { t_in = t0; ia = a; }
+        if (re(t1) < re(t_out)) { t_out = t1; oa = a; }
+    }
+    S t_end = G.tw;
+    int ea = 3;
+    if (re(t_out) < re(G.tw)) { t_end = t_out; ea = oa; }
+    if (!inside || !(re(t_in) < re(t_end))) return G;
+    G.traced = true;
+    G.t_in = t_in;
+    G.t_end = t_end;
+    G.in_axis = ia;
+    G.out_axis = ea;
+    G.ell = t_end - t_in;
+    if (sc.it->fixed_steps > 0) {
+        G.N = sc.it->fixed_steps;
+    } else {
+        double hmin = std::min(spacing(g, 0), std::min(spacing(g, 1), spacing(g, 2)));
+        G.N = (long)std::ceil(re(G.ell) / (sc.it->max_step_vox * hmin));
+    }
+    return G;
+}
+
+// Wall hit y of the projector ray aimed at `aim`: straight to the box, N integrator steps
+// of Eq. 1 inside it (v0 = eta(r_in) d, dt = ell / (N eta(r_in)), as for camera rays), then
+// straight from (r_N, v_N) to the wall plane.  Without a box segment y is the straight hit.
+template <class S>
+void trace_projector(const Scene& sc, const Field<S>& F, const S aim[3], S y[3]) {
+    const orc_wall& w = *sc.w;
+    const double* P = sc.L->proj.pos;
+    ProjGeom<S> G = projector_geometry(sc, aim);
+    if (!G.wall) {
+        for (int a = 0; a < 3; ++a) y[a] = aim[a];
+        return;
+    }
+    if (!G.traced) {
+        for (int a = 0; a < 3; ++a) y[a] = P[a] + G.tw * G.d[a];
+        return;
+    }
+    S rin[3], r[3], v[3], eta_in, gd[3];
+    for (int a = 0; a < 3; ++a) rin[a] = P[a] + G.t_in * G.d[a];
+    field_eval(F, rin, eta_in, gd);
+    for (int a = 0; a < 3; ++a) { r[a] = rin[a]; v[a] = eta_in * G.d[a]; }
+    S dt = G.ell / ((double)G.N * eta_in);
+    const S v0[3] = {v[0], v[1], v[2]};
+    for (long n = 0; n < G.N; ++n) {
+        if (sc.it->integrator == 1) step_rk4(F, r, v, dt);
+        else if (sc.it->integrator == 2) step_quasi(F, rin, v0, n, r, v, dt);
+        else step_rkn(F, r, v, dt);
+    }
+    S vn = v[0] * w.normal[0] + v[1] * w.normal[1] + v[2] * w.normal[2];
+    S qq[3] = {w.origin[0] - r[0], w.origin[1] - r[1], w.origin[2] - r[2]};
+    S ts = (qq[0] * w.normal[0] + qq[1] * w.normal[1] + qq[2] * w.normal[2]) / vn;
+    for (int a = 0; a < 3; ++a) y[a] = r[a] + ts * v[a];
+}
+
+// The wall point whose projector pattern value lights x_w: M rounds of
+// a_{k+1} = a_k + (x_w - y(a_k)) from a_0 = x_w (mode 2; modes 0, 1 return x_w).
+template <class S>
+void connect_projector(const Scene& sc, const Field<S>& F, const S xw[3], S a[3]) {
+    for (int c = 0; c < 3; ++c) a[c] = xw[c];
+    if (sc.L->mode != 2) return;
+    for (int k = 0; k < sc.L->connect_iters; ++k) {
+        S y[3];
+        trace_projector(sc, F, a, y);
+        for (int c = 0; c < 3; ++c) a[c] = a[c] + (xw[c] - y[c]);
+    }
+}
+
 // Trace one ray: straight to the box, N integrator steps of Eq. 1 inside it with
 // v0 = eta(r_in) d and dt = ell / (N eta(r_in)) (so |v| = eta, dt = ds / eta), then straight
 // from (r_N, v_N) to the wall.  `straight` forces the reference (no-flow) ray.
@@ -496,7 +618,13 @@ RayOut<S> trace_ray(const Scene& sc, const Field<S>& F, const RayGeom& R, bool s
         o.N = R.N;
     }
     S cosw = (vN[0] * w.normal[0] + vN[1] * w.normal[1] + vN[2] * w.normal[2]) / norm3(vN);
-    o.I = luminance<S>(*sc.L, w, xw) * cosw / len;
+    S xl[3];   // where the luminance is read: x_w, or its refracted projector connection
+    if (straight) {
+        for (int a = 0; a < 3; ++a) xl[a] = xw[a];
+    } else {
+        connect_projector(sc, F, xw, xl);
+    }
+    o.I = luminance<S>(*sc.L, w, xl) * cosw / len;
     wall_coords(w, xw, o.hit);
     S dx[3] = {xw[0] - xref[0], xw[1] - xref[1], xw[2] - xref[2]};
     o.disp[0] = dx[0] * w.eu[0] + dx[1] * w.eu[1] + dx[2] * w.eu[2];
@@ -732,11 +860,124 @@ void step_quasi_adjoint(const Field<double>& F, const double rin[3], const doubl
     for (int a = 0; a < 3; ++a) vb[a] = vb[a] + dt * rb[a];
 }
 
+inline double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Adjoint of y = trace_projector(aim) (Sharma RKN, full tape): for the seed yb = dL/dy,
+// adds the node adjoints of the projector ray's samples and returns ab = dL/d aim, which
+// flows through the ray's direction d = q / |q| (q = aim - P), its box segment (t_in and
+// t_end on the slab faces or the wall plane) and its entry state v0 = eta(r_in) d,
+// dt = ell / (N eta(r_in)).  N is an integer and has no derivative.
+void projector_adjoint(const Scene& sc, const Field<double>& F, const double aim[3], const double yb[3],
+                       NodeAdj& acc, double ab[3]) {
+    const orc_wall& w = *sc.w;
+    const double* P = sc.L->proj.pos;
+    ProjGeom<double> G = projector_geometry(sc, aim);
+    if (!G.wall) {   // y = aim
+        for (int a = 0; a < 3; ++a) ab[a] = yb[a];
+        return;
+    }
+    const double den = dot3(G.d, w.normal);
+    double db[3] = {0, 0, 0};
+    if (!G.traced) {
+        // y = P + t_w d,  t_w = ((o - P) . n) / (d . n)
+        double twb = dot3(yb, G.d);
+        for (int a = 0; a < 3; ++a) db[a] = G.tw * yb[a] - twb * G.tw * w.normal[a] / den;
+    } else {
+        const long N = G.N;
+        double rin[3], eta_in, gdum[3];
+        for (int a = 0; a < 3; ++a) rin[a] = P[a] + G.t_in * G.d[a];
+        field_eval(F, rin, eta_in, gdum);
+        const double dt = G.ell / ((double)N * eta_in);
+        std::vector<double> tape((size_t)(N + 1) * 6);
+        double r[3], v[3];
+        for (int a = 0; a < 3; ++a) { r[a] = rin[a]; v[a] = eta_in * G.d[a]; }
+        for (int a = 0; a < 3; ++a) { tape[a] = r[a]; tape[3 + a] = v[a]; }
+        for (long n = 0; n < N; ++n) {
+            step_rkn(F, r, v, dt);
+            for (int a = 0; a < 3; ++a) { tape[6 * (n + 1) + a] = r[a]; tape[6 * (n + 1) + 3 + a] = v[a]; }
+        }
+        // y = r_N + t* v_N,  t* = ((o - r_N) . n) / (v_N . n)
+        const double vn = dot3(v, w.normal);
+        double qq[3] = {w.origin[0] - r[0], w.origin[1] - r[1], w.origin[2] - r[2]};
+        const double ts = dot3(qq, w.normal) / vn;
+        double rb[3], vb[3], dtb = 0.0;
+        const double tb = dot3(yb, v);
+        for (int a = 0; a < 3; ++a) {
+            rb[a] = yb[a] - tb * w.normal[a] / vn;
+            vb[a] = ts * yb[a] - tb * ts * w.normal[a] / vn;
+        }
+        for (long n = N - 1; n >= 0; --n) step_rkn_adjoint(F, &tape[6 * n], &tape[6 * n + 3], dt, rb, vb, dtb, acc);
+        // eta_in = 1 + deta(r_in): node adjoints, and its slope moves r_in's adjoint
+        const double etab = dot3(vb, G.d) - dtb * dt / eta_in;
+        Corner C[8];
+        corners_at(*F.g, rin, C);
+        for (int c = 0; c < 8; ++c) {
+            acc.deta[C[c].node] += C[c].w * etab;
+            for (int k = 0; k < 3; ++k) rb[k] += etab * C[c].dw[k] * F.deta[C[c].node];
+        }
+        // r_in = P + t_in d,  v0 = eta_in d,  ell = t_end - t_in
+        for (int a = 0; a < 3; ++a) db[a] = eta_in * vb[a] + G.t_in * rb[a];
+        const double ellb = dtb / ((double)N * eta_in);
+        const double tinb = dot3(rb, G.d) - ellb, tendb = ellb;
+        if (G.in_axis >= 0) db[G.in_axis] += tinb * (-G.t_in / G.d[G.in_axis]);   // t_in = (face - P) / d
+        if (G.out_axis == 3) {
+            for (int a = 0; a < 3; ++a) db[a] += tendb * (-G.tw * w.normal[a] / den);   // t_end = t_w
+        } else {
+            db[G.out_axis] += tendb * (-G.t_end / G.d[G.out_axis]);
+        }
+    }
+    // d = q / |q|
+    const double dd = dot3(db, G.d);
+    for (int a = 0; a < 3; ++a) ab[a] = (db[a] - dd * G.d[a]) / G.nq;
+}
+
+// Adjoint of the luminance read at the projector connection of x_w (Lb = dL/dL_wall):
+// reverses a_{k+1} = a_k + (x_w - y(a_k)), a_0 = x_w, and returns dL/dx_w (modes 0 and 1:
+// Lb times the luminance gradient at x_w).
+void connection_adjoint(const Scene& sc, const Field<double>& F, const double xw[3], double Lb, NodeAdj& acc,
+                        double xwb[3]) {
+    const int M = sc.L->mode == 2 ? sc.L->connect_iters : 0;
+    std::vector<double> a((size_t)(M + 1) * 3);
+    for (int c = 0; c < 3; ++c) a[c] = xw[c];
+    for (int k = 0; k < M; ++k) {
+        double y[3];
+        trace_projector(sc, F, &a[3 * k], y);
+        for (int c = 0; c < 3; ++c) a[3 * (k + 1) + c] = a[3 * k + c] + (xw[c] - y[c]);
+    }
+    double gL[3], abar[3];
+    luminance_grad(*sc.L, *sc.w, &a[3 * M], gL);
+    for (int c = 0; c < 3; ++c) {
+        abar[c] = Lb * gL[c];
+        xwb[c] = 0.0;
+    }
+    for (int k = M - 1; k >= 0; --k) {
+        double yb[3], ak[3];
+        for (int c = 0; c < 3; ++c) {
+            xwb[c] += abar[c];
+            yb[c] = -abar[c];
+        }
+        projector_adjoint(sc, F, &a[3 * k], yb, acc, ak);
+        for (int c = 0; c < 3; ++c) abar[c] += ak[c];
+    }
+    for (int c = 0; c < 3; ++c) xwb[c] += abar[c];
+}
+
 // Adjoint of one traced ray with seed Ib = dL/dI_ray, accumulating node adjoints.
 void ray_adjoint(const Scene& sc, const Field<double>& F, const RayGeom& R, double Ib, NodeAdj& acc,
                  std::vector<double>& tape) {
-    if (!R.wall || !R.traced || Ib == 0.0) return;   // the straight part does not depend on the field
+    if (!R.wall || Ib == 0.0) return;
     const orc_wall& w = *sc.w;
+    if (!R.traced) {
+        // the straight camera ray does not depend on the field; a refracted projector
+        // connection of its wall point still does
+        if (sc.L->mode == 2) {
+            double xw[3], xwb[3];
+            for (int a = 0; a < 3; ++a) xw[a] = R.rs[a] + R.tw * R.d[a];
+            double cosw = dot3(R.d, w.normal);
+            connection_adjoint(sc, F, xw, Ib * cosw / R.tw, acc, xwb);
+        }
+        return;
+    }
     const long N = R.N;
     double rin[3];
     for (int a = 0; a < 3; ++a) rin[a] = R.rs[a] + R.t_in * R.d[a];
@@ -767,18 +1008,20 @@ void ray_adjoint(const Scene& sc, const Field<double>& F, const RayGeom& R, doub
     double vlen = norm3(v);
     double len = norm3(si) + lensum + tstar * vlen;   // signed continuation, as in trace_ray
     double cosw = vn / vlen;
-    double Lw = luminance<double>(*sc.L, w, xw);
+    double xl[3];
+    connect_projector(sc, F, xw, xl);
+    double Lw = luminance<double>(*sc.L, w, xl);
 
     // I = Lw * cosw / len
     double Lb = Ib * cosw / len, cb = Ib * Lw / len, lenb = -Ib * Lw * cosw / (len * len);
-    double gL[3];
-    luminance_grad(*sc.L, w, xw, gL);
+    double gL[3];   // dL/dx_w through the luminance (and the projector connection)
+    connection_adjoint(sc, F, xw, Lb, acc, gL);
     // x_w - r_N = t* v, so the length of the continuation t* |v| has the adjoint
     // lenb v / |v| on x_w and its negative on r_N (t* passed through x_w below).
     double xwb[3], rb[3], vb[3];
     for (int a = 0; a < 3; ++a) {
         double uo = v[a] / vlen;
-        xwb[a] = Lb * gL[a] + lenb * uo;   // luminance and t* |v|
+        xwb[a] = gL[a] + lenb * uo;   // luminance and t* |v|
         rb[a] = -lenb * uo;
         vb[a] = cb * (w.normal[a] / vlen - vn * v[a] / (vlen * vlen * vlen));   // cosine
     }
@@ -812,7 +1055,7 @@ void ray_adjoint(const Scene& sc, const Field<double>& F, const RayGeom& R, doub
 // =============================================================== C ABI of the oracle
 extern "C" {
 
-int orc_abi_version(void) { return 3; }
+int orc_abi_version(void) { return 4; }
 
 void orc_deta_from_T(const orc_grid* g, const double* T, double* deta) { deta_from_T<double>(*g, T, deta); }
 
@@ -870,6 +1113,22 @@ void orc_ray_setup(const orc_grid* g, const orc_camera* cam, const orc_wall* w, 
 
 uint64_t orc_splitmix64_output(uint64_t seed, uint64_t k) { return splitmix64_output(seed, k); }
 double orc_tent_inverse(double xi) { return tent_inverse(xi); }
+
+// Projector connection (mode 2) of npts wall points x: the aim a after the light's
+// connect_iters rounds (or `iters` >= 0 rounds when given) and the wall hit y(a) of the
+// projector ray aimed at it.  The camera is not used.
+void orc_connect(const orc_grid* g, const orc_field* f, const orc_wall* w, const orc_light* L, const orc_integ* it,
+                 long npts, const double* x, int iters, double* a_out, double* y_out) {
+    Field<double> F = make_field(g, f);
+    orc_light L2 = *L;
+    L2.mode = 2;
+    if (iters >= 0) L2.connect_iters = iters;
+    Scene sc = {g, nullptr, w, &L2, it};
+    for (long i = 0; i < npts; ++i) {
+        connect_projector(sc, F, x + 3 * i, a_out + 3 * i);
+        trace_projector(sc, F, a_out + 3 * i, y_out + 3 * i);
+    }
+}
 
 // Luminance at npts wall points.
 void orc_luminance(const orc_light* L, const orc_wall* w, long npts, const double* x, double* out) {
@@ -948,6 +1207,10 @@ void orc_grad(const orc_grid* g, const double* T, const orc_camera* cam, const o
               const orc_integ* it, const double* dLdI, int threads, double* dLdT, double* node_deta,
               double* node_grad) {
     const size_t n = (size_t)g->n[0] * g->n[1] * g->n[2];
+    if (L->mode == 2 && it->integrator != 0) {   // the projector-ray adjoint is written for Sharma RKN
+        for (size_t c = 0; c < n; ++c) dLdT[c] = NAN;
+        return;
+    }
     std::vector<double> de(n), gr(3 * n);
     deta_from_T<double>(*g, T, de.data());
     grad_from_deta<double>(*g, de.data(), gr.data());

@@ -46,7 +46,7 @@ class Wall(C.Structure):
 
 class Light(C.Structure):
     _fields_ = [("mode", C.c_int), ("proj", Camera), ("tw", C.c_int), ("th", C.c_int),
-                ("pattern", C.POINTER(C.c_float))]
+                ("pattern", C.POINTER(C.c_float)), ("connect_iters", C.c_int)]
 
 
 class Integ(C.Structure):
@@ -78,6 +78,7 @@ def lib():
         _lib.orc_trace_segment.argtypes = [P(Grid), P(Field), v, v, d, l, i, v, v, v, v]
         _lib.orc_ray_setup.argtypes = [P(Grid), P(Camera), P(Wall), P(Integ), l, i, v, v, v, v, v, v, v]
         _lib.orc_luminance.argtypes = [P(Light), P(Wall), l, v, v]
+        _lib.orc_connect.argtypes = [P(Grid), P(Field), P(Wall), P(Light), P(Integ), l, v, i, v, v]
         _lib.orc_render.argtypes = [P(Grid), P(Field), P(Camera), P(Wall), P(Light), P(Integ), l, v, i, i,
                                     v, v, v, v]
         _lib.orc_render_cs.argtypes = [P(Grid), v, v, d, P(Camera), P(Wall), P(Light), P(Integ), l, v, i, v, v]
@@ -115,7 +116,8 @@ class _LightHolder:
         self.pattern = np.ascontiguousarray(light.pattern, dtype=np.float32)
         th, tw = self.pattern.shape
         proj = camera_desc(light.proj) if light.proj is not None else Camera()
-        self.desc = Light(light.mode, proj, tw, th, self.pattern.ctypes.data_as(C.POINTER(C.c_float)))
+        self.desc = Light(light.mode, proj, tw, th, self.pattern.ctypes.data_as(C.POINTER(C.c_float)),
+                          int(getattr(light, "connect_iters", 1)))
 
 
 def integ_desc(it) -> Integ:
@@ -210,6 +212,22 @@ def luminance(light, wall, x) -> np.ndarray:
     lh = _LightHolder(light)
     lib().orc_luminance(C.byref(lh.desc), C.byref(wall_desc(wall)), x.shape[0], _ptr(x), _ptr(out))
     return out
+
+
+def connect(scene, x, iters: int = -1, field=None):
+    """Refracted projector connection of wall points x (n, 3): returns (a, y), the aim after
+    `iters` rounds (default: the light's connect_iters) and the wall hit of the projector
+    ray aimed at it."""
+    if field is None:
+        field = field_from_T(scene.grid, scene.T)
+    x = _f64(x).reshape(-1, 3)
+    a = np.empty_like(x)
+    y = np.empty_like(x)
+    lh = _LightHolder(scene.light)
+    lib().orc_connect(C.byref(grid_desc(scene.grid)), C.byref(field.desc), C.byref(wall_desc(scene.wall)),
+                      C.byref(lh.desc), C.byref(integ_desc(scene.integ)), x.shape[0], _ptr(x), int(iters),
+                      _ptr(a), _ptr(y))
+    return a, y
 
 
 # ------------------------------------------------------------------ render

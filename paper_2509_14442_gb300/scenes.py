@@ -89,9 +89,11 @@ class Wall:
 
 @dataclass
 class Light:
-    mode: int                       # 0: texture on the wall, 1: pinhole projector
+    mode: int                       # 0: texture on the wall, 1: pinhole projector (straight
+                                    # connection), 2: projector rays traced through the flow
     pattern: np.ndarray             # (th, tw) float32
-    proj: Optional[Camera] = None   # projector pinhole (mode 1)
+    proj: Optional[Camera] = None   # projector pinhole (modes 1, 2)
+    connect_iters: int = 1          # mode 2: projector rays traced per wall point
 
 
 @dataclass

@@ -502,3 +502,83 @@ def test_quasi_linear_adjoint_matches_complex_step(orc):
         dI, _ = orc.render_cs(sc, dT)
         lhs, rhs = float((gT * dT).sum()), float((w * dI).sum())
         assert abs(lhs - rhs) <= 1e-9 * abs(rhs), (lhs, rhs)
+
+
+# ------------------------------------------------- refracted projector connection, Sec. 2.3
+
+def _refracted_room(n=(16, 16, 12), w=20, h=16, seed=31, iters=1, boost=4.0, pattern=None):
+    """Room scene lit by the projector with its rays traced through the flow; the plume's
+    excess temperature is scaled by `boost` so the projector rays bend visibly."""
+    sc = S.room(n, w, h, 1, seed, pattern_size=64)
+    T = S.T_AMBIENT + boost * (sc.T.astype(np.float64) - S.T_AMBIENT)
+    pat = S.smooth_pattern(64, 64, seed) if pattern is None else pattern
+    return sc.replace(T=T, light=S.Light(2, pat, sc.light.proj, connect_iters=iters))
+
+
+def _wall_points(sc, orc, k=12, seed=0):
+    """Wall points the camera's flow rays actually hit."""
+    hit = orc.render(sc)["hit"].reshape(-1, 2)
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(len(hit), size=k, replace=False)
+    w = sc.wall
+    o, eu, ev = (np.asarray(v, dtype=np.float64) for v in (w.origin, w.eu, w.ev))
+    return o[None] + hit[idx, 0:1] * eu[None] + hit[idx, 1:2] * ev[None]
+
+
+def test_refracted_connection_is_straight_in_a_uniform_medium(orc):
+    sc = _refracted_room()
+    sc = sc.replace(T=np.full(sc.T.shape, S.T_AMBIENT))
+    x = _wall_points(sc, orc)
+    a, y = orc.connect(sc, x, iters=3)
+    np.testing.assert_allclose(a, x, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(y, x, rtol=0, atol=1e-12)
+    I2 = orc.render(sc)["I"]
+    I1 = orc.render(sc.replace(light=S.Light(1, sc.light.pattern, sc.light.proj)))["I"]
+    np.testing.assert_allclose(I2, I1, rtol=1e-12, atol=0)
+
+
+def test_refracted_connection_matches_a_brute_force_search(orc):
+    # the connected aim a* is the wall point whose projector ray lands on x; find it by a
+    # two-level grid search over aims in the wall plane, independent of the aiming rule
+    sc = _refracted_room(boost=8.0)
+    x = _wall_points(sc, orc, k=3, seed=1)
+    a6, y6 = orc.connect(sc, x, iters=6)
+    a1, _ = orc.connect(sc, x, iters=1)
+    w = sc.wall
+    eu, ev = np.asarray(w.eu, dtype=np.float64), np.asarray(w.ev, dtype=np.float64)
+    for j in range(len(x)):
+        delta = np.linalg.norm(a1[j] - x[j])
+        assert delta > 1e-6                                  # the projector rays do bend
+        assert np.linalg.norm(y6[j] - x[j]) < 1e-12          # the aiming rule converges
+        assert np.linalg.norm(a1[j] - a6[j]) < 1e-2 * delta  # one round is nearly there
+        centre, span = x[j].copy(), 2.0 * delta
+        for _ in range(2):
+            g = np.linspace(-span, span, 41)
+            aims = (centre[None, None] + g[:, None, None] * eu[None, None] + g[None, :, None] * ev[None, None])
+            aims = aims.reshape(-1, 3)
+            _, y = orc.connect(sc, aims, iters=0)            # y(a) for each candidate aim
+            best = np.argmin(np.linalg.norm(y - x[j][None], axis=1))
+            centre, span = aims[best], 2.0 * (g[1] - g[0])
+        assert np.linalg.norm(centre - a6[j]) <= 2.0 * span
+
+
+@pytest.mark.parametrize("iters", [1, 2])
+def test_refracted_adjoint_matches_complex_step(orc, iters):
+    sc = _refracted_room(n=(12, 12, 9), w=14, h=12, seed=37, iters=iters)
+    rng = np.random.default_rng(40 + iters)
+    w = rng.standard_normal((12, 14))
+    gT = orc.grad(sc, w)
+    for trial in range(2):
+        dT = rng.standard_normal(sc.T.shape)
+        dI, _ = orc.render_cs(sc, dT)
+        lhs, rhs = float((gT * dT).sum()), float((w * dI).sum())
+        assert abs(lhs - rhs) <= 1e-8 * abs(rhs), (lhs, rhs)
+
+
+def test_refracted_gradient_differs_from_the_straight_connection(orc):
+    # the projector rays' own sensitivity to T is a visible part of dL/dT
+    sc = _refracted_room(n=(12, 12, 9), w=14, h=12, seed=43)
+    w = np.random.default_rng(3).standard_normal((12, 14))
+    g2 = orc.grad(sc, w)
+    g1 = orc.grad(sc.replace(light=S.Light(1, sc.light.pattern, sc.light.proj)), w)
+    assert np.linalg.norm(g2 - g1) > 1e-3 * np.linalg.norm(g1)
