@@ -40,6 +40,12 @@ def quasi(scene):
                                             ckpt_every=scene.integ.ckpt_every))
 
 
+def refracted(scene):
+    """The same scene with the projector's rays traced through the flow (one aiming round)."""
+    L = scene.light
+    return scene.replace(light=S.Light(2, L.pattern, L.proj, connect_iters=1))
+
+
 WORKLOADS = {
     "room_adj": dict(desc="room 256x256x192 plume, 2048^2 camera, 1 spp, forward + adjoint (K=16)",
                      make=lambda seed: S.room_adjoint(seed), adjoint=True),
@@ -50,6 +56,15 @@ WORKLOADS = {
                            make=lambda seed: quasi(S.room_adjoint(seed)), adjoint=True, fwd_bytes=256, adj_bytes=512),
     "room_fwd_quasi": dict(desc="room 128x128x96 plume, 1024^2 camera, 4 jittered spp, quasi-linear forward + I_ref",
                            make=lambda seed: quasi(S.room_forward(seed)), adjoint=False, fwd_bytes=256),
+    # the projector's own rays traced through the flow too (refracted connection, light mode 2):
+    # every camera sample also traces the projector ray aimed at its wall hit; ray-steps
+    # count both rays
+    "room_fwd_refr": dict(desc="room 128x128x96 plume, 1024^2 camera, 4 jittered spp, refracted projector "
+                               "connection, forward + I_ref",
+                          make=lambda seed: refracted(S.room_forward(seed)), adjoint=False),
+    "room_adj_refr": dict(desc="room 256x256x192 plume, 2048^2 camera, 1 spp, refracted projector connection, "
+                               "forward + adjoint (K=16)",
+                          make=lambda seed: refracted(S.room_adjoint(seed)), adjoint=True),
     # small case of the same kernels for profiler captures (not a benchmark line)
     "room_fwd_small": dict(desc="room 128x128x96 plume, 256^2 camera, 4 jittered spp, forward + I_ref",
                            make=lambda seed: S.room((128, 128, 96), 256, 256, 4, seed), adjoint=False),

@@ -108,12 +108,19 @@ typedef struct {
 
 /* Wall luminance (Sec. 2.3): mode 0 -- a tw x th texture covering the wall
  * rectangle [0, size_u] x [0, size_v]; mode 1 -- a pinhole projector `proj`
- * casting a tw x th pattern, connected to the wall point by a straight line.
- * Both are bilinear on texel centres and zero outside the pattern. */
+ * casting a tw x th pattern, connected to the wall point by a straight line;
+ * mode 2 -- the same projector with a refracted connection: the pattern point that
+ * lights wall point x_w is the one whose own ray, traced through the field like a
+ * camera ray, lands on x_w, found by connect_iters (1..16) rounds of aiming
+ * a <- a + (x_w - y(a)) from a = x_w, y(a) the wall hit of the projector ray aimed at a.
+ * Mode 2 renders with the compensated tracers (BOS_PREC_FP32_COMP, BOS_PREC_BF16_COMP);
+ * its backward needs Sharma RKN and connect_iters = 1.  All patterns are bilinear on
+ * texel centres and zero outside.  connect_iters is ignored in modes 0 and 1. */
 typedef struct {
     int mode;
     bos_camera_desc proj;
     int tw, th;
+    int connect_iters;
 } bos_light_desc;
 
 /* Integrator: fixed_steps > 0 gives every ray that many steps, otherwise

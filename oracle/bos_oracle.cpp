@@ -527,18 +527,19 @@ ProjGeom<S> projector_geometry(const Scene& sc, const S aim[3]) {
 // Wall hit y of the projector ray aimed at `aim`: straight to the box, N integrator steps
 // of Eq. 1 inside it (v0 = eta(r_in) d, dt = ell / (N eta(r_in)), as for camera rays), then
 // straight from (r_N, v_N) to the wall plane.  Without a box segment y is the straight hit.
+// Returns the steps taken.
 template <class S>
-void trace_projector(const Scene& sc, const Field<S>& F, const S aim[3], S y[3]) {
+long trace_projector(const Scene& sc, const Field<S>& F, const S aim[3], S y[3]) {
     const orc_wall& w = *sc.w;
     const double* P = sc.L->proj.pos;
     ProjGeom<S> G = projector_geometry(sc, aim);
     if (!G.wall) {
         for (int a = 0; a < 3; ++a) y[a] = aim[a];
-        return;
+        return 0;
     }
     if (!G.traced) {
         for (int a = 0; a < 3; ++a) y[a] = P[a] + G.tw * G.d[a];
-        return;
+        return 0;
     }
     S rin[3], r[3], v[3], eta_in, gd[3];
     for (int a = 0; a < 3; ++a) rin[a] = P[a] + G.t_in * G.d[a];
@@ -555,19 +556,23 @@ void trace_projector(const Scene& sc, const Field<S>& F, const S aim[3], S y[3])
     S qq[3] = {w.origin[0] - r[0], w.origin[1] - r[1], w.origin[2] - r[2]};
     S ts = (qq[0] * w.normal[0] + qq[1] * w.normal[1] + qq[2] * w.normal[2]) / vn;
     for (int a = 0; a < 3; ++a) y[a] = r[a] + ts * v[a];
+    return G.N;
 }
 
 // The wall point whose projector pattern value lights x_w: M rounds of
 // a_{k+1} = a_k + (x_w - y(a_k)) from a_0 = x_w (mode 2; modes 0, 1 return x_w).
+// Returns the projector-ray steps taken.
 template <class S>
-void connect_projector(const Scene& sc, const Field<S>& F, const S xw[3], S a[3]) {
+long connect_projector(const Scene& sc, const Field<S>& F, const S xw[3], S a[3]) {
     for (int c = 0; c < 3; ++c) a[c] = xw[c];
-    if (sc.L->mode != 2) return;
+    if (sc.L->mode != 2) return 0;
+    long steps = 0;
     for (int k = 0; k < sc.L->connect_iters; ++k) {
         S y[3];
-        trace_projector(sc, F, a, y);
+        steps += trace_projector(sc, F, a, y);
         for (int c = 0; c < 3; ++c) a[c] = a[c] + (xw[c] - y[c]);
     }
+    return steps;
 }
 
 // Trace one ray: straight to the box, N integrator steps of Eq. 1 inside it with
@@ -622,7 +627,7 @@ RayOut<S> trace_ray(const Scene& sc, const Field<S>& F, const RayGeom& R, bool s
     if (straight) {
         for (int a = 0; a < 3; ++a) xl[a] = xw[a];
     } else {
-        connect_projector(sc, F, xw, xl);
+        o.N += connect_projector(sc, F, xw, xl);   // steps count the projector rays too
     }
     o.I = luminance<S>(*sc.L, w, xl) * cosw / len;
     wall_coords(w, xw, o.hit);

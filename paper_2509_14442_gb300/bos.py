@@ -58,7 +58,8 @@ class bos_wall_desc(C.Structure):
 
 
 class bos_light_desc(C.Structure):
-    _fields_ = [("mode", C.c_int), ("proj", bos_camera_desc), ("tw", C.c_int), ("th", C.c_int)]
+    _fields_ = [("mode", C.c_int), ("proj", bos_camera_desc), ("tw", C.c_int), ("th", C.c_int),
+                ("connect_iters", C.c_int)]
 
 
 class bos_integrator_desc(C.Structure):
@@ -168,7 +169,7 @@ def wall_desc(w) -> bos_wall_desc:
 def light_desc(L) -> bos_light_desc:
     th, tw = L.pattern.shape
     proj = camera_desc(L.proj) if L.proj is not None else bos_camera_desc()
-    return bos_light_desc(L.mode, proj, tw, th)
+    return bos_light_desc(L.mode, proj, tw, th, int(getattr(L, "connect_iters", 1)))
 
 
 def integ_desc(it) -> bos_integrator_desc:

@@ -28,10 +28,11 @@ constexpr int kAdjWarps = BOS_ADJ_WARPS;   // warps per block
 #define BOS_ACC_SCALAR 0                  // accumulate cell rows with scalar (1) or packed (0) FMAs
 #endif
 #ifndef BOS_ADJ_MIN_BLOCKS
-#define BOS_ADJ_MIN_BLOCKS 4              // resident blocks per SM the register budget is cut for
+#define BOS_ADJ_MIN_BLOCKS 5              // resident blocks per SM the register budget is cut for
 #endif
 constexpr int kRow = 36;              // floats per lane row of the cell accumulators (16-byte aligned rows)
-constexpr int kStageStride = 28;      // floats per lane row of a parked stage (value + 3 derivatives, cell, fractions)
+constexpr int kStageStride = 20;      // floats per lane row of a parked stage (value + 3 derivatives, cell, fractions)
+constexpr int kConnDoubles = 20;      // per-lane shared doubles of the refracted connection's adjoint
 constexpr uint32_t kNoKey = 0xffffffffu;
 
 struct InterpGrad {
@@ -66,10 +67,15 @@ __device__ __forceinline__ InterpGrad trilinear_grad2(const E* s, uint32_t o, fl
 }
 
 struct Stage {
-    int ci[3];
+    uint32_t key;   // node index of the cell's base corner
     float cf[3];
     InterpGrad ig;
 };
+
+template <class E>
+__device__ __forceinline__ uint32_t cell_key_of(const CompField<E>& F, const int ci[3]) {
+    return (uint32_t)ci[0] + (uint32_t)ci[1] * (uint32_t)F.n[0] + (uint32_t)ci[2] * ((uint32_t)F.n[0] * (uint32_t)F.n[1]);
+}
 
 __device__ __forceinline__ void rhs_from(const InterpGrad& ig, float D[3]) {
     float eta = 1.0f + ig.v.x;
@@ -81,27 +87,23 @@ __device__ __forceinline__ void rhs_from(const InterpGrad& ig, float D[3]) {
 template <class E>
 __device__ __forceinline__ void stage_eval(const CompField<E>& F, const long long U[3], const float q[3], BrickCache& bc,
                                            Stage& s) {
-    comp_cell(F, U, q, s.ci, s.cf);
-    uint32_t o = cached_offset(bc, s.ci[0], s.ci[1], s.ci[2]);
+    int ci[3];
+    comp_cell(F, U, q, ci, s.cf);
+    s.key = cell_key_of(F, ci);
+    uint32_t o = cached_offset(bc, ci[0], ci[1], ci[2]);
     s.ig = trilinear_grad2(F.store, o, s.cf[0], s.cf[1], s.cf[2]);
 }
 
-#ifndef BOS_ADJ_STAGE_F4
-#define BOS_ADJ_STAGE_F4 1                // parked stage records as float4 rows (1) or scalar columns (0)
-#endif
-
-#if BOS_ADJ_STAGE_F4
-// Park / restore a stage record in the warp's shared buffer: one row of kStageStride
-// floats per lane, accessed as float4 (the stride keeps 8 consecutive lanes on distinct
-// banks, so the 128-bit accesses are conflict-free).
+// Park / restore a stage record in the warp's shared buffer: one row of kStageStride = 20
+// floats per lane, accessed as five float4 (a stride of 20 floats puts 8 consecutive
+// lanes on distinct bank quadruples, so the 128-bit accesses are conflict-free).
 __device__ __forceinline__ void put_stage(float* b, int lane, const Stage& s) {
     float4* row = reinterpret_cast<float4*>(b + lane * kStageStride);
     row[0] = s.ig.v;
     row[1] = s.ig.d0;
     row[2] = s.ig.d1;
     row[3] = s.ig.d2;
-    row[4] = make_float4(__int_as_float(s.ci[0]), __int_as_float(s.ci[1]), __int_as_float(s.ci[2]), s.cf[0]);
-    row[5] = make_float4(s.cf[1], s.cf[2], 0.0f, 0.0f);
+    row[4] = make_float4(__uint_as_float(s.key), s.cf[0], s.cf[1], s.cf[2]);
 }
 __device__ __forceinline__ void get_stage(const float* b, int lane, Stage& s) {
     const float4* row = reinterpret_cast<const float4*>(b + lane * kStageStride);
@@ -109,38 +111,12 @@ __device__ __forceinline__ void get_stage(const float* b, int lane, Stage& s) {
     s.ig.d0 = row[1];
     s.ig.d1 = row[2];
     s.ig.d2 = row[3];
-    const float4 a = row[4], c = row[5];
-    s.ci[0] = __float_as_int(a.x);
-    s.ci[1] = __float_as_int(a.y);
-    s.ci[2] = __float_as_int(a.z);
-    s.cf[0] = a.w;
-    s.cf[1] = c.x;
-    s.cf[2] = c.y;
+    const float4 a = row[4];
+    s.key = __float_as_uint(a.x);
+    s.cf[0] = a.y;
+    s.cf[1] = a.z;
+    s.cf[2] = a.w;
 }
-#else
-// Park / restore a stage record in the warp's shared buffer: column `lane` of a
-// [22][32] block (conflict-free scalar accesses).
-__device__ __forceinline__ void put_stage(float* b, int lane, const Stage& s) {
-    const float* v = reinterpret_cast<const float*>(&s.ig);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) b[i * 32 + lane] = v[i];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        b[(16 + a) * 32 + lane] = __int_as_float(s.ci[a]);
-        b[(19 + a) * 32 + lane] = s.cf[a];
-    }
-}
-__device__ __forceinline__ void get_stage(const float* b, int lane, Stage& s) {
-    float* v = reinterpret_cast<float*>(&s.ig);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = b[i * 32 + lane];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        s.ci[a] = __float_as_int(b[(16 + a) * 32 + lane]);
-        s.cf[a] = b[(19 + a) * 32 + lane];
-    }
-}
-#endif
 
 // Adjoint of D = (1 + deta) grad at a stage point: given Db, the position adjoint (metres)
 // and the per-corner record Q (corner c receives w_c Q).
@@ -208,10 +184,10 @@ __device__ __forceinline__ void flush_rows(float* rows, bool flag, CellAcc& ca, 
 }
 
 // Warp-collective: add w_c(cf) Q to the lane's cell row (flushing first where the cell changes).
-__device__ __forceinline__ void accumulate(float* rows, bool act, const int ci[3], const float cf[3], float4 Q,
+__device__ __forceinline__ void accumulate(float* rows, bool act, uint32_t cell, const float cf[3], float4 Q,
                                            CellAcc& ca, float* acc, int nx, int nxy) {
     const int lane = threadIdx.x & 31;
-    const uint32_t key = act ? (uint32_t)ci[0] + (uint32_t)ci[1] * (uint32_t)nx + (uint32_t)ci[2] * (uint32_t)nxy : kNoKey;
+    const uint32_t key = act ? cell : kNoKey;
     flush_rows(rows, act && ca.key != kNoKey && ca.key != key, ca, acc, nx, nxy);
     if (act) {
         ca.key = key;
@@ -246,9 +222,11 @@ __device__ __forceinline__ void accumulate(float* rows, bool act, const int ci[3
 
 // Adjoint of the wall epilogue for seed Ib = dL/dI of this ray: returns the adjoints of
 // (r_N, v_N) and of the path length (which the per-step lengths feed).
+// With the refracted projector connection the luminance is read at xl (not at x_w) and
+// its sensitivity to x_w arrives as xlb; otherwise xl = xlb = nullptr.
 __device__ __forceinline__ void wall_adjoint(const SceneDev& S, const double rN[3], const double vN[3],
                                              double len_before, double Ib, double rb[3], double vb[3],
-                                             double& lenb) {
+                                             double& lenb, const double* xl = nullptr, const double* xlb = nullptr) {
     const WallDev& w = S.w;
     rb[0] = rb[1] = rb[2] = vb[0] = vb[1] = vb[2] = 0.0;
     lenb = 0.0;
@@ -262,13 +240,13 @@ __device__ __forceinline__ void wall_adjoint(const SceneDev& S, const double rN[
     double len = len_before + ts * vl;              // signed continuation x_w - r_N = t* v
     double cw = vn / vl;
     double gL[3];
-    double Lw = wall_luminance(S.L, w, xw, gL);
+    double Lw = xl ? wall_luminance(S.L, w, xl) : wall_luminance(S.L, w, xw, gL);
     double Lb = Ib * cw / len, cb = Ib * Lw / len;
     lenb = -Ib * Lw * cw / (len * len);
     double xwb[3];
     for (int a = 0; a < 3; ++a) {
         double u = vN[a] / vl;                      // d(t* |v|) through x_w = r_N + t* v
-        xwb[a] = Lb * gL[a] + lenb * u;
+        xwb[a] = (xl ? xlb[a] : Lb * gL[a]) + lenb * u;
         rb[a] = -lenb * u;
         vb[a] = cb * (w.normal[a] / vl - vn * vN[a] / (vl * vl * vl));
     }
@@ -279,14 +257,57 @@ __device__ __forceinline__ void wall_adjoint(const SceneDev& S, const double rN[
     }
 }
 
+// Adjoint of a projector ray's wall hit y = r_N + t* v_N, t* = ((o - r_N) . n) / (v_N . n),
+// for the seed yb.
+__device__ __forceinline__ void hit_adjoint(const SceneDev& S, const double rN[3], const double vN[3],
+                                            const double yb[3], double rb[3], double vb[3]) {
+    const WallDev& w = S.w;
+    rb[0] = rb[1] = rb[2] = vb[0] = vb[1] = vb[2] = 0.0;
+    double vn = vN[0] * w.normal[0] + vN[1] * w.normal[1] + vN[2] * w.normal[2];
+    if (!(vn > 0.0)) return;
+    double q[3] = {w.origin[0] - rN[0], w.origin[1] - rN[1], w.origin[2] - rN[2]};
+    double ts = (q[0] * w.normal[0] + q[1] * w.normal[1] + q[2] * w.normal[2]) / vn;
+    double tb = yb[0] * vN[0] + yb[1] * vN[1] + yb[2] * vN[2];
+    for (int a = 0; a < 3; ++a) {
+        rb[a] = yb[a] - tb * w.normal[a] / vn;
+        vb[a] = ts * rb[a];
+    }
+}
+
+// d/d aim of the straight projector ray's wall hit y = P + t_w d (d = q / |q|,
+// t_w = ((o - P) . n) / (d . n)), for the seed yb.
+__device__ __forceinline__ void straight_aim_adjoint(const SceneDev& S, const Ray& Rp, double nq, const double yb[3],
+                                                     double ab[3]) {
+    const WallDev& w = S.w;
+    double den = Rp.d[0] * w.normal[0] + Rp.d[1] * w.normal[1] + Rp.d[2] * w.normal[2];
+    double twb = yb[0] * Rp.d[0] + yb[1] * Rp.d[1] + yb[2] * Rp.d[2];
+    double db[3];
+    for (int a = 0; a < 3; ++a) db[a] = Rp.tw * yb[a] - twb * Rp.tw * w.normal[a] / den;
+    double dd = db[0] * Rp.d[0] + db[1] * Rp.d[1] + db[2] * Rp.d[2];
+    for (int a = 0; a < 3; ++a) ab[a] = (db[a] - dd * Rp.d[a]) / nq;
+}
+
 __host__ __device__ constexpr size_t adj_warp_floats(int K) {
     return (size_t)K * 6 * 32 + 32 * kRow + 2 * 32 * kStageStride;
 }
 
-template <class E>
+template <class E, bool CONN_T>
 __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
+    constexpr bool CONN = CONN_T;
     extern __shared__ float4 smem4[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // Refracted connection: values that live across a whole ray reversal are parked in
+    // shared memory (per lane: a_1, dL/dx_w, the projector seed, the projector's wall-seed
+    // adjoints, the straight-step adjoint sum and |q|) rather than held in registers
+    // through the hot loop.
+    __shared__ double conn_sh[CONN ? kAdjWarps * 32 * kConnDoubles : 1];
+    double* const xlum = conn_sh + (CONN ? (warp * 32 + lane) * kConnDoubles : 0);
+    double* const xlb = xlum + 3;
+    double* const ybar = xlum + 6;
+    double* const drbw = xlum + 9;
+    double* const dvbw = xlum + 12;
+    double* const tpb = xlum + 15;
+    double* const nqp = xlum + 18;
     const int K = ck.every;
     float* st_buf = reinterpret_cast<float*>(smem4) + (size_t)warp * adj_warp_floats(K);   // [K][6][32]
     float* rows = st_buf + (size_t)K * 6 * 32;                                             // [32][kRow]
@@ -326,16 +347,64 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                 R = ray_setup(S, px, py, s);
                 Ib = (double)adj.dLdI[(size_t)tp.out] / spp;
             }
-            act = act && R.wall && R.N > 0 && Ib != 0.0;
+            const bool act0 = act && R.wall && R.N >= 0 && Ib != 0.0;
+            // Refracted projector connection (light mode 2, one aiming round): the luminance is
+            // read at a_1 = 2 x_w - y(x_w), y the wall hit of the projector ray aimed at x_w.
+            // Pass 0 reverses that projector ray for the seed -dL/da_1 and turns its entry state
+            // into dL/d aim; pass 1 reverses the camera ray with dL/dx_w = 2 dL/da_1 + dL/d aim.
+            Ray Rp;
+            Rp.N = 0;
+            Rp.wall = false;
+            bool pact = false;
+            if constexpr (CONN) {
+                for (int a = 0; a < 3; ++a) xlum[a] = xlb[a] = ybar[a] = 0.0;
+                nqp[0] = 1.0;
+                if (act0) {
+                    const float4 c0 = ck.conn[2 * slot], c1 = ck.conn[2 * slot + 1];
+                    const float dxf[3] = {c0.x, c0.y, c0.z};
+                    double xref[3], gL[3], q[3];
+                    for (int a = 0; a < 3; ++a) {
+                        xref[a] = S.cam.pos[a] + R.tw * R.d[a];
+                        xlum[a] = xref[a] + ((double)dxf[a] - (double)(&c1.x)[a]);
+                    }
+                    const double Lb = Ib * (double)c0.w;
+                    wall_luminance(S.L, S.w, xlum, gL);
+                    for (int a = 0; a < 3; ++a) {
+                        ybar[a] = -Lb * gL[a];
+                        xlb[a] = 2.0 * Lb * gL[a];
+                        q[a] = (xref[a] - S.L.proj.pos[a]) + (double)dxf[a];
+                    }
+                    nqp[0] = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+                    Rp = projector_setup(S, xref, dxf);
+                    const bool seeded = ybar[0] != 0.0 || ybar[1] != 0.0 || ybar[2] != 0.0;
+                    if (!Rp.wall) {                 // y = aim
+                        for (int a = 0; a < 3; ++a) xlb[a] += ybar[a];
+                    } else if (Rp.N <= 0) {         // straight projector ray
+                        double ab[3];
+                        straight_aim_adjoint(S, Rp, nqp[0], ybar, ab);
+                        for (int a = 0; a < 3; ++a) xlb[a] += ab[a];
+                    } else {
+                        pact = seeded;
+                    }
+                }
+            }
+            for (int pass = CONN ? 0 : 1; pass < 2; ++pass) {
+            const bool proj = CONN && pass == 0;
+            const Ray& RR = proj ? Rp : R;
+            const double* rs = proj ? S.L.proj.pos : S.cam.pos;
+            const float4* cstate = proj ? ck.pstate : ck.state;
+            act = proj ? pact : (act0 && R.N > 0);
             CompState st0;
             CompConst k;
             double eta_in = 1.0, rin[3] = {0, 0, 0};
-            if (act) comp_setup(S, F, R, st0, k, eta_in, rin);
-            const int N = act ? R.N : 0;
+            if (act) comp_setup(S, F, rs, RR, st0, k, eta_in, rin);
+            const int N = act ? RR.N : 0;
             const int nseg = (N + K - 1) / K;
             const int nseg_max = __reduce_max_sync(0xffffffffu, (unsigned)nseg);
             float rb[3] = {0, 0, 0}, vb[3] = {0, 0, 0}, dtb = 0.0f, lenb = 0.0f;
             double etab = 0.0;
+            if constexpr (CONN)
+                for (int a = 0; a < 3; ++a) tpb[a] = 0.0;
             const float dt = act ? k.dt : 0.0f;
             BrickCache bc = {kNoKey, 0u};
             for (int c = nseg_max - 1; c >= 0; --c) {
@@ -345,9 +414,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                 // ---- recompute the segment from its checkpoint, keeping each step's state
                 if (seg) {
                     CompState st;
-                    const float4 s0 = ck.state[((size_t)c * 3 + 0) * ck.nrays + slot];
-                    const float4 s1 = ck.state[((size_t)c * 3 + 1) * ck.nrays + slot];
-                    const float4 s2 = ck.state[((size_t)c * 3 + 2) * ck.nrays + slot];
+                    const float4 s0 = cstate[((size_t)c * 3 + 0) * ck.nrays + slot];
+                    const float4 s1 = cstate[((size_t)c * 3 + 1) * ck.nrays + slot];
+                    const float4 s2 = cstate[((size_t)c * 3 + 2) * ck.nrays + slot];
                     st.dr[0] = s0.x; st.dr[1] = s0.y; st.dr[2] = s0.z;
                     st.dv[0] = s1.x; st.dv[1] = s1.y; st.dv[2] = s1.z;
                     st.cv[0] = s2.x; st.cv[1] = s2.y; st.cv[2] = s2.z;
@@ -362,35 +431,48 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                     }
                     if (c == nseg - 1) {
                         // the lane's last segment: start from the adjoint of the wall epilogue
-                        double rN[3], vN[3], drb[3], dvb[3], lb;
+                        double rN[3], vN[3], drb[3], dvb[3], lb = 0.0;
                         for (int a = 0; a < 3; ++a) {
-                            rN[a] = rin[a] + R.ell * R.d[a] + ((double)st.dr[a] - (double)st.cr[a]);
-                            vN[a] = eta_in * R.d[a] + ((double)st.dv[a] - (double)st.cv[a]);
+                            rN[a] = rin[a] + RR.ell * RR.d[a] + ((double)st.dr[a] - (double)st.cr[a]);
+                            vN[a] = eta_in * RR.d[a] + ((double)st.dv[a] - (double)st.cv[a]);
                         }
-                        double len_before = R.t_in + R.ell + (double)ck.excess[slot];
-                        wall_adjoint(S, rN, vN, len_before, Ib, drb, dvb, lb);
+                        if (proj) {
+                            hit_adjoint(S, rN, vN, ybar, drb, dvb);
+                            for (int a = 0; a < 3; ++a) {
+                                drbw[a] = drb[a];
+                                dvbw[a] = dvb[a];
+                            }
+                        } else {
+                            double len_before = R.t_in + R.ell + (double)ck.excess[slot];
+                            wall_adjoint(S, rN, vN, len_before, Ib, drb, dvb, lb, CONN ? xlum : nullptr,
+                                         CONN ? xlb : nullptr);
+                        }
                         for (int a = 0; a < 3; ++a) {
                             rb[a] = (float)drb[a];
                             vb[a] = (float)dvb[a];
                         }
                         lenb = (float)lb;
-                        etab += dvb[0] * R.d[0] + dvb[1] * R.d[1] + dvb[2] * R.d[2];
+                        etab += dvb[0] * RR.d[0] + dvb[1] * RR.d[1] + dvb[2] * RR.d[2];
                     }
                 }
                 __syncwarp();
+                const float rseg[3] = {rb[0], rb[1], rb[2]};   // rb before this segment's steps
                 // ---- reverse the segment's steps
                 const int n_hi = __reduce_max_sync(0xffffffffu, (unsigned)(seg ? n1 : 0));
+                float tps[3] = {0.0f, 0.0f, 0.0f};   // sum over the segment's stages of (t / dt_step) pb
                 for (int n = n_hi - 1; n >= n0; --n) {
                     const bool a_ = seg && n < n1;
                     Stage s3;
                     float A[3] = {0, 0, 0}, B[3] = {0, 0, 0}, dvv[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+                    float dr[3] = {0, 0, 0};
+                    long long U[3], U2[3];
                     float D1[3] = {0, 0, 0}, D2[3] = {0, 0, 0}, D3[3] = {0, 0, 0};
                     if (a_) {
                         // recompute the step's three stages (value and gradient of the field)
                         const float* p = st_buf + (size_t)(n - n0) * 6 * 32 + lane;
-                        const float dr[3] = {p[0], p[32], p[64]};
+                        dr[0] = p[0]; dr[1] = p[32]; dr[2] = p[64];
                         dvv[0] = p[96]; dvv[1] = p[128]; dvv[2] = p[160];
-                        long long U[3], U2[3], U3[3];
+                        long long U3[3];
                         for (int a = 0; a < 3; ++a) {
                             U[a] = st0.U[a] + (long long)n * k.dU[a];
                             U2[a] = U[a] + k.dUh[a];
@@ -439,7 +521,11 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                         Db[a] = dt * Cb[a];
                     }
                     if (a_) rhs_adjoint(F, s3.ig, Db, pb, Q);
-                    accumulate(rows, a_, s3.ci, s3.cf, Q, ca, acc, nx, nxy);
+                    accumulate(rows, a_, s3.key, s3.cf, Q, ca, acc, nx, nxy);
+                    if constexpr (CONN) {
+                        const float tn = (float)(n + 1 - n0);
+                        for (int a = 0; a < 3; ++a) tps[a] += tn * pb[a];
+                    }
                     for (int a = 0; a < 3; ++a) {
                         rn_[a] += pb[a];
                         vn_[a] += dt * pb[a];
@@ -456,7 +542,11 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                         get_stage(stg + 32 * kStageStride, lane, s2);
                         rhs_adjoint(F, s2.ig, Db, pb, Q);
                     }
-                    accumulate(rows, a_, s2.ci, s2.cf, Q, ca, acc, nx, nxy);
+                    accumulate(rows, a_, s2.key, s2.cf, Q, ca, acc, nx, nxy);
+                    if constexpr (CONN) {
+                        const float tn = (float)(n - n0) + 0.5f;
+                        for (int a = 0; a < 3; ++a) tps[a] += tn * pb[a];
+                    }
                     for (int a = 0; a < 3; ++a) {
                         rn_[a] += pb[a];
                         vn_[a] += (0.5f * dt) * pb[a];
@@ -473,13 +563,21 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                         get_stage(stg, lane, s1);
                         rhs_adjoint(F, s1.ig, Db, pb, Q);
                     }
-                    accumulate(rows, a_, s1.ci, s1.cf, Q, ca, acc, nx, nxy);
+                    accumulate(rows, a_, s1.key, s1.cf, Q, ca, acc, nx, nxy);
+                    if constexpr (CONN) {
+                        const float tn = (float)(n - n0);
+                        for (int a = 0; a < 3; ++a) tps[a] += tn * pb[a];
+                    }
                     if (a_) {
                         for (int a = 0; a < 3; ++a) {
                             rb[a] = rn_[a] + pb[a] - lenb * u[a];
                             vb[a] = vn_[a];
                         }
                     }
+                }
+                if constexpr (CONN) {
+                    if (proj && seg)
+                        for (int a = 0; a < 3; ++a) tpb[a] += (double)tps[a] + (double)n0 * (double)(rb[a] - rseg[a]);
                 }
                 __syncwarp();
             }
@@ -491,7 +589,40 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                 const float zero[3] = {0, 0, 0};
                 comp_cell(F, st0.U, zero, ci, cf);
             }
-            accumulate(rows, act, ci, cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), ca, acc, nx, nxy);
+            accumulate(rows, act, cell_key_of(F, ci), cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), ca, acc, nx, nxy);
+            if constexpr (CONN) {
+                if (proj && act) {
+                    // the projector ray's entry state as a function of its aim: r_in = P + t_in d,
+                    // v0 = eta_in d (base of v_N), straight step (ell/N) d, dt = ell / (N eta_in),
+                    // eta_in = 1 + deta(r_in), d = q / |q|, t_in and t_end on slab faces or the wall
+                    const double Nd = (double)RR.N, ds = RR.ell / Nd;
+                    Stage se;
+                    const float zero[3] = {0, 0, 0};
+                    stage_eval(F, st0.U, zero, bc, se);
+                    const double ge[3] = {(double)se.ig.d0.x * (double)F.inv_h[0], (double)se.ig.d1.x * (double)F.inv_h[1],
+                                          (double)se.ig.d2.x * (double)F.inv_h[2]};
+                    double dSb[3], rbi[3], db[3];
+                    for (int a = 0; a < 3; ++a) {
+                        dSb[a] = tpb[a] + Nd * drbw[a];
+                        rbi[a] = (double)rb[a] + etab * ge[a];
+                        db[a] = eta_in * dvbw[a] + ds * dSb[a] + RR.t_in * rbi[a];
+                    }
+                    const double ellb = (double)dtb / (Nd * eta_in) +
+                                        (RR.d[0] * dSb[0] + RR.d[1] * dSb[1] + RR.d[2] * dSb[2]) / Nd;
+                    const double tinb = RR.d[0] * rbi[0] + RR.d[1] * rbi[1] + RR.d[2] * rbi[2] - ellb;
+                    if (RR.in_axis >= 0) db[RR.in_axis] += tinb * (-RR.t_in / RR.d[RR.in_axis]);
+                    if (RR.out_axis == 3) {
+                        const double den = RR.d[0] * S.w.normal[0] + RR.d[1] * S.w.normal[1] + RR.d[2] * S.w.normal[2];
+                        for (int a = 0; a < 3; ++a) db[a] += ellb * (-RR.tw * S.w.normal[a] / den);
+                    } else {
+                        const int oa = RR.out_axis;
+                        db[oa] += ellb * (-(RR.t_in + RR.ell) / RR.d[oa]);
+                    }
+                    const double dd = db[0] * RR.d[0] + db[1] * RR.d[1] + db[2] * RR.d[2];
+                    for (int a = 0; a < 3; ++a) xlb[a] += (db[a] - dd * RR.d[a]) / nqp[0];
+                }
+            }
+            }   // passes
         }
     }
     flush_rows(rows, ca.key != kNoKey, ca, acc, nx, nxy);
@@ -554,7 +685,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_quasi_kernel(SceneDev 
             float rb[3] = {0, 0, 0}, vbN[3] = {0, 0, 0}, lenb = 0.0f, usum[3] = {0, 0, 0};
             double etab = 0.0;
             if (act) {
-                comp_setup(S, F, R, st, k, eta_in, rin);
+                comp_setup(S, F, S.cam.pos, R, st, k, eta_in, rin);
                 const float4 s0 = ck.state[0 * ck.nrays + slot];
                 const float4 s1 = ck.state[1 * ck.nrays + slot];
                 const float4 s2 = ck.state[2 * ck.nrays + slot];
@@ -634,23 +765,23 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_quasi_kernel(SceneDev 
                 float pb[3];
                 float4 Q = make_float4(0, 0, 0, 0);
                 if (a_) rhs_adjoint(F, p0.ig, Db0, pb, Q);
-                accumulate(rows, a_, p0.ci, p0.cf, Q, ca, acc, nx, nxy);
+                accumulate(rows, a_, p0.key, p0.cf, Q, ca, acc, nx, nxy);
                 if (a_) rhs_adjoint(F, pm.ig, Dbm, pb, Q);
-                accumulate(rows, a_, pm.ci, pm.cf, Q, ca, acc, nx, nxy);
+                accumulate(rows, a_, pm.key, pm.cf, Q, ca, acc, nx, nxy);
                 if (a_) p0 = pe;
             }
             // the end sample of the last step, then eta_in = 1 + deta(r_in)
             float pb[3];
             float4 Q = make_float4(0, 0, 0, 0);
             if (act) rhs_adjoint(F, p0.ig, carry, pb, Q);
-            accumulate(rows, act, p0.ci, p0.cf, Q, ca, acc, nx, nxy);
+            accumulate(rows, act, p0.key, p0.cf, Q, ca, acc, nx, nxy);
             int ci[3] = {0, 0, 0};
             float cf[3] = {0, 0, 0};
             if (act) {
                 etab -= (double)dtb * (double)dt / eta_in;
                 comp_cell(F, st.U, zero, ci, cf);
             }
-            accumulate(rows, act, ci, cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), ca, acc, nx, nxy);
+            accumulate(rows, act, cell_key_of(F, ci), cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), ca, acc, nx, nxy);
         }
     }
     flush_rows(rows, ca.key != kNoKey, ca, acc, nx, nxy);
@@ -682,18 +813,31 @@ __global__ void gradient_kernel(GridDev g, const float4* __restrict__ acc, const
     }
 }
 
+template <class E, bool CONN>
+static cudaError_t launch_adjoint_c(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
+                                    int num_sms, cudaStream_t st) {
+    size_t smem = (size_t)kAdjWarps * adj_warp_floats(ck.every) * sizeof(float);
+    cudaError_t e =
+        cudaFuncSetAttribute(adjoint_kernel<E, CONN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel<E, CONN>, kAdjWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    adjoint_kernel<E, CONN><<<num_sms * per_sm, kAdjWarps * 32, smem, st>>>(S, ck, adj, w);
+    return cudaGetLastError();
+}
+
+// The refracted projector connection (light mode 2) reverses each sample's projector ray
+// too; it has its own instantiation so that the other modes do not carry it.
 template <class E>
 static cudaError_t launch_adjoint_t(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
                                     int num_sms, cudaStream_t st) {
-    size_t smem = (size_t)kAdjWarps * adj_warp_floats(ck.every) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel<E>, kAdjWarps * 32, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    adjoint_kernel<E><<<num_sms * per_sm, kAdjWarps * 32, smem, st>>>(S, ck, adj, w);
-    return cudaGetLastError();
+    if (S.L.mode == 2) {
+        if (ck.pstate == nullptr || ck.conn == nullptr) return cudaErrorInvalidValue;
+        return launch_adjoint_c<E, true>(S, ck, adj, w, num_sms, st);
+    }
+    return launch_adjoint_c<E, false>(S, ck, adj, w, num_sms, st);
 }
 
 template <class E>

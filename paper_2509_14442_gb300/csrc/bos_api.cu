@@ -116,6 +116,10 @@ struct bos_ctx {
     size_t ckpt_bytes = 0;
     float* excess = nullptr;
     size_t excess_bytes = 0;
+    float4* pckpt = nullptr;        // projector-ray checkpoints (light mode 2)
+    size_t pckpt_bytes = 0;
+    float4* conn = nullptr;         // per-slot connection records (light mode 2)
+    size_t conn_bytes = 0;
     bool saved = false;
     CkptDev saved_ck{};
     int saved_mode = 0;
@@ -225,6 +229,13 @@ RayConst ray_const_of(const SceneDev& S) {
     double hmin = S.g.h[0] < S.g.h[1] ? S.g.h[0] : S.g.h[1];
     hmin = S.g.h[2] < hmin ? S.g.h[2] : hmin;
     rc.step = S.it.max_step_vox * hmin;
+    const double* pp = S.L.proj.pos;
+    for (int a = 0; a < 3; ++a) {
+        rc.plo_m[a] = S.g.origin[a] - pp[a];
+        rc.phi_m[a] = (S.g.origin[a] + S.g.extent[a]) - pp[a];
+    }
+    const double pq[3] = {S.w.origin[0] - pp[0], S.w.origin[1] - pp[1], S.w.origin[2] - pp[2]};
+    rc.pqn = (pq[0] * S.w.normal[0] + pq[1] * S.w.normal[1]) + pq[2] * S.w.normal[2];
     return rc;
 }
 
@@ -232,7 +243,7 @@ RayConst ray_const_of(const SceneDev& S) {
 // context's grid, geometry and saved render.
 void ctx_bind_arena(bos_ctx* c, void* base, size_t bytes, cudaStream_t stream) {
     if (!c->arena) {
-        void* bufs[] = {c->store, c->ckpt, c->excess, c->acc};
+        void* bufs[] = {c->store, c->ckpt, c->excess, c->acc, c->pckpt, c->conn};
         for (void* p : bufs)
             if (p) cudaFree(p);
         c->bytes = 256;
@@ -241,7 +252,9 @@ void ctx_bind_arena(bos_ctx* c, void* base, size_t bytes, cudaStream_t stream) {
     c->ckpt = nullptr;
     c->excess = nullptr;
     c->acc = nullptr;
-    c->store_bytes = c->ckpt_bytes = c->excess_bytes = c->acc_bytes = 0;
+    c->pckpt = nullptr;
+    c->conn = nullptr;
+    c->store_bytes = c->ckpt_bytes = c->excess_bytes = c->acc_bytes = c->pckpt_bytes = c->conn_bytes = 0;
     c->arena = (char*)base;
     c->arena_size = bytes;
     c->arena_used = 0;
@@ -251,7 +264,8 @@ void ctx_bind_arena(bos_ctx* c, void* base, size_t bytes, cudaStream_t stream) {
 
 // Device bytes a render (and, with adjoint != 0, its backward) needs, as carved from an
 // arena: the same sizes render_impl / bos_set_grid / bos_backward allocate.
-size_t request_bytes(const bos_grid_desc& g, const bos_camera_desc& cam, const bos_integrator_desc& it, int adjoint) {
+size_t request_bytes(const bos_grid_desc& g, const bos_camera_desc& cam, const bos_light_desc& light,
+                     const bos_integrator_desc& it, int adjoint) {
     uint32_t nb[3] = {(uint32_t)(g.nx - 1 + kBrick - 1) / kBrick, (uint32_t)(g.ny - 1 + kBrick - 1) / kBrick,
                       (uint32_t)(g.nz - 1 + kBrick - 1) / kBrick};
     size_t slots = (size_t)morton3(nb[0] - 1, nb[1] - 1, nb[2] - 1) + 1;
@@ -271,6 +285,10 @@ size_t request_bytes(const bos_grid_desc& g, const bos_camera_desc& cam, const b
         size_t max_ckpt = it.integrator == 2 ? 1 : (size_t)((bound + it.ckpt_every - 1) / it.ckpt_every);
         bytes += align_up(max_ckpt * 3 * nslots * sizeof(float4));
         bytes += align_up(nslots * sizeof(float));
+        if (light.mode == 2) {   // the projector rays' checkpoints and the connection records
+            bytes += align_up(max_ckpt * 3 * nslots * sizeof(float4));
+            bytes += align_up(2 * nslots * sizeof(float4));
+        }
         bytes += align_up((size_t)g.nx * g.ny * g.nz * sizeof(float4));
     }
     return bytes;
@@ -337,7 +355,7 @@ bos_status_t bos_destroy(bos_ctx* c) {
     DeviceGuard dg(c->device);
     if (c->small) cudaFree(c->small);
     if (!c->arena) {
-        void* bufs[] = {c->store, c->ckpt, c->excess, c->acc};
+        void* bufs[] = {c->store, c->ckpt, c->excess, c->acc, c->pckpt, c->conn};
         for (void* p : bufs)
             if (p) cudaFree(p);
     }
@@ -399,10 +417,12 @@ bos_status_t bos_set_geometry(bos_ctx* c, const bos_camera_desc* cam, const bos_
     if (!finite3(wall->origin) || !unit3(wall->eu) || !unit3(wall->ev) || !unit3(wall->normal) ||
         !(wall->size_u > 0) || !(wall->size_v > 0))
         return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: wall needs a finite origin, unit axes and sizes > 0");
-    if (light->mode != 0 && light->mode != 1) return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: light mode");
+    if (light->mode < 0 || light->mode > 2) return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: light mode");
     if (light->tw <= 0 || light->th <= 0 || !pattern_dev)
         return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: pattern size must be > 0 and pattern non-NULL");
-    if (light->mode == 1) {
+    if (light->mode == 2 && (light->connect_iters < 1 || light->connect_iters > 16))
+        return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: connect_iters must be in [1, 16]");
+    if (light->mode >= 1) {
         s = check_camera(&light->proj, "bos_set_geometry: projector");
         if (s != BOS_OK) return s;
     }
@@ -425,6 +445,7 @@ bos_status_t bos_set_geometry(bos_ctx* c, const bos_camera_desc* cam, const bos_
     c->light.tw = light->tw;
     c->light.th = light->th;
     c->light.pattern = pattern_dev;
+    c->light.connect_iters = light->mode == 2 ? light->connect_iters : 0;
     c->integ.fixed_steps = it->fixed_steps;
     c->integ.max_step_vox = it->max_step_vox;
     c->integ.integrator = it->integrator;
@@ -438,6 +459,8 @@ static bos_status_t render_impl(bos_ctx* c, int mode, float* I, float* disp, dou
                                 const int32_t* pix = nullptr, long long npix = 0) {
     if (!c || !I) return fail(BOS_ERR_INVALID_ARG, "bos_render: NULL context or I");
     if (!c->has_grid || !c->has_geom) return fail(BOS_ERR_NOT_READY, "bos_render: set_grid and set_geometry first");
+    if (c->light.mode == 2 && (mode == 3 || mode == 4))
+        return fail(BOS_ERR_UNIMPLEMENTED, "bos_render: the refracted projector connection needs FP32_COMP or BF16_COMP");
     DeviceGuard dg(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     c->integ.max_steps = step_bound(c);
@@ -465,6 +488,18 @@ static bos_status_t render_impl(bos_ctx* c, int mode, float* I, float* disp, dou
         if (s != BOS_OK) return s;
         ck.state = c->ckpt;
         ck.excess = c->excess;
+        if (c->light.mode == 2) {
+            if (c->integ.integrator != 0 || c->light.connect_iters != 1)
+                return fail(BOS_ERR_UNIMPLEMENTED,
+                            "bos_render: the refracted connection's adjoint needs Sharma RKN and connect_iters = 1");
+            s = dev_alloc(c, (void**)&c->pckpt, &c->pckpt_bytes, want, "bos_render: projector checkpoints");
+            if (s != BOS_OK) return s;
+            s = dev_alloc(c, (void**)&c->conn, &c->conn_bytes, 2 * (size_t)ck.nrays * sizeof(float4),
+                          "bos_render: connection records");
+            if (s != BOS_OK) return s;
+            ck.pstate = c->pckpt;
+            ck.conn = c->conn;
+        }
     }
     cudaError_t e = cudaMemsetAsync(c->small, 0, 4, st);               // tile counter
     if (e == cudaSuccess && mode != 0) e = cudaMemsetAsync(c->steps, 0, 8, st);   // the reference traces nothing

@@ -158,13 +158,14 @@ __device__ __forceinline__ void comp_step(const CompField<E>& F, CompState& st, 
 __device__ __forceinline__ long long to_fixed(double u, double scale) { return __double2ll_rn(u * scale); }
 
 // Set-up shared by the forward and the adjoint: fixed-point line, eta at entry, dt.
+// Set-up of the compensated state of the ray rs + t d (camera or projector pinhole rs).
 template <class E>
-__device__ __forceinline__ void comp_setup(const SceneDev& S, const CompField<E>& F, const Ray& R, CompState& st,
-                                           CompConst& k, double& eta_in, double rin[3]) {
+__device__ __forceinline__ void comp_setup(const SceneDev& S, const CompField<E>& F, const double rs[3], const Ray& R,
+                                           CompState& st, CompConst& k, double& eta_in, double rin[3]) {
     const GridDev& g = S.g;
     double sl = R.ell / (double)R.N;
     for (int a = 0; a < 3; ++a) {
-        rin[a] = S.cam.pos[a] + R.t_in * R.d[a];
+        rin[a] = rs[a] + R.t_in * R.d[a];
         double u = (rin[a] - g.origin[a]) * g.inv_h[a] - 0.5;
         double du = sl * R.d[a] * g.inv_h[a];
         st.U[a] = to_fixed(u, 4294967296.0) + 256;   // +2^-24: see comp_cell
@@ -237,11 +238,18 @@ __device__ __forceinline__ float luminance_rel(const SceneDev& S, const double x
     return bilinear_f(L, px, py);
 }
 
-__device__ __forceinline__ RayResult comp_epilogue(const SceneDev& S, const Ray& R, double eta_in, const float dr[3],
-                                                   const float dv[3], float excess, bool want_hit) {
-    RayResult o;
-    o.I = 0.0;
-    o.hit[0] = o.hit[1] = o.disp[0] = o.disp[1] = 0.0;
+// Wall hit of a traced ray relative to its straight hit rs + t_w d, from the end
+// deviation (dr, dv): dx = x_w - x_ref, the cosine factor <n, v_N> / |v_N| and the path
+// length (signed straight continuation t* |v_N|).  valid = the ray reaches the wall.
+struct WallRel {
+    float dx[3];
+    float cosw, len;
+    bool valid;
+};
+
+__device__ __forceinline__ WallRel comp_wall(const SceneDev& S, const Ray& R, double eta_in, const float dr[3],
+                                             const float dv[3], float excess) {
+    WallRel h;
     const WallDev& w = S.w;
     float nf[3] = {(float)w.normal[0], (float)w.normal[1], (float)w.normal[2]};
     float df[3] = {(float)R.d[0], (float)R.d[1], (float)R.d[2]};
@@ -251,19 +259,37 @@ __device__ __forceinline__ RayResult comp_epilogue(const SceneDev& S, const Ray&
     const float ndr = nf[0] * dr[0] + nf[1] * dr[1] + nf[2] * dr[2];
     const float ndv = nf[0] * dv[0] + nf[1] * dv[1] + nf[2] * dv[2];
     const float den = e * cd + ndv;                       // <n, v_N>
-    if (!(den > 0.0f)) return o;
+    h.valid = den > 0.0f;
+    if (!h.valid) {
+        h.dx[0] = h.dx[1] = h.dx[2] = 0.0f;
+        h.cosw = h.len = 0.0f;
+        return h;
+    }
     const float iden = 1.0f / den;
     const float ts = (Lrem * cd - ndr) * iden;
     const float kk = -(e * ndr + Lrem * ndv) * iden;
-    float dx[3];
-    for (int a = 0; a < 3; ++a) dx[a] = dr[a] + ts * dv[a] + kk * df[a];
+    for (int a = 0; a < 3; ++a) h.dx[a] = dr[a] + ts * dv[a] + kk * df[a];
     const float ddv = df[0] * dv[0] + df[1] * dv[1] + df[2] * dv[2];
     const float vl = sqrtf(e * e + 2.0f * e * ddv + (dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]));
-    const float len = (float)(R.t_in + R.ell) + (excess + ts * vl);   // signed continuation t* |v|
+    h.len = (float)(R.t_in + R.ell) + (excess + ts * vl);   // signed continuation t* |v|
+    h.cosw = den / vl;
+    return h;
+}
+
+// Finish a camera ray whose wall point is x_ref + dx, reading the luminance at x_ref + e
+// (e = dx, or the refracted projector connection of the wall point).
+__device__ __forceinline__ RayResult comp_finish(const SceneDev& S, const Ray& R, const WallRel& h, const float e[3],
+                                                 bool want_hit) {
+    RayResult o;
+    o.I = 0.0;
+    o.hit[0] = o.hit[1] = o.disp[0] = o.disp[1] = 0.0;
+    if (!h.valid) return o;
+    const WallDev& w = S.w;
+    const float* dx = h.dx;
     double xref[3];
     for (int a = 0; a < 3; ++a) xref[a] = S.cam.pos[a] + R.tw * R.d[a];
-    const float Lw = luminance_rel(S, xref, dx);
-    o.I = (double)(Lw * (den / vl) / len);
+    const float Lw = luminance_rel(S, xref, e);
+    o.I = (double)(Lw * h.cosw / h.len);
     o.disp[0] = (double)(dx[0] * (float)w.eu[0] + dx[1] * (float)w.eu[1] + dx[2] * (float)w.eu[2]);
     o.disp[1] = (double)(dx[0] * (float)w.ev[0] + dx[1] * (float)w.ev[1] + dx[2] * (float)w.ev[2]);
     if (want_hit) {

@@ -13,6 +13,7 @@ namespace bos {
 void ctx_bind_arena(bos_ctx* c, void* base, size_t bytes, cudaStream_t stream);
 
 // Device bytes a render (adjoint != 0: render with checkpoints + backward) carves from an arena.
-size_t request_bytes(const bos_grid_desc& g, const bos_camera_desc& cam, const bos_integrator_desc& it, int adjoint);
+size_t request_bytes(const bos_grid_desc& g, const bos_camera_desc& cam, const bos_light_desc& light,
+                     const bos_integrator_desc& it, int adjoint);
 
 }  // namespace bos

@@ -41,10 +41,11 @@ struct WallDev {
 };
 
 struct LightDev {
-    int mode;
+    int mode;            // 0 texture, 1 projector (straight connection), 2 projector (refracted)
     CamDev proj;
     int tw, th;
     const float* pattern;
+    int connect_iters;   // mode 2: aiming rounds per wall point
 };
 
 struct IntegDev {
@@ -63,6 +64,9 @@ struct RayConst {
     double hi_m[3];        // (grid origin + extent) - camera position
     double qn;             // (wall origin - camera position) . wall normal
     double step;           // max_step_vox * min(h)
+    double plo_m[3];       // the same three terms for the projector pinhole (light modes 1, 2)
+    double phi_m[3];
+    double pqn;
 };
 
 struct SceneDev {
@@ -324,25 +328,29 @@ struct Ray {
     double ell;     // traced segment length
     int N;          // steps (0: straight to the wall)
     bool wall;      // reaches the wall plane
+    signed char in_axis;    // slab axis that sets t_in (-1: t_in = 0)
+    signed char out_axis;   // slab axis that sets the segment end (3: the wall plane)
 };
 
 // Straight-line set-up: wall plane, slab test, traced segment and N (bit-exact with a
 // plain IEEE double evaluation of the same formulas).
-__device__ __forceinline__ Ray ray_setup(const SceneDev& S, int px, int py, int s) {
-    Ray R;
-    double x, y;
-    image_point(S.cam, px, py, s, x, y);
-    pinhole_direction(S.cam, S.rc.right, x, y, R.d);
-    const double* rs = S.cam.pos;
+// Slab test and step count of the straight ray rs + t d (unit d) whose direction is
+// already in R.d: wall-plane distance, traced segment [t_in, min(t_out, t_w)] and N.
+// lo_m / hi_m are the box faces minus rs and qn = (wall origin - rs) . normal.
+__device__ __forceinline__ void ray_segment(const SceneDev& S, const double rs[3], const double lo_m[3],
+                                            const double hi_m[3], double qn, Ray& R) {
     R.N = 0;
     R.t_in = 0.0;
     R.ell = 0.0;
     R.tw = 0.0;
+    R.in_axis = -1;
+    R.out_axis = 3;
     double den = ddot(R.d, S.w.normal);
     R.wall = den > 0.0;
-    if (!R.wall) return R;
-    R.tw = ddiv(S.rc.qn, den);
+    if (!R.wall) return;
+    R.tw = ddiv(qn, den);
     double t_in = 0.0, t_out = __longlong_as_double(0x7ff0000000000000LL);
+    int ia = -1, oa = -1;
     bool inside = true;
     for (int a = 0; a < 3; ++a) {
         if (R.d[a] == 0.0) {
@@ -350,19 +358,32 @@ __device__ __forceinline__ Ray ray_setup(const SceneDev& S, int px, int py, int 
             continue;
         }
         double inv = ddiv(1.0, R.d[a]);
-        double t0 = dmul(S.rc.lo_m[a], inv);
-        double t1 = dmul(S.rc.hi_m[a], inv);
+        double t0 = dmul(lo_m[a], inv);
+        double t1 = dmul(hi_m[a], inv);
         if (t0 > t1) {
             double t = t0;
             t0 = t1;
             t1 = t;
         }
-        if (t0 > t_in) t_in = t0;
-        if (t1 < t_out) t_out = t1;
+        if (t0 > t_in) {
+            t_in = t0;
+            ia = a;
+        }
+        if (t1 < t_out) {
+            t_out = t1;
+            oa = a;
+        }
     }
-    double t_end = t_out < R.tw ? t_out : R.tw;
-    if (!inside || !(t_in < t_end)) return R;
+    double t_end = R.tw;
+    int ea = 3;
+    if (t_out < R.tw) {
+        t_end = t_out;
+        ea = oa;
+    }
+    if (!inside || !(t_in < t_end)) return;
     R.t_in = t_in;
+    R.in_axis = (signed char)ia;
+    R.out_axis = (signed char)ea;
     R.ell = dsub(t_end, t_in);
     if (S.it.fixed_steps > 0) {
         R.N = S.it.fixed_steps;
@@ -370,6 +391,29 @@ __device__ __forceinline__ Ray ray_setup(const SceneDev& S, int px, int py, int 
         double nn = ceil(ddiv(R.ell, S.rc.step));
         R.N = nn > (double)S.it.max_steps ? -1 : (int)nn;   // -1: over the step budget
     }
+}
+
+// Straight-line set-up of a camera ray: wall plane, slab test, traced segment and N
+// (bit-exact with a plain IEEE double evaluation of the same formulas).
+__device__ __forceinline__ Ray ray_setup(const SceneDev& S, int px, int py, int s) {
+    Ray R;
+    double x, y;
+    image_point(S.cam, px, py, s, x, y);
+    pinhole_direction(S.cam, S.rc.right, x, y, R.d);
+    ray_segment(S, S.cam.pos, S.rc.lo_m, S.rc.hi_m, S.rc.qn, R);
+    return R;
+}
+
+// The projector ray aimed at wall point base + e (base float64, e a small float offset):
+// unit direction q / |q| from the projector pinhole, q = aim - P, and its segment.
+__device__ __forceinline__ Ray projector_setup(const SceneDev& S, const double base[3], const float e[3]) {
+    Ray R;
+    const double* P = S.L.proj.pos;
+    double q[3];
+    for (int a = 0; a < 3; ++a) q[a] = dadd(dsub(base[a], P[a]), (double)e[a]);
+    double inv_n = ddiv(1.0, dsqrt(ddot(q, q)));
+    for (int a = 0; a < 3; ++a) R.d[a] = dmul(q[a], inv_n);
+    ray_segment(S, P, S.rc.plo_m, S.rc.phi_m, S.rc.pqn, R);
     return R;
 }
 

@@ -171,14 +171,15 @@ struct Sums {
     double I, du, dv, hu, hv;
 };
 
-// Trace one ray of the comp path; optionally store checkpoints every K steps.
+// Integrate one ray of the comp path (N > 0) from the pinhole rs; optionally store its
+// checkpoints every K steps in `state` (slot `ray`).  Leaves the end state in st.
 template <class E, int INTEG>
-__device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const Ray& R, const CkptDev& ck,
-                                long long ray, bool want_hit) {
-    CompState st;
+__device__ __forceinline__ void comp_run(const SceneDev& S, const CompField<E>& F, const double rs[3], const Ray& R,
+                                         const CkptDev& ck, float4* state, long long ray, CompState& st,
+                                         double& eta_in) {
     CompConst k;
-    double eta_in, rin[3];
-    comp_setup(S, F, R, st, k, eta_in, rin);
+    double rin[3];
+    comp_setup(S, F, rs, R, st, k, eta_in, rin);
     BrickCache bc = {0xffffffffu, 0u};
     const int K = ck.every;
 #ifndef BOS_FWD_PIPELINE
@@ -214,7 +215,7 @@ __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const 
             float ii = inc_r[0] * inc_r[0] + inc_r[1] * inc_r[1] + inc_r[2] * inc_r[2];
             float di = k.dhat[0] * inc_r[0] + k.dhat[1] * inc_r[1] + k.dhat[2] * inc_r[2];
             st.excess += __fdividef(2.0f * si + ii, 2.0f * k.step_len + di);
-            if (ck.state != nullptr) {          // sum of the unit step directions, for the adjoint
+            if (state != nullptr) {          // sum of the unit step directions, for the adjoint
                 float w[3] = {k.dS[0] + inc_r[0], k.dS[1] + inc_r[1], k.dS[2] + inc_r[2]};
                 float rn = rsqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
                 for (int a = 0; a < 3; ++a) usum[a] += w[a] * rn;
@@ -226,12 +227,12 @@ __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const 
                 A[a] = C[a];
             }
         }
-        if (ck.state != nullptr) {   // the final state, for the one-sweep adjoint
-            ck.state[0 * ck.nrays + ray] = make_float4(st.dr[0] - st.cr[0], st.dr[1] - st.cr[1], st.dr[2] - st.cr[2],
+        if (state != nullptr) {   // the final state, for the one-sweep adjoint
+            state[0 * ck.nrays + ray] = make_float4(st.dr[0] - st.cr[0], st.dr[1] - st.cr[1], st.dr[2] - st.cr[2],
                                                        st.excess);
-            ck.state[1 * ck.nrays + ray] = make_float4(st.dv[0] - st.cv[0], st.dv[1] - st.cv[1], st.dv[2] - st.cv[2],
+            state[1 * ck.nrays + ray] = make_float4(st.dv[0] - st.cv[0], st.dv[1] - st.cv[1], st.dv[2] - st.cv[2],
                                                        usum[0]);
-            ck.state[2 * ck.nrays + ray] = make_float4(usum[1], usum[2], 0.0f, 0.0f);
+            state[2 * ck.nrays + ray] = make_float4(usum[1], usum[2], 0.0f, 0.0f);
         }
     } else if constexpr (INTEG == 0 && BOS_FWD_PIPELINE) {
         // Sharma steps, software-pipelined: the next step's first stage needs only the new
@@ -244,11 +245,11 @@ __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const 
         const float dt = k.dt;
         for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
         for (int n = 0; n < R.N; ++n) {
-            if (ck.state != nullptr && n % K == 0) {
+            if (state != nullptr && n % K == 0) {
                 size_t c = (size_t)(n / K);
-                ck.state[(c * 3 + 0) * ck.nrays + ray] = make_float4(st.dr[0], st.dr[1], st.dr[2], st.cr[0]);
-                ck.state[(c * 3 + 1) * ck.nrays + ray] = make_float4(st.dv[0], st.dv[1], st.dv[2], st.cr[1]);
-                ck.state[(c * 3 + 2) * ck.nrays + ray] = make_float4(st.cv[0], st.cv[1], st.cv[2], st.cr[2]);
+                state[(c * 3 + 0) * ck.nrays + ray] = make_float4(st.dr[0], st.dr[1], st.dr[2], st.cr[0]);
+                state[(c * 3 + 1) * ck.nrays + ray] = make_float4(st.dv[0], st.dv[1], st.dv[2], st.cr[1]);
+                state[(c * 3 + 2) * ck.nrays + ray] = make_float4(st.cv[0], st.cv[1], st.cv[2], st.cr[2]);
             }
             float B[3], C[3], q[3], inc_r[3], inc_v[3];
             long long U2[3], U3[3];
@@ -295,22 +296,81 @@ __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const 
         }
     } else {
         for (int n = 0; n < R.N; ++n) {
-            if (ck.state != nullptr && n % K == 0) {
+            if (state != nullptr && n % K == 0) {
                 size_t c = (size_t)(n / K);
-                ck.state[(c * 3 + 0) * ck.nrays + ray] = make_float4(st.dr[0], st.dr[1], st.dr[2], st.cr[0]);
-                ck.state[(c * 3 + 1) * ck.nrays + ray] = make_float4(st.dv[0], st.dv[1], st.dv[2], st.cr[1]);
-                ck.state[(c * 3 + 2) * ck.nrays + ray] = make_float4(st.cv[0], st.cv[1], st.cv[2], st.cr[2]);
+                state[(c * 3 + 0) * ck.nrays + ray] = make_float4(st.dr[0], st.dr[1], st.dr[2], st.cr[0]);
+                state[(c * 3 + 1) * ck.nrays + ray] = make_float4(st.dv[0], st.dv[1], st.dv[2], st.cr[1]);
+                state[(c * 3 + 2) * ck.nrays + ray] = make_float4(st.cv[0], st.cv[1], st.cv[2], st.cr[2]);
             }
             comp_step<E, INTEG>(F, st, k, bc);
         }
     }
-    if (ck.state != nullptr) ck.excess[ray] = st.excess;
-    float dr[3], dv[3];
+}
+
+__device__ __forceinline__ void comp_end(const CompState& st, float dr[3], float dv[3]) {
     for (int a = 0; a < 3; ++a) {
         dr[a] = st.dr[a] - st.cr[a];
         dv[a] = st.dv[a] - st.cv[a];
     }
-    return comp_epilogue(S, R, eta_in, dr, dv, st.excess, want_hit);
+}
+
+// Trace one camera ray of the comp path (checkpoints every K steps when ck.state is set).
+// With CONN (light mode 2) the luminance is read at the refracted projector connection of
+// the wall point x_w = x_ref + dx: M rounds of a <- a + (x_w - y(a)) from a = x_w, y(a) the
+// wall hit of the projector ray aimed at a (traced like a camera ray), so that
+// a = x_ref + e with e <- dx - (y(a) - (P + t_w d_p)) - ((P + t_w d_p) - a).
+template <class E, int INTEG, bool CONN>
+__device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const Ray& R, const CkptDev& ck,
+                                long long ray, bool want_hit, unsigned long long& steps) {
+    WallRel h;
+    if (R.N > 0) {
+        CompState st;
+        double eta_in;
+        comp_run<E, INTEG>(S, F, S.cam.pos, R, ck, ck.state, ray, st, eta_in);
+        if (ck.state != nullptr) ck.excess[ray] = st.excess;
+        steps += (unsigned long long)R.N;
+        float dr[3], dv[3];
+        comp_end(st, dr, dv);
+        h = comp_wall(S, R, eta_in, dr, dv, st.excess);
+    } else {   // straight camera ray (only with CONN: the projector rays may still bend)
+        h.dx[0] = h.dx[1] = h.dx[2] = 0.0f;
+        h.cosw = (float)(R.d[0] * S.w.normal[0] + R.d[1] * S.w.normal[1] + R.d[2] * S.w.normal[2]);
+        h.len = (float)R.tw;
+        h.valid = h.cosw > 0.0f;
+        if (ck.state != nullptr) ck.excess[ray] = 0.0f;
+    }
+    float e[3] = {h.dx[0], h.dx[1], h.dx[2]};
+    if constexpr (CONN) {
+        if (h.valid) {
+            double xref[3];
+            for (int a = 0; a < 3; ++a) xref[a] = S.cam.pos[a] + R.tw * R.d[a];
+            const double* P = S.L.proj.pos;
+            for (int m = 0; m < S.L.connect_iters; ++m) {
+                const Ray Rp = projector_setup(S, xref, e);
+                float yrel[3] = {0.0f, 0.0f, 0.0f};
+                if (Rp.wall && Rp.N > 0) {
+                    CompState sp;
+                    double eta_p;
+                    comp_run<E, INTEG>(S, F, P, Rp, ck, m == 0 ? ck.pstate : nullptr, ray, sp, eta_p);
+                    steps += (unsigned long long)Rp.N;
+                    float pr[3], pv[3];
+                    comp_end(sp, pr, pv);
+                    const WallRel hp = comp_wall(S, Rp, eta_p, pr, pv, 0.0f);
+                    if (hp.valid)
+                        for (int a = 0; a < 3; ++a) yrel[a] = hp.dx[a];
+                }
+                for (int a = 0; a < 3; ++a) {
+                    const double eps = (xref[a] + (double)e[a]) - (P[a] + Rp.tw * Rp.d[a]);
+                    e[a] = (h.dx[a] - yrel[a]) + (float)eps;
+                }
+            }
+        }
+        if (ck.conn != nullptr) {   // (a zero cosine factor marks a ray that misses the wall)
+            ck.conn[2 * ray] = make_float4(h.dx[0], h.dx[1], h.dx[2], h.valid ? h.cosw / h.len : 0.0f);
+            ck.conn[2 * ray + 1] = make_float4(h.dx[0] - e[0], h.dx[1] - e[1], h.dx[2] - e[2], 0.0f);
+        }
+    }
+    return comp_finish(S, R, h, e, want_hit);
 }
 
 template <class T, int INTEG>
@@ -358,29 +418,31 @@ __device__ RayResult trace_full(const SceneDev& S, const FullField<T>& F, const 
 template <int MODE>   // 0 straight, 1 comp fp32, 2 comp bf16, 3 full fp32, 4 full fp64
 struct Tracer;
 
-template <int MODE, int INTEG>
+template <int MODE, int INTEG, bool CONN>
 __device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, const CkptDev& ck, long long ray,
-                                               bool want_hit) {
+                                               bool want_hit, unsigned long long& steps) {
     if constexpr (MODE == 0) {
         return straight_epilogue(S, R, want_hit);
     } else if constexpr (MODE == 1) {
         CompField<float4> F = {static_cast<const float4*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
                                {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
-        return trace_comp<float4, INTEG>(S, F, R, ck, ray, want_hit);
+        return trace_comp<float4, INTEG, CONN>(S, F, R, ck, ray, want_hit, steps);
     } else if constexpr (MODE == 2) {
         CompField<uint2> F = {static_cast<const uint2*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
                               {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
-        return trace_comp<uint2, INTEG>(S, F, R, ck, ray, want_hit);
+        return trace_comp<uint2, INTEG, CONN>(S, F, R, ck, ray, want_hit, steps);
     } else if constexpr (MODE == 3) {
         FullField<float> F = {S.g};
+        steps += (unsigned long long)R.N;
         return trace_full<float, INTEG>(S, F, R);
     } else {
         FullField<double> F = {S.g};
+        steps += (unsigned long long)R.N;
         return trace_full<double, INTEG>(S, F, R);
     }
 }
 
-template <int MODE, int INTEG>
+template <int MODE, int INTEG, bool CONN>
 #ifndef BOS_FWD_MIN_BLOCKS
 #define BOS_FWD_MIN_BLOCKS 6              // resident 128-thread blocks per SM the register budget is cut for
 #endif
@@ -412,12 +474,11 @@ __global__ void __launch_bounds__(128, BOS_FWD_MIN_BLOCKS) render_kernel(SceneDe
                     continue;
                 }
                 RayResult r;
-                if (MODE == 0 || R.N == 0) {
+                if (MODE == 0 || (R.N == 0 && !CONN)) {
                     r = straight_epilogue(S, R, out.hit != nullptr);
                     if (R.N == 0 && ck.state != nullptr) ck.excess[ray] = 0.0f;
                 } else {
-                    r = trace_ray<MODE, INTEG>(S, R, ck, ray, out.hit != nullptr);
-                    my_steps += (unsigned long long)R.N;
+                    r = trace_ray<MODE, INTEG, CONN>(S, R, ck, ray, out.hit != nullptr, my_steps);
                 }
                 acc.I += r.I;
                 acc.du += r.disp[0];
@@ -530,15 +591,26 @@ cudaError_t launch_build_store(const GridDev& g, const float* T, void* store, cu
     return cudaGetLastError();
 }
 
+template <int MODE, int INTEG, bool CONN>
+static cudaError_t launch_render_c(const SceneDev& S, const RenderOut& o, const WorkDev& w, const CkptDev& ck,
+                                   int num_sms, cudaStream_t st) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<MODE, INTEG, CONN>, 128, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    render_kernel<MODE, INTEG, CONN><<<num_sms * per_sm, 128, 0, st>>>(S, o, w, ck);
+    return cudaGetLastError();
+}
+
+// The refracted projector connection (light mode 2) has its own instantiation for the
+// compensated tracers; the straight reference render and the plain tracers do not use it.
 template <int MODE, int INTEG>
 static cudaError_t launch_render_t(const SceneDev& S, const RenderOut& o, const WorkDev& w, const CkptDev& ck,
                                    int num_sms, cudaStream_t st) {
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<MODE, INTEG>, 128, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    render_kernel<MODE, INTEG><<<num_sms * per_sm, 128, 0, st>>>(S, o, w, ck);
-    return cudaGetLastError();
+    if constexpr (MODE == 1 || MODE == 2) {
+        if (S.L.mode == 2) return launch_render_c<MODE, INTEG, true>(S, o, w, ck, num_sms, st);
+    }
+    return launch_render_c<MODE, INTEG, false>(S, o, w, ck, num_sms, st);
 }
 
 cudaError_t launch_render(int mode, const SceneDev& S, const RenderOut& o, const WorkDev& w, const CkptDev& ck,

@@ -32,6 +32,9 @@ struct CkptDev {
     long long nrays;                // number of slots (tiles * 32 * samples_per_lane)
     int every;
     int max_ckpt;
+    // refracted projector connection (light mode 2), kept when state != nullptr:
+    float4* pstate;                 // checkpoints of each slot's projector ray (same layout as state)
+    float4* conn;                   // 2 per slot: (x_w - x_ref, cos/len), (x_w - a_1, 0)
 };
 
 // Grid adjoint accumulators: per node (d L/d deta, d L/d grad eta) in float32.
@@ -44,7 +47,7 @@ struct AdjDev {
 // Message returned by bos_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
-// Ray-independent float64 set-up terms of a scene (S.g, S.cam, S.w and S.it filled in).
+// Ray-independent float64 set-up terms of a scene (S.g, S.cam, S.w, S.L and S.it filled in).
 RayConst ray_const_of(const SceneDev& S);
 
 cudaError_t launch_build_store(const GridDev& g, const float* T, void* store, cudaStream_t st);

@@ -100,10 +100,13 @@ extern "C" bos_status_t bos_render_noalloc(const bos_grid_desc* grid, const floa
         grid->prec > BOS_PREC_BF16_COMP)
         return refuse(BOS_ERR_INVALID_ARG, "malformed grid descriptor");
     if (cam->width <= 0 || cam->height <= 0 || cam->spp <= 0 || !(cam->fx > 0) || !(cam->fy > 0) ||
-        light->tw <= 0 || light->th <= 0 || (light->mode != 0 && light->mode != 1) || integ->ckpt_every < 1 ||
+        light->tw <= 0 || light->th <= 0 || (light->mode < 0 || light->mode > 2) ||
+        (light->mode == 2 && (light->connect_iters < 1 || light->connect_iters > 16)) || integ->ckpt_every < 1 ||
         (integ->fixed_steps <= 0 && !(integ->max_step_vox > 1e-3)) || integ->fixed_steps < 0 ||
         (integ->integrator != 0 && integ->integrator != 1))
         return refuse(BOS_ERR_INVALID_ARG, "malformed camera, light or integrator descriptor");
+    if (light->mode == 2 && grid->prec != BOS_PREC_FP32_COMP && grid->prec != BOS_PREC_BF16_COMP)
+        return refuse(BOS_ERR_UNIMPLEMENTED, "the refracted projector connection needs a compensated precision");
 
     GridDev g{};
     const int n[3] = {grid->nx, grid->ny, grid->nz};
@@ -160,6 +163,7 @@ extern "C" bos_status_t bos_render_noalloc(const bos_grid_desc* grid, const floa
     S.L.proj = cam_dev(light->proj);
     S.L.tw = light->tw;
     S.L.th = light->th;
+    S.L.connect_iters = light->mode == 2 ? light->connect_iters : 0;
     S.L.pattern = pattern_dev;
     S.it.fixed_steps = integ->fixed_steps;
     S.it.max_step_vox = integ->max_step_vox;

@@ -253,7 +253,7 @@ extern "C" {
 
 bos_status_t bos_request_footprint(const bos_request* r, uint64_t* bytes) {
     if (!bytes || validate_request(r) != BOS_OK) return BOS_ERR_INVALID_ARG;
-    *bytes = bos::request_bytes(r->grid, r->cam, r->integ, r->target_dev != nullptr) + scratch_bytes(*r);
+    *bytes = bos::request_bytes(r->grid, r->cam, r->light, r->integ, r->target_dev != nullptr) + scratch_bytes(*r);
     return BOS_OK;
 }
 
@@ -309,7 +309,7 @@ bos_status_t bos_submit(bos_server* s, const bos_request* r, uint64_t* ticket) {
     if (!s || !ticket) return BOS_ERR_INVALID_ARG;
     bos_status_t v = validate_request(r);
     if (v != BOS_OK) return v;
-    uint64_t fp = bos::request_bytes(r->grid, r->cam, r->integ, r->target_dev != nullptr) + scratch_bytes(*r);
+    uint64_t fp = bos::request_bytes(r->grid, r->cam, r->light, r->integ, r->target_dev != nullptr) + scratch_bytes(*r);
     if (bos::align_up(fp) > s->limit) return BOS_ERR_ADMISSION;
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return BOS_ERR_NOT_READY;
