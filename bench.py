@@ -81,13 +81,35 @@ BYTES_PER_STEP = {"fp32_comp": 384, "fp32": 384, "bf16_comp": 192, "fp64": 768}
 ADJ_BYTES_PER_STEP = {"fp32_comp": 3 * 384, "bf16_comp": 2 * 192 + 384}
 L2_BYTES = 129 * 2 ** 20
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the timed kernels,
+# from one ncu capture of the default workload (profiles/adjoint_kernel_room_adj.md).  It is
+# reported only while the kernel sources still hash to what was captured.
+TRAFFIC_SOURCES = ("bos_forward.cu", "bos_adjoint.cu", "bos_comp.cuh", "bos_device.cuh")
+KERNEL_TRAFFIC = {"workload": "room_adj", "sha256": None, "render_kernel": None, "adjoint_kernel": None}
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2509_14442_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(workload: str, name: str):
+    if KERNEL_TRAFFIC["sha256"] is None or workload != KERNEL_TRAFFIC["workload"]:
+        return None
+    return KERNEL_TRAFFIC[name] if kernel_sources_sha256() == KERNEL_TRAFFIC["sha256"] else None
+
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--workload", default="room_adj", choices=sorted(WORKLOADS) + ["serving", "precision"])
+    p.add_argument("--workload", default="room_adj", choices=sorted(WORKLOADS) + ["serving", "precision", "recon"])
     p.add_argument("--prec", default="fp32_comp", choices=sorted(BYTES_PER_STEP))
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
@@ -397,18 +419,20 @@ def gpu_arm(args):
     adj_b = wl.get("adj_bytes", ADJ_BYTES_PER_STEP.get(args.prec, 0))
     fwd_gbs = fwd_b * steps_per_frame / (render_avg_ms * 1e-3) / 1e9
     kernels = {"render_kernel": {"ms": render_avg_ms, "bytes_per_ray_step": fwd_b,
-                                 "achieved_gbs": fwd_gbs, "frac": fwd_gbs / l2_peak}}
+                                 "achieved_gbs": fwd_gbs, "frac": fwd_gbs / l2_peak,
+                                 "traffic": kernel_traffic(args.workload, "render_kernel")}}
     dominant = "render_kernel"
     if wl["adjoint"]:
         back_avg_ms = statistics.mean(back_ms)
         adj_gbs = adj_b * steps_per_frame / (back_avg_ms * 1e-3) / 1e9
         kernels["adjoint_kernel"] = {"ms": back_avg_ms, "bytes_per_ray_step": adj_b,
                                      "achieved_gbs": adj_gbs, "frac": adj_gbs / l2_peak,
+                                     "traffic": kernel_traffic(args.workload, "adjoint_kernel"),
                                      "timed": "bos_backward: accumulator clear + adjoint_kernel + gradient_kernel"}
         dominant = "adjoint_kernel"
     dk = kernels[dominant]
     roofline = {"bound": "l2", "kernel": dominant, "achieved": dk["achieved_gbs"], "peak": l2_peak, "unit": "GB/s",
-                "frac": dk["frac"], "traffic": None,
+                "frac": dk["frac"], "traffic": dk["traffic"],
                 "peak_source": "in-run L2 read probe (bos_probe_read, 24 MiB x 50 passes, best of 10)",
                 "bytes_per_ray_step": dk["bytes_per_ray_step"],
                 "note": ("gather roofline R = L2 read bandwidth / algorithmic bytes per ray-step; the gathers "
@@ -532,6 +556,97 @@ def serving_arm(args):
     }))
 
 
+# ------------------------------------------------------------------ reconstruction loop
+
+RECON_ITERS_PER_STEP = 100
+
+
+def recon_arm(args):
+    """Voxel reconstruction on the paper's measurement set-up (Sec. 3.1-3.2): 64^3 grid over
+    the room, 100 x 100 sensor with 2 samples per pixel, 5000-pixel minibatches, AdaBelief,
+    and the paper's quasi-linear tracer (Sec. 2.2).
+    One iteration = minibatch draw, field build, subset render, minibatch L_BOS, backward and
+    the AdaBelief update, all on the device.  A timed step is RECON_ITERS_PER_STEP iterations."""
+    import torch
+
+    from paper_2509_14442_gb300 import bos
+    from paper_2509_14442_gb300.recon import Reconstructor
+
+    dev = torch.device("cuda", 0)
+    sc = quasi(S.paper_sensor())
+    truth = torch.as_tensor(sc.T, device=dev)
+    ctx = bos.Context(0)
+    ctx.set_scene(sc, bos.BOS_PREC_FP32_COMP, T=truth)
+    target, _, _ = ctx.render(disp=False)
+    ctx.close()
+
+    def full_loss(T):
+        c = bos.Context(0)
+        c.set_scene(sc, bos.BOS_PREC_FP32_COMP, T=T.contiguous())
+        I, _, _ = c.render(disp=False)
+        torch.cuda.synchronize()
+        c.close()
+        return float(((I - target) ** 2).sum())
+
+    T0 = torch.full_like(truth, S.T_AMBIENT)
+    loss0 = full_loss(T0)
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    def timed(rec, graph: bool, clk=None):
+        """ms per RECON_ITERS_PER_STEP iterations, launched call by call or as graph replays."""
+        def chunk():
+            if graph:
+                rec.run(RECON_ITERS_PER_STEP)
+            else:
+                for _ in range(RECON_ITERS_PER_STEP):
+                    rec.step()
+        for _ in range(args.warmup):
+            chunk()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+        for k in range(args.steps):
+            flush.fill_(0.0)
+            ev[2 * k].record(stream)
+            chunk()
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]))
+
+    eager = Reconstructor(sc, target, T0, batch=5000, lr=0.2, loss_scale=1e11, seed=1)
+    ms_eager = timed(eager, False)
+    eager.close()
+    rec = Reconstructor(sc, target, T0, batch=5000, lr=0.2, loss_scale=1e11, seed=1)
+    with Clocks(0) as clk:
+        ms = timed(rec, True)
+    # ray-steps of one iteration's minibatch render (every one is also reversed)
+    counts = []
+    for _ in range(4):
+        rec.step()
+        torch.cuda.synchronize()
+        counts.append(rec.ctx.last_ray_steps())
+    rs_per_iter = float(np.mean(counts))
+    loss1 = full_loss(rec.T)
+    iters_done = rec.it
+    rec.close()
+    it_per_s = RECON_ITERS_PER_STEP * 1e3 / ms
+    print(json.dumps({
+        "metric": "reconstruction iterations/s", "value": it_per_s, "unit": "iterations/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded plume field, its own render as the measurement)",
+        "config": {"workload": "recon", "grid": [64, 64, 64], "image": [100, 100], "spp": 2, "batch": 5000,
+                   "tracer": "quasi-linear (Sec. 2.2)", "minibatch_order": "Z-order sorted (bos_sort_pixels)",
+                   "iterations_per_step": RECON_ITERS_PER_STEP, "optimizer": "AdaBelief lr 0.2, loss scale 1e11",
+                   "launch": "one CUDA graph replay per iteration",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "ray_steps_per_s": rs_per_iter * it_per_s, "ray_steps_per_iteration": rs_per_iter,
+        "eager_iterations_per_s": RECON_ITERS_PER_STEP * 1e3 / ms_eager,
+        "loss_full_image": {"start": loss0, "after": loss1, "iterations": iters_done},
+        "clocks": clk.summary(),
+    }))
+
+
 # ------------------------------------------------------------------ precision variants
 
 def bf16_round(x):
@@ -607,6 +722,8 @@ def main():
         serving_arm(args)
     elif args.workload == "precision":
         precision_arm(args)
+    elif args.workload == "recon":
+        recon_arm(args)
     else:
         gpu_arm(args)
 

@@ -207,16 +207,31 @@ bos_status_t bos_loss_l2_pixels(const float* I_dev, const float* target_dev, con
                                 float scale, double* loss_dev, float* dLdI_dev, void* stream);
 
 /* A minibatch of npix uniformly random pixel indices in [0, n_pixels) (with repeats):
- * entry k is the splitmix64 output number draw*npix + k + 1 for `seed`, scaled to the range
- * by a 64x64-bit multiply-high.  Used for the random BOS-pixel minibatches of Sec. 3.2. */
+ * entry k is the splitmix64 output number d*npix + k + 1 for `seed`, scaled to the range
+ * by a 64x64-bit multiply-high, with draw number d = draw + *draw_dev (draw_dev nullable,
+ * read on the device, so a captured CUDA graph can replay successive draws).  Used for the
+ * random BOS-pixel minibatches of Sec. 3.2. */
 bos_status_t bos_sample_pixels(int32_t* pix_dev, int64_t npix, int64_t n_pixels, uint64_t seed, uint64_t draw,
-                               void* stream);
+                               const uint64_t* draw_dev, void* stream);
 
 /* One AdaBelief step (the optimiser of Sec. 3.2; Zhuang et al., NeurIPS 2020) on n float32
  * parameters: m = b1 m + (1-b1) g; s = b2 s + (1-b2) (g-m)^2 + eps;
- * theta -= lr (m / (1 - b1^step)) / (sqrt(s / (1 - b2^step)) + eps).  step >= 1; m and s start at 0. */
+ * theta -= lr (m / (1 - b1^t)) / (sqrt(s / (1 - b2^t)) + eps), with step number
+ * t = step + *step_dev (step_dev nullable, read on the device); t >= 1; m and s start at 0. */
 bos_status_t bos_adabelief_step(float* theta_dev, const float* grad_dev, float* m_dev, float* s_dev, int64_t n,
-                                float lr, float beta1, float beta2, float eps, int64_t step, void* stream);
+                                float lr, float beta1, float beta2, float eps, int64_t step, const uint64_t* step_dev,
+                                void* stream);
+
+/* Reorder a pixel list in place (npix <= 16384, width and height <= 65535) by the Morton
+ * (Z-order) key of (px, py), so that the 32 rays of a warp come from neighbouring pixels.
+ * The list keeps its entries (with repeats), so every sum over it is unchanged up to
+ * summation order; random minibatches (Sec. 3.2) otherwise give each warp rays from all over
+ * the image.  One block; asynchronous on `stream`. */
+bos_status_t bos_sort_pixels(int32_t* pix_dev, int64_t npix, int width, int height, void* stream);
+
+/* *counter_dev += inc on the device (an iteration counter for bos_sample_pixels and
+ * bos_adabelief_step inside a captured CUDA graph). */
+bos_status_t bos_counter_add(uint64_t* counter_dev, uint64_t inc, void* stream);
 
 /* Step a6 (Sec. 2.4): given dL/dI (height*width float32, or npix values after
  * bos_render_pixels) for the most recent render with save_for_backward=1, write dL/dT
@@ -244,10 +259,10 @@ bos_status_t bos_probe_read(const void* buf_dev, uint64_t bytes, int repeats, fl
  * a host whose device memory is already handed out by another allocator).  No
  * counterpart in the paper: it runs the same field build and render as bos_set_grid +
  * bos_render (no displacement-free shortcut, no checkpoints), with the field store and
- * the work counters in one file-scope device array of 64 MiB that the library reserves
+ * the work counters in one file-scope device array of 128 MiB that the library reserves
  * on every GPU it is loaded on, until the process exits.  The caller passes the inputs
  * (T_dev, pattern_dev) and outputs (I_dev, disp_dev nullable) as in bos_render.
- * Grids whose field store exceeds the array (64 MiB - 256 B; e.g. 128x128x96 cells
+ * Grids whose field store exceeds the array (128 MiB - 256 B; e.g. 128x128x96 cells
  * fit in float32, 256x256x192 do not) are rejected with BOS_ERR_INVALID_ARG and a
  * message in bos_last_error().  The first call on a device looks up the array's
  * address with that device current; make that first call before any stream capture.

@@ -98,8 +98,10 @@ SIGNATURES = {
     "bos_loss_l2": (_i, [_v, _v, _i64, _v, _v, _v]),
     "bos_backward": (_i, [_v, _v, _v, _v]),
     "bos_loss_l2_pixels": (_i, [_v, _v, _v, _i64, C.c_float, _v, _v, _v]),
-    "bos_sample_pixels": (_i, [_v, _i64, _i64, _u64, _u64, _v]),
-    "bos_adabelief_step": (_i, [_v, _v, _v, _v, _i64, C.c_float, C.c_float, C.c_float, C.c_float, _i64, _v]),
+    "bos_sample_pixels": (_i, [_v, _i64, _i64, _u64, _u64, _v, _v]),
+    "bos_adabelief_step": (_i, [_v, _v, _v, _v, _i64, C.c_float, C.c_float, C.c_float, C.c_float, _i64, _v, _v]),
+    "bos_counter_add": (_i, [_v, _u64, _v]),
+    "bos_sort_pixels": (_i, [_v, _i64, _i, _i, _v]),
     "bos_export_nodes": (_i, [_v, _v, _v]),
     "bos_probe_read": (_i, [_v, _u64, _i, _v, _v]),
     "bos_render_noalloc": (_i, [_P(bos_grid_desc), _v, _P(bos_camera_desc), _P(bos_wall_desc), _P(bos_light_desc),
@@ -242,14 +244,22 @@ def bos_loss_l2_pixels(I_dev, target_dev, pix_dev, npix: int, loss_dev, dLdI_dev
           "bos_loss_l2_pixels")
 
 
-def bos_sample_pixels(pix_dev, npix: int, n_pixels: int, seed: int, draw: int, stream) -> None:
-    check(lib().bos_sample_pixels(pix_dev, npix, n_pixels, seed, draw, stream), "bos_sample_pixels")
+def bos_sample_pixels(pix_dev, npix: int, n_pixels: int, seed: int, draw: int, stream, draw_dev=None) -> None:
+    check(lib().bos_sample_pixels(pix_dev, npix, n_pixels, seed, draw, draw_dev, stream), "bos_sample_pixels")
 
 
 def bos_adabelief_step(theta_dev, grad_dev, m_dev, s_dev, n: int, lr: float, beta1: float, beta2: float, eps: float,
-                       step: int, stream) -> None:
-    check(lib().bos_adabelief_step(theta_dev, grad_dev, m_dev, s_dev, n, lr, beta1, beta2, eps, step, stream),
-          "bos_adabelief_step")
+                       step: int, stream, step_dev=None) -> None:
+    check(lib().bos_adabelief_step(theta_dev, grad_dev, m_dev, s_dev, n, lr, beta1, beta2, eps, step, step_dev,
+                                   stream), "bos_adabelief_step")
+
+
+def bos_sort_pixels(pix_dev, npix: int, width: int, height: int, stream) -> None:
+    check(lib().bos_sort_pixels(pix_dev, npix, width, height, stream), "bos_sort_pixels")
+
+
+def bos_counter_add(counter_dev, inc: int, stream) -> None:
+    check(lib().bos_counter_add(counter_dev, inc, stream), "bos_counter_add")
 
 
 def bos_backward(ctx, dLdI_dev, dLdT_dev, stream) -> None:

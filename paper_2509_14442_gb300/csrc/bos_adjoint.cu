@@ -52,17 +52,17 @@ __device__ __forceinline__ float4 to4(Cell2 c) {
 template <class E>
 __device__ __forceinline__ InterpGrad trilinear_grad2(const E* s, uint32_t o, float f0, float f1, float f2) {
     const f32x2 t0 = pack2(f0, f0), t1 = pack2(f1, f1), t2 = pack2(f2, f2);
-    const Cell2 c000 = load_cell2(s, o), c100 = load_cell2(s, o + 1), c010 = load_cell2(s, o + 9),
-                c110 = load_cell2(s, o + 10), c001 = load_cell2(s, o + 81), c101 = load_cell2(s, o + 82),
-                c011 = load_cell2(s, o + 90), c111 = load_cell2(s, o + 91);
-    const Cell2 a0 = lerpc(c000, c100, t0), a1 = lerpc(c010, c110, t0);
-    const Cell2 a2 = lerpc(c001, c101, t0), a3 = lerpc(c011, c111, t0);
+    Cell2 a0, a1, a2, a3, e0, e1, e2, e3;   // x-interpolated corner pairs and their x differences
+    xlerp(s, o, t0, a0, e0);
+    xlerp(s, o + 9, t0, a1, e1);
+    xlerp(s, o + 81, t0, a2, e2);
+    xlerp(s, o + 90, t0, a3, e3);
     const Cell2 b0 = lerpc(a0, a1, t1), b1 = lerpc(a2, a3, t1);
     InterpGrad r;
     r.v = to4(lerpc(b0, b1, t2));
     r.d2 = to4(subc(b1, b0));
     r.d1 = to4(lerpc(subc(a1, a0), subc(a3, a2), t2));
-    r.d0 = to4(lerpc(lerpc(subc(c100, c000), subc(c110, c010), t1), lerpc(subc(c101, c001), subc(c111, c011), t1), t2));
+    r.d0 = to4(lerpc(lerpc(e0, e1, t1), lerpc(e2, e3, t1), t2));
     return r;
 }
 
@@ -857,10 +857,10 @@ cudaError_t launch_backward(int mode, const SceneDev& S, const CkptDev& ck, cons
     const bool quasi = S.it.integrator == 2;
     if (!quasi && ck.every > 64) return cudaErrorNotSupported;
     cudaError_t e;
-    if (mode == 1) e = quasi ? launch_adjoint_quasi_t<float4>(S, ck, adj, w, num_sms, st)
-                             : launch_adjoint_t<float4>(S, ck, adj, w, num_sms, st);
-    else if (mode == 2) e = quasi ? launch_adjoint_quasi_t<uint2>(S, ck, adj, w, num_sms, st)
-                                  : launch_adjoint_t<uint2>(S, ck, adj, w, num_sms, st);
+    if (mode == 1) e = quasi ? launch_adjoint_quasi_t<F4P>(S, ck, adj, w, num_sms, st)
+                             : launch_adjoint_t<F4P>(S, ck, adj, w, num_sms, st);
+    else if (mode == 2) e = quasi ? launch_adjoint_quasi_t<B4P>(S, ck, adj, w, num_sms, st)
+                                  : launch_adjoint_t<B4P>(S, ck, adj, w, num_sms, st);
     else return cudaErrorNotSupported;
     if (e != cudaSuccess) return e;
     gradient_kernel<<<num_sms * 8, 256, 0, st>>>(S.g, adj.acc, T, dLdT);

@@ -75,7 +75,8 @@ CamDev to_dev(const bos_camera_desc& c) {
     return d;
 }
 
-size_t elem_bytes(int prec) { return prec == BOS_PREC_FP64 ? 32 : prec == BOS_PREC_BF16_COMP ? 8 : 16; }
+// Bytes per store element: float32 and bfloat16 records are stored as x pairs (F4P, B4P).
+size_t elem_bytes(int prec) { return prec == BOS_PREC_FP64 ? 32 : prec == BOS_PREC_BF16_COMP ? 16 : 32; }
 
 // Tracer variant of a precision (see the MODE switch of the render kernel).
 int mode_of(int prec) {

@@ -192,14 +192,62 @@ __device__ __forceinline__ Cell2 load_cell2(const uint2* s, uint32_t o) {
 }
 __device__ __forceinline__ Cell2 lerpc(Cell2 a, Cell2 b, f32x2 t) { return Cell2{lerp2(a.lo, b.lo, t), lerp2(a.hi, b.hi, t)}; }
 
-// Trilinear (deta, grad eta) in packed arithmetic; bit-identical to `trilinear`.
+// ---- paired store elements
+//
+// The compensated and plain float32 tracers read their store as pairs along x: element o
+// holds record o and what the first interpolation level needs of record o + 1, so the 8
+// corners of a cell are 4 loads.  Float32: (record, record[o+1] - record[o]) -- the
+// difference is the float32 subtraction the interpolation would make, so one fma gives
+// the x-interpolated value, bit-identical to lerp(record[o], record[o+1]).  32 bytes,
+// read with one 256-bit load.  Bfloat16: the two raw records (16 bytes).
+struct __align__(32) F4P {
+    float4 v, d;
+};
+struct __align__(16) B4P {
+    uint2 a, b;
+};
+
+__device__ __forceinline__ void load_pair(const F4P* s, uint32_t o, Cell2& v, Cell2& d) {
+    float v0, v1, v2, v3, d0, d1, d2, d3;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(v0), "=f"(v1), "=f"(v2), "=f"(v3), "=f"(d0), "=f"(d1), "=f"(d2), "=f"(d3)
+        : "l"(s + o));
+    v = Cell2{pack2(v0, v1), pack2(v2, v3)};
+    d = Cell2{pack2(d0, d1), pack2(d2, d3)};
+}
+
+__device__ __forceinline__ Cell2 bf16_cell(uint2 u) {
+    return Cell2{pack2(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u)),
+                 pack2(__uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u))};
+}
+
+// x-interpolated corner pair at element o (t0 = the x fraction, packed) and the x
+// difference record[o+1] - record[o].
+__device__ __forceinline__ void xlerp(const F4P* s, uint32_t o, f32x2 t0, Cell2& lerped, Cell2& diff) {
+    Cell2 v;
+    load_pair(s, o, v, diff);
+    lerped = Cell2{fma2(t0, diff.lo, v.lo), fma2(t0, diff.hi, v.hi)};
+}
+__device__ __forceinline__ void xlerp(const B4P* s, uint32_t o, f32x2 t0, Cell2& lerped, Cell2& diff) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(s + o));
+    const Cell2 a = bf16_cell(make_uint2(u.x, u.y)), b = bf16_cell(make_uint2(u.z, u.w));
+    diff = Cell2{sub2(b.lo, a.lo), sub2(b.hi, a.hi)};
+    lerped = Cell2{fma2(t0, diff.lo, a.lo), fma2(t0, diff.hi, a.hi)};
+}
+
+// The record at element o (for reading nodes back).
+__device__ __forceinline__ float4 pair_record(const F4P* s, uint32_t o) { return s[o].v; }
+
+// Trilinear (deta, grad eta) in packed arithmetic from a paired store; bit-identical to
+// `trilinear` on the records.
 template <class E>
 __device__ __forceinline__ float4 trilinear2(const E* s, uint32_t o, float f0, float f1, float f2) {
     const f32x2 t0 = pack2(f0, f0), t1 = pack2(f1, f1), t2 = pack2(f2, f2);
-    Cell2 a0 = lerpc(load_cell2(s, o), load_cell2(s, o + 1), t0);
-    Cell2 a1 = lerpc(load_cell2(s, o + 9), load_cell2(s, o + 10), t0);
-    Cell2 a2 = lerpc(load_cell2(s, o + 81), load_cell2(s, o + 82), t0);
-    Cell2 a3 = lerpc(load_cell2(s, o + 90), load_cell2(s, o + 91), t0);
+    Cell2 a0, a1, a2, a3, d;
+    xlerp(s, o, t0, a0, d);
+    xlerp(s, o + 9, t0, a1, d);
+    xlerp(s, o + 81, t0, a2, d);
+    xlerp(s, o + 90, t0, a3, d);
     Cell2 r = lerpc(lerpc(a0, a1, t1), lerpc(a2, a3, t1), t2);
     float4 v;
     unpack2(r.lo, v.x, v.y);
@@ -212,15 +260,16 @@ __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t) {
                        fmaf(t, b.w - a.w, a.w));
 }
 
-// Trilinear (deta, grad eta) from the 8 corners at base offset o, fractions f.
-template <class E>
-__device__ __forceinline__ float4 trilinear(const E* s, uint32_t o, float f0, float f1, float f2) {
-    float4 c000 = load_cell(s, o), c100 = load_cell(s, o + 1);
-    float4 c010 = load_cell(s, o + 9), c110 = load_cell(s, o + 10);
-    float4 c001 = load_cell(s, o + 81), c101 = load_cell(s, o + 82);
-    float4 c011 = load_cell(s, o + 90), c111 = load_cell(s, o + 91);
-    float4 a0 = lerp4(c000, c100, f0), a1 = lerp4(c010, c110, f0);
-    float4 a2 = lerp4(c001, c101, f0), a3 = lerp4(c011, c111, f0);
+// Trilinear (deta, grad eta) from the 4 pairs at base offset o, fractions f (scalar
+// float32: fma(t, d, v) along x is lerp(record[o], record[o+1]) exactly).
+__device__ __forceinline__ float4 xlerp4(const F4P* s, uint32_t o, float t) {
+    const F4P p = s[o];
+    return make_float4(fmaf(t, p.d.x, p.v.x), fmaf(t, p.d.y, p.v.y), fmaf(t, p.d.z, p.v.z), fmaf(t, p.d.w, p.v.w));
+}
+
+__device__ __forceinline__ float4 trilinear(const F4P* s, uint32_t o, float f0, float f1, float f2) {
+    float4 a0 = xlerp4(s, o, f0), a1 = xlerp4(s, o + 9, f0);
+    float4 a2 = xlerp4(s, o + 81, f0), a3 = xlerp4(s, o + 90, f0);
     float4 b0 = lerp4(a0, a1, f1), b1 = lerp4(a2, a3, f1);
     return lerp4(b0, b1, f2);
 }

@@ -45,10 +45,41 @@ __device__ __forceinline__ double deta_at(const GridDev& g, const float* T, int 
 // coordinates beyond the grid are clamped (those records are never read).
 constexpr int kHalo = kBrickSide + 2;   // 11
 
-template <class E>
+// Store element of each record type: float32 and bfloat16 records are stored as x pairs
+// (F4P, B4P), float64 records as they are.
+template <class R>
+struct StoreElem {
+    using type = R;
+};
+template <>
+struct StoreElem<float4> {
+    using type = F4P;
+};
+template <>
+struct StoreElem<uint2> {
+    using type = B4P;
+};
+
+__device__ __forceinline__ void write_elem(F4P* dst, const float4* rec, int l, bool next) {
+    const float4 a = rec[l], b = next ? rec[l + 1] : a;
+    F4P p;
+    p.v = a;
+    p.d = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);   // float32 subtractions
+    *dst = p;
+}
+__device__ __forceinline__ void write_elem(B4P* dst, const uint2* rec, int l, bool next) {
+    B4P p;
+    p.a = rec[l];
+    p.b = next ? rec[l + 1] : make_uint2(0u, 0u);
+    *dst = p;
+}
+__device__ __forceinline__ void write_elem(D4* dst, const D4* rec, int l, bool) { store_cell<D4>(dst, rec[l].x, rec[l].y, rec[l].z, rec[l].w); }
+
+template <class R>
 __global__ void __launch_bounds__(256) build_store_kernel(GridDev g, const float* __restrict__ T,
-                                                          E* __restrict__ store) {
+                                                          typename StoreElem<R>::type* __restrict__ store) {
     __shared__ double de[kHalo * kHalo * kHalo];
+    __shared__ __align__(32) R rec[kBrickCells];   // records are written with 16-byte stores
     const int b = blockIdx.x;
     const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
     const int ox = bx * kBrick - 1, oy = by * kBrick - 1, oz = bz * kBrick - 1;
@@ -59,7 +90,6 @@ __global__ void __launch_bounds__(256) build_store_kernel(GridDev g, const float
         de[t] = deta_at(g, T, i, j, k);
     }
     __syncthreads();
-    const uint32_t slot = morton3((uint32_t)bx, (uint32_t)by, (uint32_t)bz);
     for (int local = threadIdx.x; local < kBrickCells; local += blockDim.x) {
         const int lx = local % kBrickSide, ly = (local / kBrickSide) % kBrickSide, lz = local / (kBrickSide * kBrickSide);
         const int c[3] = {min(bx * kBrick + lx, g.n[0] - 1), min(by * kBrick + ly, g.n[1] - 1),
@@ -82,8 +112,12 @@ __global__ void __launch_bounds__(256) build_store_kernel(GridDev g, const float
             }
             gr[a] = ddiv(dsub(at(hi[0], hi[1], hi[2]), at(lo[0], lo[1], lo[2])), den);
         }
-        store_cell<E>(store + (size_t)slot * kBrickCells + local, at(c[0], c[1], c[2]), gr[0], gr[1], gr[2]);
+        store_cell<R>(rec + local, at(c[0], c[1], c[2]), gr[0], gr[1], gr[2]);
     }
+    __syncthreads();
+    const uint32_t slot = morton3((uint32_t)bx, (uint32_t)by, (uint32_t)bz);
+    for (int local = threadIdx.x; local < kBrickCells; local += blockDim.x)
+        write_elem(store + (size_t)slot * kBrickCells + local, rec, local, local % kBrickSide < kBrickSide - 1);
 }
 
 // ===================================================================== a3: integrators
@@ -118,7 +152,7 @@ struct FullField<float> {
             float u = (x[a] - (float)g.origin[a]) * g.inv_hf[a] - 0.5f;
             split_coord(u, g.n[a], i[a], f[a]);
         }
-        return trilinear(static_cast<const float4*>(g.store), brick_offset(i[0], i[1], i[2]), f[0], f[1], f[2]);
+        return trilinear(static_cast<const F4P*>(g.store), brick_offset(i[0], i[1], i[2]), f[0], f[1], f[2]);
     }
     __device__ __forceinline__ void rhs(const float x[3], float D[3]) const { rhs_of(at(x), D); }
     __device__ __forceinline__ float eta(const float x[3]) const { return 1.0f + at(x).x; }
@@ -424,13 +458,13 @@ __device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, 
     if constexpr (MODE == 0) {
         return straight_epilogue(S, R, want_hit);
     } else if constexpr (MODE == 1) {
-        CompField<float4> F = {static_cast<const float4*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
+        CompField<F4P> F = {static_cast<const F4P*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
                                {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
-        return trace_comp<float4, INTEG, CONN>(S, F, R, ck, ray, want_hit, steps);
+        return trace_comp<F4P, INTEG, CONN>(S, F, R, ck, ray, want_hit, steps);
     } else if constexpr (MODE == 2) {
-        CompField<uint2> F = {static_cast<const uint2*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
+        CompField<B4P> F = {static_cast<const B4P*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
                               {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
-        return trace_comp<uint2, INTEG, CONN>(S, F, R, ck, ray, want_hit, steps);
+        return trace_comp<B4P, INTEG, CONN>(S, F, R, ck, ray, want_hit, steps);
     } else if constexpr (MODE == 3) {
         FullField<float> F = {S.g};
         steps += (unsigned long long)R.N;
@@ -525,8 +559,13 @@ __global__ void ray_steps_kernel(SceneDev S, int32_t* __restrict__ nsteps) {
     }
 }
 
-template <class E>
-__global__ void export_nodes_kernel(GridDev g, E* __restrict__ out) {
+__device__ __forceinline__ float4 node_record(const F4P& p) { return p.v; }
+__device__ __forceinline__ uint2 node_record(const B4P& p) { return p.a; }
+__device__ __forceinline__ D4 node_record(const D4& p) { return p; }
+
+template <class R>
+__global__ void export_nodes_kernel(GridDev g, R* __restrict__ out) {
+    using E = typename StoreElem<R>::type;
     const long long n = (long long)g.n[0] * g.n[1] * g.n[2];
     const E* st = static_cast<const E*>(g.store);
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
@@ -534,7 +573,7 @@ __global__ void export_nodes_kernel(GridDev g, E* __restrict__ out) {
         // read node (i, j, k) as a corner of the cell whose base is clamped to n-2
         int bi = min(i, g.n[0] - 2), bj = min(j, g.n[1] - 2), bk = min(k, g.n[2] - 2);
         uint32_t o = brick_offset(bi, bj, bk) + (uint32_t)((k - bk) * 81 + (j - bj) * 9 + (i - bi));
-        out[c] = st[o];
+        out[c] = node_record(st[o]);
     }
 }
 
@@ -585,8 +624,8 @@ cudaError_t launch_build_store(const GridDev& g, const float* T, void* store, cu
     const unsigned blocks = (unsigned)g.nb[0] * g.nb[1] * g.nb[2];
     switch (g.prec) {
         case 0: build_store_kernel<D4><<<blocks, 256, 0, st>>>(g, T, (D4*)store); break;
-        case 3: build_store_kernel<uint2><<<blocks, 256, 0, st>>>(g, T, (uint2*)store); break;
-        default: build_store_kernel<float4><<<blocks, 256, 0, st>>>(g, T, (float4*)store); break;
+        case 3: build_store_kernel<uint2><<<blocks, 256, 0, st>>>(g, T, (B4P*)store); break;
+        default: build_store_kernel<float4><<<blocks, 256, 0, st>>>(g, T, (F4P*)store); break;
     }
     return cudaGetLastError();
 }

@@ -24,7 +24,7 @@
 namespace {
 
 // Scratch: 256 bytes of work counters, then the field store.
-constexpr size_t kScratchBytes = (size_t)64 << 20;     // 64 MiB
+constexpr size_t kScratchBytes = (size_t)128 << 20;    // 128 MiB
 constexpr size_t kCounterBytes = 256;
 constexpr int kMaxDevices = 64;
 
@@ -122,7 +122,7 @@ extern "C" bos_status_t bos_render_noalloc(const bos_grid_desc* grid, const floa
     }
     g.K = grid->rho0 * grid->G * grid->T0;
     g.prec = grid->prec;
-    const size_t elem = grid->prec == BOS_PREC_FP64 ? 32 : grid->prec == BOS_PREC_BF16_COMP ? 8 : 16;
+    const size_t elem = grid->prec == BOS_PREC_BF16_COMP ? 16 : 32;   // store element (x pairs, or FP64 records)
     const size_t slots = (size_t)morton3(g.nb[0] - 1, g.nb[1] - 1, g.nb[2] - 1) + 1;
     const size_t store_bytes = slots * kBrickCells * elem;
     if (store_bytes > kScratchBytes - kCounterBytes)

@@ -29,6 +29,14 @@ def test_pixel_sampler_matches_splitmix64(bos, orc):
     want = [(orc.splitmix64_output(seed, draw * n + k + 1) * npx) >> 64 for k in range(n)]
     assert np.array_equal(got, np.array(want))
     assert got.min() >= 0 and got.max() < npx
+    # the same draw with its number read from device memory (1 + 2), and a counter bump
+    ctr = torch.tensor([1], dtype=torch.int64, device="cuda")
+    bos.bos_counter_add(ctr.data_ptr(), 1, sp())
+    pix2 = torch.empty_like(pix)
+    bos.bos_sample_pixels(pix2.data_ptr(), n, npx, seed, 1, sp(), draw_dev=ctr.data_ptr())
+    torch.cuda.synchronize()
+    assert ctr.item() == 2
+    assert torch.equal(pix2, pix)
 
 
 def test_minibatch_loss_and_adabelief_match_torch(bos):
@@ -55,10 +63,16 @@ def test_minibatch_loss_and_adabelief_match_torch(bos):
     s = torch.zeros_like(theta)
     th_ref, m_ref, s_ref = theta.clone().double(), m.clone().double(), s.clone().double()
     lr, b1, b2, eps = 0.01, 0.9, 0.999, 1e-12
+    ctr = torch.tensor([1], dtype=torch.int64, device="cuda")
     for step in range(1, 4):
         grad = torch.as_tensor(rng.standard_normal(1000).astype(np.float32), device="cuda")
-        bos.bos_adabelief_step(theta.data_ptr(), grad.data_ptr(), m.data_ptr(), s.data_ptr(), 1000, lr, b1, b2, eps,
-                               step, sp())
+        if step < 3:
+            bos.bos_adabelief_step(theta.data_ptr(), grad.data_ptr(), m.data_ptr(), s.data_ptr(), 1000, lr, b1, b2,
+                                   eps, step, sp())
+        else:   # step number 1 + *ctr = 3, read on the device
+            ctr += 1
+            bos.bos_adabelief_step(theta.data_ptr(), grad.data_ptr(), m.data_ptr(), s.data_ptr(), 1000, lr, b1, b2,
+                                   eps, 1, sp(), step_dev=ctr.data_ptr())
         gd = grad.double()
         m_ref = b1 * m_ref + (1 - b1) * gd
         s_ref = b2 * s_ref + (1 - b2) * (gd - m_ref) ** 2 + eps
@@ -97,3 +111,55 @@ def test_reconstruction_lowers_the_image_loss(bos):
     # the same loop on the oracle (full-image renders, the same minibatch sizes) falls by
     # more than 1000x in 100 iterations
     assert l0 > 0 and l1 < 0.05 * l0, (l0, l1)
+
+
+def test_graph_replayed_iterations_match_eager_ones(bos):
+    from paper_2509_14442_gb300.recon import Reconstructor
+
+    sc = S.room((24, 24, 18), 96, 96, 1, 3950, pattern_size=64)
+    truth = torch.as_tensor(sc.T, device="cuda")
+    ctx = bos.Context(0)
+    ctx.set_scene(sc, bos.BOS_PREC_FP32_COMP, T=truth)
+    target, _, _ = ctx.render(disp=False)
+    ctx.close()
+    T0 = torch.full_like(truth, S.T_AMBIENT)
+    eager = Reconstructor(sc, target, T0, batch=2048, lr=0.2, loss_scale=1e11, seed=9)
+    graph = Reconstructor(sc, target, T0, batch=2048, lr=0.2, loss_scale=1e11, seed=9)
+    for _ in range(6):
+        eager.step()
+    graph.run(6)
+    torch.cuda.synchronize()
+    assert graph.it == eager.it == 6
+    assert int(graph.it_dev.item()) == int(eager.it_dev.item()) == 6
+    d_e, d_g = eager.T - T0, graph.T - T0
+    assert float(d_e.abs().max()) > 0.1                     # the field moved
+    # same draws and updates; only the float atomics' summation order differs
+    assert float((d_g - d_e).norm() / d_e.norm()) < 1e-3
+    eager.close()
+    graph.close()
+
+
+def _morton2(x, y):
+    def spread(v):
+        v = v & 0xFFFF
+        v = (v | (v << 8)) & 0x00FF00FF
+        v = (v | (v << 4)) & 0x0F0F0F0F
+        v = (v | (v << 2)) & 0x33333333
+        v = (v | (v << 1)) & 0x55555555
+        return v
+    return spread(x) | (spread(y) << 1)
+
+
+@pytest.mark.parametrize("n", [1, 777, 5000, 16384])
+def test_sort_pixels_is_a_z_order_permutation(bos, n):
+    w, h = 100, 100
+    rng = np.random.default_rng(n)
+    pix = rng.integers(0, w * h, n).astype(np.int32)
+    t = torch.as_tensor(pix, device="cuda")
+    bos.bos_sort_pixels(t.data_ptr(), n, w, h, sp())
+    got = t.cpu().numpy()
+    assert np.array_equal(np.sort(got), np.sort(pix))          # same entries, repeats kept
+    keys = np.array([_morton2(int(p) % w, int(p) // w) for p in got])
+    assert np.all(np.diff(keys) >= 0)
+    with pytest.raises(bos.BosError):
+        bos.bos_sort_pixels(t.data_ptr(), 16385, w, h, sp())

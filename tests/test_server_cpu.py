@@ -28,9 +28,10 @@ def request(bos, n=(64, 64, 64), img=(256, 256), adjoint=False, prec=None):
 
 
 def test_footprint_counts_every_buffer(bos):
-    # 64^3 cells: 8 bricks per axis, Morton slots 0..511, 729 float4 records each
+    # 64^3 cells: 8 bricks per axis, Morton slots 0..511, 729 elements each; a float32
+    # element is an x pair of (deta, grad eta) records: 32 bytes
     fwd = bos.bos_request_footprint(request(bos, (64, 64, 64)))
-    assert fwd == 512 * 729 * 16
+    assert fwd == 512 * 729 * 32
     adj = bos.bos_request_footprint(request(bos, (64, 64, 64), adjoint=True))
     # + checkpoints (rays x ceil(N_max / 16) x 48 B), path excess, node accumulators, dL/dI
     rays = 256 * 256
