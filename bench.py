@@ -161,6 +161,10 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm times the ray-tracing workloads, "
+                                                              f"not '{args.workload}'"}))
+        return
     wl = WORKLOADS[args.workload]
     scene = wl["make"](S.BASE_SEED + 2 if wl["adjoint"] else S.BASE_SEED + 1)
     per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))

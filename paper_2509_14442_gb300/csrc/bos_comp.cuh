@@ -182,8 +182,7 @@ __device__ __forceinline__ void comp_setup(const SceneDev& S, const CompField<E>
     float zero[3] = {0.0f, 0.0f, 0.0f};
     float4 v = comp_eval(F, st.U, zero, bc, ci, cf);
     eta_in = 1.0 + (double)v.x;
-    double dt = R.ell / ((double)R.N * eta_in);
-    k.dt = (float)dt;
+    k.dt = (float)sl / (float)eta_in;   // dt = (ell / N) / eta_in; float precision is all it carries
     k.step_len = (float)sl;
 }
 

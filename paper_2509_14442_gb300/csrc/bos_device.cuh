@@ -97,6 +97,8 @@ __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
+// 1/a rounded to nearest: the same double as ddiv(1.0, a)
+__device__ __forceinline__ double drcp(double a) { return __drcp_rn(a); }
 __device__ __forceinline__ double ddot(const double a[3], const double b[3]) {
     return dadd(dadd(dmul(a[0], b[0]), dmul(a[1], b[1])), dmul(a[2], b[2]));
 }
@@ -366,7 +368,7 @@ __device__ __forceinline__ void pinhole_direction(const CamDev& c, const double 
     double b = dmul(dsub(y, c.cy), c.inv_fy);
     for (int i = 0; i < 3; ++i) d[i] = dadd(dsub(dmul(a, right[i]), dmul(b, c.up[i])), c.fwd[i]);
     double n = dsqrt(ddot(d, d));
-    double inv_n = ddiv(1.0, n);
+    double inv_n = drcp(n);
     for (int i = 0; i < 3; ++i) d[i] = dmul(d[i], inv_n);
 }
 
@@ -406,7 +408,7 @@ __device__ __forceinline__ void ray_segment(const SceneDev& S, const double rs[3
             if (rs[a] < S.g.origin[a] || rs[a] > dadd(S.g.origin[a], S.g.extent[a])) inside = false;
             continue;
         }
-        double inv = ddiv(1.0, R.d[a]);
+        double inv = drcp(R.d[a]);
         double t0 = dmul(lo_m[a], inv);
         double t1 = dmul(hi_m[a], inv);
         if (t0 > t1) {
@@ -460,7 +462,7 @@ __device__ __forceinline__ Ray projector_setup(const SceneDev& S, const double b
     const double* P = S.L.proj.pos;
     double q[3];
     for (int a = 0; a < 3; ++a) q[a] = dadd(dsub(base[a], P[a]), (double)e[a]);
-    double inv_n = ddiv(1.0, dsqrt(ddot(q, q)));
+    double inv_n = drcp(dsqrt(ddot(q, q)));
     for (int a = 0; a < 3; ++a) R.d[a] = dmul(q[a], inv_n);
     ray_segment(S, P, S.rc.plo_m, S.rc.phi_m, S.rc.pqn, R);
     return R;

@@ -96,3 +96,27 @@ def test_server_result_matches_oracle(bos, orc):
     o = orc.render(d["scene"])
     e = errors(dict(I=d["I"].cpu().numpy().astype(np.float64), disp=d["disp"].cpu().numpy().astype(np.float64)), o)
     assert e["I_abs"] <= I_ABS_TOL and e["disp_rel"] <= DISP_REL_TOL, e
+
+
+def test_refracted_requests_alone_equal_results_in_the_mix(bos):
+    # requests lit through the refracted projector connection (light mode 2) share the
+    # server with straight-connection ones; each result is the same as alone
+    reqs = []
+    for i, s in enumerate(SPECS[:6]):
+        d = make(bos, 100 + i, s)
+        if i % 2 == 0:
+            sc = d["scene"]
+            d["scene"] = sc.replace(light=S.Light(2, sc.light.pattern, sc.light.proj, connect_iters=1))
+        reqs.append(d)
+    ref = [alone(bos, d) for d in reqs]
+    srv = bos.Server(0, 2 << 30, 3)
+    tickets = [submit(bos, srv, d) for d in reqs]
+    for t in tickets:
+        assert srv.wait(t, 120.0) == bos.BOS_OK
+    torch.cuda.synchronize()
+    srv.close()
+    for d, r in zip(reqs, ref):
+        assert torch.equal(d["I"], r["I"])
+        assert torch.equal(d["disp"], r["disp"])
+        if "dLdT" in d:
+            assert torch.linalg.norm(d["dLdT"] - r["dLdT"]) <= 1e-5 * torch.linalg.norm(r["dLdT"])

@@ -43,6 +43,14 @@ def test_footprint_counts_every_buffer(bos):
     q = request(bos, (64, 64, 64), adjoint=True)
     q.integ.integrator = 2
     assert bos.bos_request_footprint(q) == fwd + 48 * rays + rays * 4 + 64 ** 3 * 16 + rays * 4
+    # the refracted projector connection adds the projector rays' checkpoints and a
+    # 32-byte connection record per ray (adjoint only)
+    r2 = request(bos, (64, 64, 64), adjoint=True)
+    r2.light.mode, r2.light.connect_iters = 2, 1
+    assert bos.bos_request_footprint(r2) == expect + ck + 32 * rays
+    f2 = request(bos, (64, 64, 64))
+    f2.light.mode, f2.light.connect_iters = 2, 1
+    assert bos.bos_request_footprint(f2) == fwd
     # bigger grids and images need more
     assert bos.bos_request_footprint(request(bos, (128, 128, 96))) > fwd
     assert bos.bos_request_footprint(request(bos, img=(512, 512), adjoint=True)) > adj
