@@ -59,13 +59,15 @@ typedef enum {
 
 /* Arithmetic of the field store and of the integrator.
  *  FP64:       float64 store (32 B per cell), float64 ray state.
- *  FP32:       float32 store (16 B per cell), plain float32 absolute ray state.
+ *  FP32:       float32 store (32 B per cell: the cell's record and its difference to
+ *              the next cell along x), plain float32 absolute ray state.
  *  FP32_COMP:  float32 store; each ray keeps its straight line in 32.32 fixed
  *              point (grid units) derived from its float64 origin and integrates
  *              only its small deviation from that line in float32 with
  *              compensated (Kahan) sums; float64 only at the ray origin and the
  *              wall intersection.
- *  BF16_COMP:  as FP32_COMP with a bfloat16 store (8 B per cell). */
+ *  BF16_COMP:  as FP32_COMP with a bfloat16 store (16 B per cell: the cell's record
+ *              and the next one along x). */
 typedef enum {
     BOS_PREC_FP64 = 0,
     BOS_PREC_FP32 = 1,
@@ -146,8 +148,9 @@ bos_status_t bos_destroy(bos_ctx* ctx);
  * all > 0).  Per cell, in float64: deta = rho0 G T0 / T; grad eta by central
  * differences (deta[i+1] - deta[i-1]) / (2h), one-sided (deta[1]-deta[0])/h at the
  * faces; then rounded to the store type of desc->prec.  The store is a Morton-ordered
- * array of 8x8x8-cell bricks with a one-cell apron, so every trilinear corner is one
- * 16-byte (bf16: 8-byte, fp64: 32-byte) load at a fixed offset.
+ * array of 8x8x8-cell bricks with a one-cell apron, so every trilinear corner sits at a
+ * fixed offset; float32 and bf16 stores keep x pairs, so a cell's 8 corners are four
+ * 32-byte (bf16: 16-byte) loads, and a float64 store eight 32-byte loads.
  * T_dev must stay allocated and unchanged until the last bos_backward that uses
  * this grid (the adjoint's chain rule d eta / dT = -rho0 G T0 / T^2 reads it). */
 bos_status_t bos_set_grid(bos_ctx* ctx, const bos_grid_desc* desc, const float* T_dev, void* stream);

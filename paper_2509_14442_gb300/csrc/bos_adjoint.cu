@@ -24,9 +24,6 @@ namespace bos {
 #define BOS_ADJ_WARPS 2
 #endif
 constexpr int kAdjWarps = BOS_ADJ_WARPS;   // warps per block
-#ifndef BOS_ACC_SCALAR
-#define BOS_ACC_SCALAR 0                  // accumulate cell rows with scalar (1) or packed (0) FMAs
-#endif
 #ifndef BOS_ADJ_MIN_BLOCKS
 #define BOS_ADJ_MIN_BLOCKS 5              // resident blocks per SM the register budget is cut for
 #endif
@@ -193,18 +190,6 @@ __device__ __forceinline__ void accumulate(float* rows, bool act, uint32_t cell,
         ca.key = key;
         float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
         const float g0 = 1.0f - cf[0], g1 = 1.0f - cf[1], g2 = 1.0f - cf[2];
-#if BOS_ACC_SCALAR
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float w = ((c & 1) ? cf[0] : g0) * ((c & 2) ? cf[1] : g1) * ((c & 4) ? cf[2] : g2);
-            float4 r = row[c];
-            r.x = fmaf(w, Q.x, r.x);
-            r.y = fmaf(w, Q.y, r.y);
-            r.z = fmaf(w, Q.z, r.z);
-            r.w = fmaf(w, Q.w, r.w);
-            row[c] = r;
-        }
-#else
         const f32x2 qlo = pack2(Q.x, Q.y), qhi = pack2(Q.z, Q.w);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -216,7 +201,6 @@ __device__ __forceinline__ void accumulate(float* rows, bool act, uint32_t cell,
             unpack2(hi, r.z, r.w);
             row[c] = r;
         }
-#endif
     }
 }
 
@@ -636,6 +620,30 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
 // is known from the final state and a running prefix of u: one sweep in forward order
 // recomputes the samples and scatters every stage's sensitivity (the end sample of a
 // step and the start sample of the next are one point and one scatter).
+// A quasi-linear line sample: its cell and the field value only (the samples sit on the
+// straight line, so no position adjoint and hence no field gradient is needed).
+struct LineSample {
+    uint32_t key;
+    float cf[3];
+    float4 v;   // (deta, grad eta)
+};
+
+template <class E>
+__device__ __forceinline__ void line_sample(const CompField<E>& F, const long long U[3], BrickCache& bc,
+                                            LineSample& p) {
+    const float zero[3] = {0.0f, 0.0f, 0.0f};
+    int ci[3];
+    comp_cell(F, U, zero, ci, p.cf);
+    p.key = cell_key_of(F, ci);
+    p.v = trilinear2(F.store, cached_offset(bc, ci[0], ci[1], ci[2]), p.cf[0], p.cf[1], p.cf[2]);
+}
+
+// Corner record of D = (1 + deta) grad at a line sample for the adjoint Db of D.
+__device__ __forceinline__ float4 line_corner_record(const float4 v, const float Db[3]) {
+    const float eta = 1.0f + v.x;
+    return make_float4(Db[0] * v.y + Db[1] * v.z + Db[2] * v.w, eta * Db[0], eta * Db[1], eta * Db[2]);
+}
+
 template <class E>
 __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_quasi_kernel(SceneDev S, CkptDev ck, AdjDev adj,
                                                                        WorkDev wk) {
@@ -711,17 +719,17 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_quasi_kernel(SceneDev 
             const float dt = act ? k.dt : 0.0f;
             BrickCache bc = {kNoKey, 0u};
             // the start sample of step 0
-            Stage p0 = {};
+            LineSample p0 = {};
             float A[3] = {0, 0, 0}, dv[3] = {0, 0, 0}, prefix[3] = {0, 0, 0}, carry[3] = {0, 0, 0}, dtb = 0.0f;
             if (act) {
-                stage_eval(F, st.U, zero, bc, p0);
+                line_sample(F, st.U, bc, p0);
                 float D[3];
-                rhs_from(p0.ig, D);
+                rhs_of(p0.v, D);
                 for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
             }
             for (int n = 0; n < n_max; ++n) {
                 const bool a_ = act && n < N;
-                Stage pm = {}, pe = {};
+                LineSample pm = {}, pe = {};
                 float B[3] = {0, 0, 0}, C[3] = {0, 0, 0}, u[3] = {0, 0, 0}, Dm[3] = {0, 0, 0}, De[3] = {0, 0, 0};
                 float Db0[3] = {0, 0, 0}, Dbm[3] = {0, 0, 0};
                 if (a_) {
@@ -730,10 +738,10 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_quasi_kernel(SceneDev 
                         U2[a] = st.U[a] + (long long)n * k.dU[a] + k.dUh[a];
                         U3[a] = st.U[a] + (long long)(n + 1) * k.dU[a];
                     }
-                    stage_eval(F, U2, zero, bc, pm);
-                    rhs_from(pm.ig, Dm);
-                    stage_eval(F, U3, zero, bc, pe);
-                    rhs_from(pe.ig, De);
+                    line_sample(F, U2, bc, pm);
+                    rhs_of(pm.v, Dm);
+                    line_sample(F, U3, bc, pe);
+                    rhs_of(pe.v, De);
                     float inc[3], nn = 0.0f;
                     for (int a = 0; a < 3; ++a) {
                         B[a] = dt * Dm[a];
@@ -762,18 +770,16 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_quasi_kernel(SceneDev 
                         A[a] = C[a];
                     }
                 }
-                float pb[3];
                 float4 Q = make_float4(0, 0, 0, 0);
-                if (a_) rhs_adjoint(F, p0.ig, Db0, pb, Q);
+                if (a_) Q = line_corner_record(p0.v, Db0);
                 accumulate(rows, a_, p0.key, p0.cf, Q, ca, acc, nx, nxy);
-                if (a_) rhs_adjoint(F, pm.ig, Dbm, pb, Q);
+                if (a_) Q = line_corner_record(pm.v, Dbm);
                 accumulate(rows, a_, pm.key, pm.cf, Q, ca, acc, nx, nxy);
                 if (a_) p0 = pe;
             }
             // the end sample of the last step, then eta_in = 1 + deta(r_in)
-            float pb[3];
             float4 Q = make_float4(0, 0, 0, 0);
-            if (act) rhs_adjoint(F, p0.ig, carry, pb, Q);
+            if (act) Q = line_corner_record(p0.v, carry);
             accumulate(rows, act, p0.key, p0.cf, Q, ca, acc, nx, nxy);
             int ci[3] = {0, 0, 0};
             float cf[3] = {0, 0, 0};

@@ -230,6 +230,9 @@ __device__ __forceinline__ void comp_run(const SceneDev& S, const CompField<E>& 
         const float dt = k.dt;
         rhs_of(comp_eval(F, st.U, zero, bc, ci, cf), D);
         for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
+        // two steps per iteration: their four line samples do not depend on one another,
+        // so their gathers overlap (the quasi-linear kernel gets a larger register budget for this)
+#pragma unroll 2
         for (int n = 0; n < R.N; ++n) {
             long long U2[3], U3[3];
             for (int a = 0; a < 3; ++a) {
@@ -480,7 +483,10 @@ template <int MODE, int INTEG, bool CONN>
 #ifndef BOS_FWD_MIN_BLOCKS
 #define BOS_FWD_MIN_BLOCKS 6              // resident 128-thread blocks per SM the register budget is cut for
 #endif
-__global__ void __launch_bounds__(128, BOS_FWD_MIN_BLOCKS) render_kernel(SceneDev S, RenderOut out, WorkDev wk, CkptDev ck) {
+#ifndef BOS_FWD_QUASI_MIN_BLOCKS
+#define BOS_FWD_QUASI_MIN_BLOCKS 3        // the same for quasi-linear tracing (more registers, more overlap)
+#endif
+__global__ void __launch_bounds__(128, INTEG == 2 ? BOS_FWD_QUASI_MIN_BLOCKS : BOS_FWD_MIN_BLOCKS) render_kernel(SceneDev S, RenderOut out, WorkDev wk, CkptDev ck) {
     const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
     const TileShape ts = tile_shape(W, H, spp);
     const int ntiles = tile_count(S, ts);
