@@ -443,6 +443,12 @@ def gpu_arm(args):
                 "note": ("gather roofline R = L2 read bandwidth / algorithmic bytes per ray-step; the gathers "
                          "hit L1 (ncu: ~95 % forward, ~80 % adjoint), so a kernel can exceed R"),
                 "kernels": kernels, "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    if dk["traffic"] is not None and peaks.get("hbm_gbs"):
+        # the same kernel against the HBM roofline: measured DRAM bytes per launch over its time
+        # (its timed region also clears the accumulators and runs the gradient epilogue)
+        hbm_gbs = dk["traffic"] / (dk["ms"] * 1e-3) / 1e9
+        roofline["hbm"] = {"achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                           "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         r, threads, desc = oracle_rate(scene, wl["adjoint"], args.cpu_seconds)
