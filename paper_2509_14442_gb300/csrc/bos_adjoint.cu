@@ -20,10 +20,7 @@
 
 namespace bos {
 
-#ifndef BOS_ADJ_WARPS
-#define BOS_ADJ_WARPS 2
-#endif
-constexpr int kAdjWarps = BOS_ADJ_WARPS;   // warps per block
+constexpr int kAdjWarps = kAdjWarpsPerBlock;   // warps per block
 #ifndef BOS_ADJ_MIN_BLOCKS
 #define BOS_ADJ_MIN_BLOCKS 5              // resident blocks per SM the register budget is cut for
 #endif
@@ -272,7 +269,7 @@ __device__ __forceinline__ void straight_aim_adjoint(const SceneDev& S, const Ra
 }
 
 __host__ __device__ constexpr size_t adj_warp_floats(int K) {
-    return (size_t)K * 6 * 32 + 32 * kRow + 2 * 32 * kStageStride;
+    return (size_t)32 * kRow + 2 * 32 * kStageStride;   // K is carried by the global segment states
 }
 
 template <class E, bool CONN_T>
@@ -293,8 +290,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
     double* const tpb = xlum + 15;
     double* const nqp = xlum + 18;
     const int K = ck.every;
-    float* st_buf = reinterpret_cast<float*>(smem4) + (size_t)warp * adj_warp_floats(K);   // [K][6][32]
-    float* rows = st_buf + (size_t)K * 6 * 32;                                             // [32][kRow]
+    float* rows = reinterpret_cast<float*>(smem4) + (size_t)warp * adj_warp_floats(K);      // [32][kRow]
+    // [K][6][32] step states of the segment being reversed (this warp's slice)
+    float* st_buf = adj.seg + ((size_t)blockIdx.x * kAdjWarps + warp) * ((size_t)K * 6 * 32);
     float* stg = rows + 32 * kRow;                                                          // [2][32][kStageStride]
     const CompField<E> F = {static_cast<const E*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
                             {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
@@ -829,8 +827,9 @@ static cudaError_t launch_adjoint_c(const SceneDev& S, const CkptDev& ck, const 
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel<E, CONN>, kAdjWarps * 32, smem);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    adjoint_kernel<E, CONN><<<num_sms * per_sm, kAdjWarps * 32, smem, st>>>(S, ck, adj, w);
+    if (per_sm < 1 || adj.seg == nullptr) return cudaErrorInvalidConfiguration;
+    const int blocks = num_sms * per_sm < kAdjMaxBlocks ? num_sms * per_sm : kAdjMaxBlocks;
+    adjoint_kernel<E, CONN><<<blocks, kAdjWarps * 32, smem, st>>>(S, ck, adj, w);
     return cudaGetLastError();
 }
 

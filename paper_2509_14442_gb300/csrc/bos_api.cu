@@ -128,6 +128,8 @@ struct bos_ctx {
     long long saved_npix = 0;
 
     float4* acc = nullptr;
+    float* seg = nullptr;           // adjoint segment states
+    size_t seg_bytes = 0;
     size_t acc_bytes = 0;
 
     // Optional caller-provided device arena: when set, buffers are carved from it and
@@ -244,11 +246,13 @@ RayConst ray_const_of(const SceneDev& S) {
 // context's grid, geometry and saved render.
 void ctx_bind_arena(bos_ctx* c, void* base, size_t bytes, cudaStream_t stream) {
     if (!c->arena) {
-        void* bufs[] = {c->store, c->ckpt, c->excess, c->acc, c->pckpt, c->conn};
+        void* bufs[] = {c->store, c->ckpt, c->excess, c->acc, c->pckpt, c->conn, c->seg};
         for (void* p : bufs)
             if (p) cudaFree(p);
         c->bytes = 256;
     }
+    c->seg = nullptr;
+    c->seg_bytes = 0;
     c->store = nullptr;
     c->ckpt = nullptr;
     c->excess = nullptr;
@@ -291,6 +295,7 @@ size_t request_bytes(const bos_grid_desc& g, const bos_camera_desc& cam, const b
             bytes += align_up(2 * nslots * sizeof(float4));
         }
         bytes += align_up((size_t)g.nx * g.ny * g.nz * sizeof(float4));
+        if (it.integrator != 2) bytes += align_up(adjoint_segment_bytes(it.ckpt_every));
     }
     return bytes;
 }
@@ -356,7 +361,7 @@ bos_status_t bos_destroy(bos_ctx* c) {
     DeviceGuard dg(c->device);
     if (c->small) cudaFree(c->small);
     if (!c->arena) {
-        void* bufs[] = {c->store, c->ckpt, c->excess, c->acc, c->pckpt, c->conn};
+        void* bufs[] = {c->store, c->ckpt, c->excess, c->acc, c->pckpt, c->conn, c->seg};
         for (void* p : bufs)
             if (p) cudaFree(p);
     }
@@ -569,11 +574,16 @@ bos_status_t bos_backward(bos_ctx* c, const float* dLdI, float* dLdT, void* stre
     size_t cells = (size_t)c->g.n[0] * c->g.n[1] * c->g.n[2];
     bos_status_t s = dev_alloc(c, (void**)&c->acc, &c->acc_bytes, cells * sizeof(float4), "bos_backward: accumulators");
     if (s != BOS_OK) return s;
+    if (c->integ.integrator != 2) {   // the quasi-linear adjoint keeps no segment states
+        s = dev_alloc(c, (void**)&c->seg, &c->seg_bytes, adjoint_segment_bytes(c->saved_ck.every),
+                      "bos_backward: segment states");
+        if (s != BOS_OK) return s;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(c->acc, 0, cells * sizeof(float4), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->small, 0, 4, st);
     if (e != cudaSuccess) return cuda_fail(e, "bos_backward: memset");
-    AdjDev adj{c->acc, dLdI, c->err};
+    AdjDev adj{c->acc, dLdI, c->err, c->seg};
     WorkDev w{c->tile_counter, c->steps, c->err};
     SceneDev S = scene_of(c);
     S.pix = c->saved_pix;
