@@ -104,3 +104,75 @@ def test_refracted_backward_limits_are_reported(bos):
         ctx.render()
     assert e.value.status == bos.BOS_ERR_UNIMPLEMENTED
     ctx.close()
+
+
+# ------------------------------------------------- full size (the benchmarked launch)
+
+@pytest.mark.slow
+def test_refracted_full_size_sampled(bos, orc):
+    sc = refracted(S.room_adjoint(), boost=1.0)      # 256x256x192, 2048^2, 1 spp, unscaled plume
+    g = gpu_render(sc, bos.BOS_PREC_FP32_COMP)
+    pix = np.random.default_rng(5).choice(sc.pixels, 400, replace=False)
+    e = errors(g, orc.render(sc, pix=pix), pix)
+    assert e["I_abs"] <= I_ABS_TOL and e["disp_rel"] <= DISP_REL_TOL, e
+
+
+def _box_hits(origin, d, center, margin):
+    lo, hi = np.asarray(center) - margin, np.asarray(center) + margin
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t0 = (lo - origin) / d
+        t1 = (hi - origin) / d
+    tmin = np.nanmax(np.minimum(t0, t1), axis=-1)
+    tmax = np.nanmin(np.maximum(t0, t1), axis=-1)
+    return (tmin <= tmax).reshape(-1)
+
+
+def _pixels_near_either_ray(scene, center, margin):
+    """Pixels whose straight camera ray, or the projector ray aimed at that ray's wall hit,
+    passes within `margin` (a box) of `center`: the only pixels a voxel there can change."""
+    c, w, P = scene.camera, scene.wall, np.asarray(scene.light.proj.pos, dtype=np.float64)
+    px, py = np.meshgrid(np.arange(c.width) + 0.5, np.arange(c.height) + 0.5, indexing="xy")
+    fwd, up = np.array(c.fwd), np.array(c.up)
+    right = np.cross(fwd, up)
+    d = ((px - c.cx) / c.fx)[..., None] * right - ((py - c.cy) / c.fy)[..., None] * up + fwd
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    pos, n = np.array(c.pos), np.array(w.normal)
+    tw = ((np.array(w.origin) - pos) @ n) / (d @ n)
+    xw = pos + tw[..., None] * d
+    dp = xw - P
+    dp /= np.linalg.norm(dp, axis=-1, keepdims=True)
+    hit = _box_hits(pos, d, center, margin) | _box_hits(P, dp, center, margin)
+    return np.flatnonzero(hit)
+
+
+@pytest.mark.slow
+def test_refracted_adjoint_full_size_against_oracle_finite_differences(bos, orc):
+    # the benchmarked refracted launch: dL/dT at 16 seeded plume voxels against central
+    # differences of the oracle (h = 0.01 K) over the pixels the voxel can reach through the
+    # camera ray or the projector ray
+    sc = refracted(S.room_adjoint(), boost=1.0)
+    rng = np.random.default_rng(65)
+    w = rng.standard_normal((sc.camera.height, sc.camera.width))
+    g_gpu = gpu_grad(bos, sc, w)
+    hot = np.argwhere(sc.T > 300.0)
+    vox = hot[rng.choice(len(hot), 16, replace=False)]
+    hgrid = np.array(sc.grid.spacing())
+    eps = 1e-2
+    T64 = sc.T.astype(np.float64)
+    fd, gp = [], []
+    for k, j, i in vox:
+        center = np.array(sc.grid.origin) + (np.array([i, j, k]) + 0.5) * hgrid
+        pix = _pixels_near_either_ray(sc, center, 3.0 * hgrid + 1e-3)
+        vals = []
+        for sgn in (1.0, -1.0):
+            T = T64.copy()
+            T[k, j, i] += sgn * eps
+            I = orc.render(sc.replace(T=T), pix=pix)["I"]
+            vals.append(float((w.reshape(-1)[pix] * I).sum()))
+        fd.append((vals[0] - vals[1]) / (2 * eps))
+        gp.append(g_gpu[k, j, i])
+    fd, gp = np.array(fd), np.array(gp)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    bad = np.abs(gp - fd) > 1e-3 * np.abs(fd) + 1e-3 * scale
+    assert bad.sum() == 0, (np.flatnonzero(bad), gp[bad], fd[bad])
