@@ -80,6 +80,29 @@ BYTES_PER_STEP = {"fp32_comp": 384, "fp32": 384, "bf16_comp": 192, "fp64": 768}
 # scatters those 2 points: 512 B.)
 ADJ_BYTES_PER_STEP = {"fp32_comp": 3 * 384, "bf16_comp": 2 * 192 + 384}
 L2_BYTES = 129 * 2 ** 20
+# Algorithmic floating-point operations of one ray-step (an FMA counts 2), counted from the
+# method's formulas, not from the kernels (which add the compensation of the fixed-point
+# straight line, bounds tests and index arithmetic):
+#   field evaluation D(r) = (1 + deta) grad eta at a point: 3 fractions (sub, mul) = 6,
+#     trilinear interpolation of the 4 channels, 7 lerps x 3 flops each = 84, D = 4:  94
+#   Sharma RKN step (Sec. 2.2, Eq. 1): 3 evaluations 282, A, B, C = dt D 9, the two inner
+#     stage points 24, the position update 18, the velocity update 15, the path-length
+#     increment |dr| 8:  356
+#   quasi-linear step: 2 new line samples (point on the line 6 + 94 each) 200, the same
+#     updates and path length 41:  241
+#   adjoint of an RKN step: the segment recompute 356, 3 value-and-fraction-derivative
+#     evaluations 3 x (6 + 4 x 36) = 450, the adjoint of D per stage 3 x 36 = 108, the
+#     transpose of the step's linear combinations 66, the path-length adjoint 11, and the
+#     corner scatter per stage (3 complements, 8 weights x 2, 8 x 4 FMAs) 3 x 83 = 249:  1240
+#   one-sweep quasi-linear adjoint: per line sample the point, fractions and value 96, the
+#     adjoint of D 9 and the corner scatter 83 (2 samples: 376), the velocity adjoint 24:  400
+FLOPS_PER_STEP = {"rkn": 356, "quasi": 241}
+ADJ_FLOPS_PER_STEP = {"rkn": 1240, "quasi": 400}
+# The arithmetic peak: 152 SMs x 128 float32 FMA lanes x 2 flops x the SM clock (derived
+# from the unit counts; the in-run probe measures it as well).  Float64: GB300's nominal
+# 1.25 TFLOP/s at 2070 MHz.
+FP32_LANES_PER_SM = 128
+FP64_NOMINAL_FLOPS = 1.25e12
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the timed kernels,
 # from one ncu capture of the default workload (profiles/adjoint_kernel_room_adj.md).  It is
@@ -275,6 +298,27 @@ def l2_read_peak(torch, dev, bos):
     return nbytes * reps / (best * 1e-3) / 1e9
 
 
+def fma_peaks(torch, dev, bos):
+    """FMA throughput of this GPU (TFLOP/s): float32, packed float32 pairs and float64, each
+    the best of 5 launches of the probe (about 2-4 ms each)."""
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    sp = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for name, kind, reps in (("fp32", 0, 4000), ("fp32x2", 1, 4000), ("fp64", 2, 100)):
+        bos.bos_probe_fma(kind, reps, sink.data_ptr(), sp)
+        best = 1e30
+        flops = 0.0
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            flops = bos.bos_probe_fma(kind, reps, sink.data_ptr(), sp)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name] = flops / (best * 1e-3) / 1e12
+    return out
+
+
 def aggregate(my_ms: float, units_per_rank: int, dist=None, device=None):
     """Whole-job rate of a weak-scaling run: every rank processed `units_per_rank` units in
     `my_ms` of device time; the job took the slowest rank's time.  Returns (job_ms, units/s)."""
@@ -415,37 +459,63 @@ def gpu_arm(args):
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_value = steps_per_frame * args.steps / (sum(e2e_ms) * 1e-3) * world
 
-    # ---- roofline of the tracer (the dominant forward kernel)
+    # ---- roofline of the timed kernels
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     l2_peak = l2_read_peak(torch, dev, bos)
+    probe = fma_peaks(torch, dev, bos)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clock_mhz = float(peaks.get("sm_max_mhz") or 2070.0)
+    if args.prec == "fp64":
+        derived = FP64_NOMINAL_FLOPS * clock_mhz / 2070.0 / 1e12
+        measured = probe["fp64"]
+        alu_src = (f"float64: GB300 nominal 1.25 TFLOP/s at 2070 MHz, scaled to {clock_mhz:.0f} MHz; "
+                   f"in-run probe {measured:.2f} TFLOP/s; the larger is the peak")
+    else:
+        derived = sms * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+        measured = max(probe["fp32"], probe["fp32x2"])
+        alu_src = (f"float32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x {clock_mhz:.0f} MHz "
+                   f"= {derived:.1f} TFLOP/s (derived); in-run probe {measured:.1f} TFLOP/s; the larger is the peak")
+    alu_peak = max(derived, measured)
+    integ = {0: "rkn", 2: "quasi"}.get(scene.integ.integrator)
     render_avg_ms = statistics.mean(render_ms)
     fwd_b = wl.get("fwd_bytes", BYTES_PER_STEP[args.prec])
     adj_b = wl.get("adj_bytes", ADJ_BYTES_PER_STEP.get(args.prec, 0))
-    fwd_gbs = fwd_b * steps_per_frame / (render_avg_ms * 1e-3) / 1e9
-    kernels = {"render_kernel": {"ms": render_avg_ms, "bytes_per_ray_step": fwd_b,
-                                 "achieved_gbs": fwd_gbs, "frac": fwd_gbs / l2_peak,
-                                 "traffic": kernel_traffic(args.workload, "render_kernel")}}
+
+    def kernel_entry(ms, flops_per_step, bytes_per_step, name):
+        tflops = flops_per_step * steps_per_frame / (ms * 1e-3) / 1e12 if flops_per_step else None
+        gbs = bytes_per_step * steps_per_frame / (ms * 1e-3) / 1e9
+        return {"ms": ms, "flops_per_ray_step": flops_per_step, "achieved_tflops": tflops,
+                "frac": tflops / alu_peak if tflops is not None else None,
+                "bytes_per_ray_step": bytes_per_step, "achieved_gbs": gbs, "l2_frac": gbs / l2_peak,
+                "traffic": kernel_traffic(args.workload, name)}
+
+    kernels = {"render_kernel": kernel_entry(render_avg_ms, FLOPS_PER_STEP.get(integ), fwd_b, "render_kernel")}
     dominant = "render_kernel"
     if wl["adjoint"]:
-        back_avg_ms = statistics.mean(back_ms)
-        adj_gbs = adj_b * steps_per_frame / (back_avg_ms * 1e-3) / 1e9
-        kernels["adjoint_kernel"] = {"ms": back_avg_ms, "bytes_per_ray_step": adj_b,
-                                     "achieved_gbs": adj_gbs, "frac": adj_gbs / l2_peak,
-                                     "traffic": kernel_traffic(args.workload, "adjoint_kernel"),
-                                     "timed": "bos_backward: accumulator clear + adjoint_kernel + gradient_kernel"}
+        kernels["adjoint_kernel"] = kernel_entry(statistics.mean(back_ms), ADJ_FLOPS_PER_STEP.get(integ), adj_b,
+                                                 "adjoint_kernel")
+        kernels["adjoint_kernel"]["timed"] = "bos_backward: accumulator clear + adjoint_kernel + gradient_kernel"
         dominant = "adjoint_kernel"
     dk = kernels[dominant]
-    roofline = {"bound": "l2", "kernel": dominant, "achieved": dk["achieved_gbs"], "peak": l2_peak, "unit": "GB/s",
-                "frac": dk["frac"], "traffic": dk["traffic"],
-                "peak_source": "in-run L2 read probe (bos_probe_read, 24 MiB x 50 passes, best of 10)",
-                "bytes_per_ray_step": dk["bytes_per_ray_step"],
-                "note": ("gather roofline R = L2 read bandwidth / algorithmic bytes per ray-step; the gathers "
-                         "hit L1 (ncu: ~95 % forward, ~80 % adjoint), so a kernel can exceed R"),
-                "kernels": kernels, "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    roofline = {"bound": "alu", "kernel": dominant, "achieved": dk["achieved_tflops"], "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": dk["frac"], "traffic": dk["traffic"], "peak_source": alu_src,
+                "flops_per_ray_step": dk["flops_per_ray_step"],
+                "fma_probe_tflops": probe,
+                "note": ("algorithmic flops per ray-step counted from the method's formulas; the gathers are "
+                         "served on chip and DRAM carries only the store, checkpoints and outputs, so the "
+                         "arithmetic roof is the one that applies; the kernels sit below it, limited by "
+                         "instruction latency at 12 (adjoint) / 24 (forward) warps per SM"),
+                "kernels": kernels,
+                "l2": {"achieved": dk["achieved_gbs"], "peak": l2_peak, "unit": "GB/s", "frac": dk["l2_frac"],
+                       "bytes_per_ray_step": dk["bytes_per_ray_step"],
+                       "peak_source": "in-run L2 read probe (bos_probe_read, 24 MiB x 50 passes, best of 10)",
+                       "note": ("gather roofline R = L2 read bandwidth / algorithmic gathered bytes per ray-step; "
+                                "the gathers hit L1, so a kernel can exceed R")},
+                "hbm_peak_gbs": peaks.get("hbm_gbs")}
     if dk["traffic"] is not None and peaks.get("hbm_gbs"):
         # the same kernel against the HBM roofline: measured DRAM bytes per launch over its time
-        # (its timed region also clears the accumulators and runs the gradient epilogue)
+        # (the backward's timed region also clears the accumulators and runs the gradient epilogue)
         hbm_gbs = dk["traffic"] / (dk["ms"] * 1e-3) / 1e9
         roofline["hbm"] = {"achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                            "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
@@ -692,6 +762,11 @@ def precision_arm(args):
         return {"disp_rel": float(np.abs(D.reshape(-1, 2)[pix] - ref["disp"]).max()) / dmax,
                 "I_abs": float(np.abs(I.reshape(-1)[pix] - ref["I"]).max())}
 
+    # arithmetic peaks (as in the main bench line: the larger of the derived and the probed)
+    probe = fma_peaks(torch, dev, bos)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = max(sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12, probe["fp32"], probe["fp32x2"])
+    fp64_peak = max(FP64_NOMINAL_FLOPS / 1e12, probe["fp64"])
     out = {}
     for name in ("fp64", "fp32", "fp32_comp", "bf16_comp"):
         ctx = bos.Context(0)
@@ -709,7 +784,12 @@ def precision_arm(args):
         ctx.status()
         steps = ctx.last_ray_steps()
         Ih, Dh = I.cpu().numpy().astype(np.float64), D.cpu().numpy().astype(np.float64)
-        r = {"render_ms": statistics.mean(ms), "ray_steps_per_s": steps / (statistics.mean(ms) * 1e-3),
+        rate = steps / (statistics.mean(ms) * 1e-3)
+        tflops = rate * FLOPS_PER_STEP["rkn"] / 1e12
+        peak = fp64_peak if name == "fp64" else fp32_peak
+        r = {"render_ms": statistics.mean(ms), "ray_steps_per_s": rate,
+             "alu": {"achieved_tflops": tflops, "peak_tflops": peak, "frac": tflops / peak,
+                     "dtype": "f64" if name == "fp64" else "f32"},
              "vs_fp64_oracle": err(Ih, Dh, orc)}
         if name == "bf16_comp":
             r["vs_oracle_on_bf16_field"] = err(Ih, Dh, orc_bf16)
@@ -722,7 +802,7 @@ def precision_arm(args):
         "config": {"workload": "precision", "grid": list(scene.grid.n), "image": [scene.camera.width,
                    scene.camera.height], "spp": scene.camera.spp, "sample_pixels": args.sample_pixels,
                    "max_displacement_m": dmax, "oracle_seconds": t_orc, "oracle_threads": threads},
-        "precisions": out}))
+        "fma_probe_tflops": probe, "precisions": out}))
 
 
 def main():

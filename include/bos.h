@@ -257,6 +257,15 @@ bos_status_t bos_export_nodes(bos_ctx* ctx, void* out_dev, void* stream);
  * the tracer's gathers.  sink_dev (1 float) is written only to keep the loads alive. */
 bos_status_t bos_probe_read(const void* buf_dev, uint64_t bytes, int repeats, float* sink_dev, void* stream);
 
+/* Measurement probe, no counterpart in the paper: the fused multiply-add throughput of
+ * this GPU.  kind 0 = float32 fma, 1 = packed float32 pairs (fma.rn.f32x2), 2 = float64
+ * fma.  Launches 4 blocks of 256 threads per SM; each thread runs eight independent
+ * recurrences x <- x*a + b for repeats x 16 rounds.  The caller times the launch on
+ * `stream`; *flops_out (host, may be NULL) receives the launch's flop count (2 per FMA,
+ * 4 per packed FMA).  sink_dev (1 float) is written only to keep the chains alive.
+ * Errors: BOS_ERR_INVALID_ARG for another kind, repeats < 1 or a NULL sink. */
+bos_status_t bos_probe_fma(int kind, int repeats, float* sink_dev, double* flops_out, void* stream);
+
 /* Forward render that allocates nothing, for callers that must not call cudaMalloc
  * (a latency-critical loop, where allocation and freeing can synchronise the device, or
  * a host whose device memory is already handed out by another allocator).  No

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libbos.so")
-SOURCES = ["bos_forward.cu", "bos_adjoint.cu", "bos_api.cu", "bos_server.cu", "bos_noalloc.cu", "bos_optim.cu"]
+SOURCES = ["bos_forward.cu", "bos_adjoint.cu", "bos_api.cu", "bos_server.cu", "bos_noalloc.cu", "bos_optim.cu",
+           "bos_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr",
          f"-I{INCLUDE}"]

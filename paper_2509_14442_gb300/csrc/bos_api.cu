@@ -611,6 +611,16 @@ bos_status_t bos_probe_read(const void* buf, uint64_t bytes, int repeats, float*
     return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_probe_read");
 }
 
+bos_status_t bos_probe_fma(int kind, int repeats, float* sink, double* flops, void* stream) {
+    if (!sink || kind < 0 || kind > 2 || repeats < 1)
+        return fail(BOS_ERR_INVALID_ARG, "bos_probe_fma: need kind 0, 1 or 2, repeats >= 1 and a sink");
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = launch_probe_fma(kind, repeats, sink, sms, flops, (cudaStream_t)stream);
+    return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_probe_fma");
+}
+
 bos_status_t bos_status(bos_ctx* c) {
     if (!c) return fail(BOS_ERR_INVALID_ARG, "bos_status: NULL context");
     DeviceGuard dg(c->device);

@@ -50,6 +50,8 @@ def test_null_arguments_are_rejected_without_touching_the_gpu():
     assert L.bos_backward(None, None, None, None) == bos.BOS_ERR_INVALID_ARG
     assert L.bos_loss_l2(None, None, 0, None, None, None) == bos.BOS_ERR_INVALID_ARG
     assert b"NULL" in L.bos_last_error() or b"bad argument" in L.bos_last_error()
+    assert L.bos_probe_fma(3, 1, None, None, None) == bos.BOS_ERR_INVALID_ARG
+    assert L.bos_probe_fma(0, 0, None, None, None) == bos.BOS_ERR_INVALID_ARG
     assert L.bos_destroy(None) == bos.BOS_OK
 
 

@@ -184,3 +184,28 @@ def test_quasi_linear_full_size_sampled(bos, orc):
     pix = np.random.default_rng(3).choice(sc.pixels, 600, replace=False)
     e = errors(g, orc.render(sc, pix=pix), pix)
     assert e["I_abs"] <= I_ABS_TOL and e["disp_rel"] <= DISP_REL_TOL, e
+
+
+# ------------------------------------------------------------------ measurement probes
+
+def test_fma_probe_rates_are_physical(bos):
+    """The arithmetic-roofline probe: its flop count matches its launch shape, and the
+    rates sit within a factor of the GPU's FMA unit counts (no folded-away work)."""
+    sink = torch.zeros(1, device="cuda")
+    sp = torch.cuda.current_stream().cuda_stream
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    rates = {}
+    for kind, reps in ((0, 2000), (1, 2000), (2, 50)):
+        bos.bos_probe_fma(kind, reps, sink.data_ptr(), sp)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        flops = bos.bos_probe_fma(kind, reps, sink.data_ptr(), sp)
+        e1.record()
+        e1.synchronize()
+        assert flops == 2 * (2 if kind == 1 else 1) * sms * 4 * 256 * reps * 16 * 8
+        rates[kind] = flops / (e0.elapsed_time(e1) * 1e-3)
+    fp32_units = sms * 128 * 2 * 2.2e9          # above any boost clock of this part
+    assert 0.3 * fp32_units < rates[0] <= 1.05 * fp32_units
+    assert 0.3 * fp32_units < rates[1] <= 2.1 * fp32_units
+    assert 0.0 < rates[2] < rates[0]
+    assert sink.item() == 0.0
