@@ -409,6 +409,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                         float* p = st_buf + (size_t)(n - n0) * 6 * 32 + lane;
                         p[0] = st.dr[0]; p[32] = st.dr[1]; p[64] = st.dr[2];
                         p[96] = st.dv[0]; p[128] = st.dv[1]; p[160] = st.dv[2];
+                        // the state after the segment's last step is needed only at the
+                        // ray's end (the wall adjoint); elsewhere the next checkpoint holds it
+                        if (n + 1 == n1 && c != nseg - 1) break;
                         comp_step<E, 0>(F, st, k, bc);
                     }
                     if (c == nseg - 1) {
