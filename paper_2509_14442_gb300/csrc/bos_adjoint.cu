@@ -24,6 +24,9 @@ constexpr int kAdjWarps = kAdjWarpsPerBlock;   // warps per block
 #ifndef BOS_ADJ_MIN_BLOCKS
 #define BOS_ADJ_MIN_BLOCKS 5              // resident blocks per SM the register budget is cut for
 #endif
+#ifndef BOS_ADJ_QUASI_MIN_BLOCKS
+#define BOS_ADJ_QUASI_MIN_BLOCKS 7        // the same for the quasi-linear adjoint (128 registers, 16 warps/SM)
+#endif
 constexpr int kRow = 36;              // floats per lane row of the cell accumulators (16-byte aligned rows)
 constexpr int kStageStride = 20;      // floats per lane row of a parked stage (value + 3 derivatives, cell, fractions)
 constexpr int kConnDoubles = 20;      // per-lane shared doubles of the refracted connection's adjoint
@@ -646,8 +649,8 @@ __device__ __forceinline__ float4 line_corner_record(const float4 v, const float
 }
 
 template <class E>
-__global__ void __launch_bounds__(kAdjWarps * 32) adjoint_quasi_kernel(SceneDev S, CkptDev ck, AdjDev adj,
-                                                                       WorkDev wk) {
+__global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_QUASI_MIN_BLOCKS)
+    adjoint_quasi_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
     extern __shared__ float4 smem4[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* rows = reinterpret_cast<float*>(smem4) + (size_t)warp * 32 * kRow;
