@@ -25,7 +25,10 @@ constexpr int kAdjWarps = kAdjWarpsPerBlock;   // warps per block
 #define BOS_ADJ_MIN_BLOCKS 5              // resident blocks per SM the register budget is cut for
 #endif
 #ifndef BOS_ADJ_QUASI_MIN_BLOCKS
-#define BOS_ADJ_QUASI_MIN_BLOCKS 7        // the same for the quasi-linear adjoint (128 registers, 16 warps/SM)
+#define BOS_ADJ_QUASI_MIN_BLOCKS 7        // the same for the quasi-linear adjoint (128 registers, 16 warps/SM),
+#endif                                    // used when there are more than 12 warp tiles per SM
+#ifndef BOS_ADJ_QUASI_SMALL_MIN_BLOCKS
+#define BOS_ADJ_QUASI_SMALL_MIN_BLOCKS 1  // the quasi-linear adjoint for few tiles (no register cap)
 #endif
 constexpr int kRow = 36;              // floats per lane row of the cell accumulators (16-byte aligned rows)
 constexpr int kStageStride = 20;      // floats per lane row of a parked stage (value + 3 derivatives, cell, fractions)
@@ -648,8 +651,8 @@ __device__ __forceinline__ float4 line_corner_record(const float4 v, const float
     return make_float4(Db[0] * v.y + Db[1] * v.z + Db[2] * v.w, eta * Db[0], eta * Db[1], eta * Db[2]);
 }
 
-template <class E>
-__global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_QUASI_MIN_BLOCKS)
+template <class E, int MINB>
+__global__ void __launch_bounds__(kAdjWarps * 32, MINB)
     adjoint_quasi_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
     extern __shared__ float4 smem4[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -851,16 +854,29 @@ static cudaError_t launch_adjoint_t(const SceneDev& S, const CkptDev& ck, const 
     return launch_adjoint_c<E, false>(S, ck, adj, w, num_sms, st);
 }
 
-template <class E>
-static cudaError_t launch_adjoint_quasi_t(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
+template <class E, int MINB>
+static cudaError_t launch_adjoint_quasi_b(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
                                           int num_sms, cudaStream_t st) {
     size_t smem = (size_t)kAdjWarps * 32 * kRow * sizeof(float);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_quasi_kernel<E>, kAdjWarps * 32, smem);
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_quasi_kernel<E, MINB>, kAdjWarps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    adjoint_quasi_kernel<E><<<num_sms * per_sm, kAdjWarps * 32, smem, st>>>(S, ck, adj, w);
+    adjoint_quasi_kernel<E, MINB><<<num_sms * per_sm, kAdjWarps * 32, smem, st>>>(S, ck, adj, w);
     return cudaGetLastError();
+}
+
+// Two register budgets of the quasi-linear adjoint: with more than 12 warp tiles per SM,
+// the 128-register form's 16 resident warps per SM hide more latency; with fewer (a
+// 5000-pixel minibatch is ~300 tiles) the GPU is not full either way, and the form without
+// a register cap (180-200 registers, no spills) finishes each ray sooner.
+template <class E>
+static cudaError_t launch_adjoint_quasi_t(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
+                                          int num_sms, cudaStream_t st) {
+    const int ntiles = tile_count(S, tile_shape(S.cam.width, S.cam.height, S.cam.spp));
+    if (ntiles > num_sms * 12) return launch_adjoint_quasi_b<E, BOS_ADJ_QUASI_MIN_BLOCKS>(S, ck, adj, w, num_sms, st);
+    return launch_adjoint_quasi_b<E, BOS_ADJ_QUASI_SMALL_MIN_BLOCKS>(S, ck, adj, w, num_sms, st);
 }
 
 cudaError_t launch_backward(int mode, const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,

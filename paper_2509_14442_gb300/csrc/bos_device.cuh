@@ -592,7 +592,7 @@ struct TilePix {
     bool valid, bad;
 };
 
-__device__ __forceinline__ int tile_count(const SceneDev& S, const TileShape& ts) {
+__host__ __device__ __forceinline__ int tile_count(const SceneDev& S, const TileShape& ts) {
     if (S.pix) return (int)((S.npix + (32 / ts.G) - 1) / (32 / ts.G));
     return ts.tiles_x * ts.tiles_y;
 }

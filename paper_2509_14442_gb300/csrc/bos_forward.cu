@@ -479,14 +479,17 @@ __device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, 
     }
 }
 
-template <int MODE, int INTEG, bool CONN>
 #ifndef BOS_FWD_MIN_BLOCKS
 #define BOS_FWD_MIN_BLOCKS 6              // resident 128-thread blocks per SM the register budget is cut for
 #endif
 #ifndef BOS_FWD_QUASI_MIN_BLOCKS
 #define BOS_FWD_QUASI_MIN_BLOCKS 3        // the same for quasi-linear tracing (more registers, more overlap)
 #endif
-__global__ void __launch_bounds__(128, INTEG == 2 ? BOS_FWD_QUASI_MIN_BLOCKS : BOS_FWD_MIN_BLOCKS) render_kernel(SceneDev S, RenderOut out, WorkDev wk, CkptDev ck) {
+// FEW: the form for launches with few warp tiles (a pixel minibatch), without a register
+// cap: the GPU is not full either way, and each ray finishes sooner without spills.
+template <int MODE, int INTEG, bool CONN, bool FEW = false>
+__global__ void __launch_bounds__(128, FEW ? 1 : INTEG == 2 ? BOS_FWD_QUASI_MIN_BLOCKS : BOS_FWD_MIN_BLOCKS)
+    render_kernel(SceneDev S, RenderOut out, WorkDev wk, CkptDev ck) {
     const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
     const TileShape ts = tile_shape(W, H, spp);
     const int ntiles = tile_count(S, ts);
@@ -636,14 +639,15 @@ cudaError_t launch_build_store(const GridDev& g, const float* T, void* store, cu
     return cudaGetLastError();
 }
 
-template <int MODE, int INTEG, bool CONN>
+template <int MODE, int INTEG, bool CONN, bool FEW = false>
 static cudaError_t launch_render_c(const SceneDev& S, const RenderOut& o, const WorkDev& w, const CkptDev& ck,
                                    int num_sms, cudaStream_t st) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<MODE, INTEG, CONN>, 128, 0);
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<MODE, INTEG, CONN, FEW>, 128, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    render_kernel<MODE, INTEG, CONN><<<num_sms * per_sm, 128, 0, st>>>(S, o, w, ck);
+    render_kernel<MODE, INTEG, CONN, FEW><<<num_sms * per_sm, 128, 0, st>>>(S, o, w, ck);
     return cudaGetLastError();
 }
 
@@ -654,6 +658,11 @@ static cudaError_t launch_render_t(const SceneDev& S, const RenderOut& o, const 
                                    int num_sms, cudaStream_t st) {
     if constexpr (MODE == 1 || MODE == 2) {
         if (S.L.mode == 2) return launch_render_c<MODE, INTEG, true>(S, o, w, ck, num_sms, st);
+        // quasi-linear tracing of a few tiles (up to 8 warps per SM): the uncapped form
+        if constexpr (INTEG == 2) {
+            if (tile_count(S, tile_shape(S.cam.width, S.cam.height, S.cam.spp)) <= num_sms * 8)
+                return launch_render_c<MODE, INTEG, false, true>(S, o, w, ck, num_sms, st);
+        }
     }
     return launch_render_c<MODE, INTEG, false>(S, o, w, ck, num_sms, st);
 }

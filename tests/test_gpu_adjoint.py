@@ -165,6 +165,16 @@ def test_quasi_linear_adjoint_matches_oracle(bos, orc, spp):
     assert rel_l2(gpu_grad(bos, sc, w), orc.grad(sc, w)) <= GRAD_REL_L2
 
 
+def test_quasi_linear_adjoint_many_tiles_matches_oracle(bos, orc):
+    # 256^2 rays = 2048 warp tiles, more than 12 per SM: the launch takes the quasi-linear
+    # adjoint's 128-register form (the small cases above take the uncapped one)
+    sc = S.room((40, 40, 30), 256, 256, 1, 3410)
+    sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=2))
+    assert (256 * 256) // 32 > 12 * torch.cuda.get_device_properties(0).multi_processor_count
+    w = np.random.default_rng(21).standard_normal((sc.camera.height, sc.camera.width))
+    assert rel_l2(gpu_grad(bos, sc, w), orc.grad(sc, w)) <= GRAD_REL_L2
+
+
 def test_quasi_linear_adjoint_matches_oracle_on_32cube_crop(bos, orc):
     sc = crop_scene()
     sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=2))
