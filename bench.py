@@ -108,8 +108,8 @@ FP64_NOMINAL_FLOPS = 1.25e12
 # from one ncu capture of the default workload (profiles/adjoint_kernel_room_adj.md).  It is
 # reported only while the kernel sources still hash to what was captured.
 TRAFFIC_SOURCES = ("bos_forward.cu", "bos_adjoint.cu", "bos_comp.cuh", "bos_device.cuh")
-KERNEL_TRAFFIC = {"workload": "room_adj", "sha256": "3e74f6ae26adec627852feffd7e3a78b2d9bb9628c92a5c8649ed89c2cfb3fac",
-                  "render_kernel": 963664128 + 7275163648, "adjoint_kernel": 7067506944 + 473239296}
+KERNEL_TRAFFIC = {"workload": "room_adj", "sha256": "6806fe47d7c0089532af839abcf38abeadb027231f34a4469d88f931508cf48e",
+                  "render_kernel": 970397952 + 7275392768, "adjoint_kernel": 7074277632 + 503452928}
 
 
 def kernel_sources_sha256() -> str:
