@@ -73,3 +73,23 @@ def test_out_of_range_pixels_are_skipped_and_flagged(bos):
     good = torch.tensor([0, 2, 4], device="cuda")
     assert torch.equal(Ip[good], I.reshape(-1)[pix[good].long()])
     ctx.close()
+
+
+def test_empty_and_single_pixel_minibatches(bos):
+    # an empty list is refused on the host (nothing launched, the context stays usable);
+    # a one-pixel list is a warp tile with 31 idle lanes
+    sc = S.room((32, 32, 24), 40, 30, 1, 3800)
+    ctx = bos.Context(0)
+    ctx.set_scene(sc, bos.BOS_PREC_FP32_COMP)
+    I, D, _ = ctx.render(disp=True)
+    with pytest.raises(bos.BosError) as e:
+        ctx.render_pixels(torch.empty((0,), dtype=torch.int32, device="cuda"))
+    assert e.value.status == bos.BOS_ERR_INVALID_ARG
+    for p in (0, 611, 40 * 30 - 1):
+        pix = torch.tensor([p], dtype=torch.int32, device="cuda")
+        Ip, Dp = ctx.render_pixels(pix, disp=True)
+        torch.cuda.synchronize()
+        ctx.status()
+        assert torch.equal(Ip, I.reshape(-1)[pix.long()])
+        assert torch.equal(Dp, D.reshape(-1, 2)[pix.long()])
+    ctx.close()
