@@ -582,3 +582,117 @@ def test_refracted_gradient_differs_from_the_straight_connection(orc):
     g2 = orc.grad(sc, w)
     g1 = orc.grad(sc.replace(light=S.Light(1, sc.light.pattern, sc.light.proj)), w)
     assert np.linalg.norm(g2 - g1) > 1e-3 * np.linalg.norm(g1)
+
+
+# ----------------------------------------------------------------- one ray, brute force
+
+def _py_trace_pixel(sc, px, py):
+    """One pixel (1 spp: its centre) of a constant-luminance wall, traced by a plain Python
+    FP64 loop written from the definitions: eta - 1 = rho0 G T0 / T per cell (Sec. 2.1),
+    central / one-sided differences for grad eta, trilinear interpolation with the base
+    cell clamped and the fraction not (A4, A5), the pinhole ray, its box segment and
+    N = ceil(l / (0.5 min h)) (A13), v0 = eta_in d and dt = ds / eta_in (A3), Sharma's RKN
+    steps of Eq. 1 (A2), the straight continuation to the wall, the path length from the
+    pinhole with the signed continuation (A7) and the weight <n, v> / (|v| len) of Eq. 2."""
+    g, cam, wall = sc.grid, sc.camera, sc.wall
+    nx, ny, nz = g.n
+    h = np.array(g.spacing())
+    o = np.array(g.origin)
+    T = sc.T.astype(np.float64)
+    de = g.rho0 * g.G * g.T0 / T                              # (nz, ny, nx)
+    eta = 1.0 + de
+    grad = np.zeros(T.shape + (3,))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                idx = [i, j, k]
+                for a, n in enumerate((nx, ny, nz)):
+                    lo, hi = list(idx), list(idx)
+                    if idx[a] == 0:
+                        hi[a] += 1
+                        den = h[a]
+                    elif idx[a] == n - 1:
+                        lo[a] -= 1
+                        den = h[a]
+                    else:
+                        lo[a] -= 1
+                        hi[a] += 1
+                        den = 2.0 * h[a]
+                    grad[k, j, i, a] = (eta[hi[2], hi[1], hi[0]] - eta[lo[2], lo[1], lo[0]]) / den
+
+    def interp(x):
+        base, frac = [], []
+        for a, n in enumerate((nx, ny, nz)):
+            u = (x[a] - o[a]) / h[a] - 0.5
+            i0 = min(max(int(math.floor(u)), 0), n - 2)
+            base.append(i0)
+            frac.append(u - i0)
+        val = np.zeros(4)
+        for c in range(8):
+            bits = [(c >> a) & 1 for a in range(3)]
+            w = 1.0
+            for a in range(3):
+                w *= frac[a] if bits[a] else 1.0 - frac[a]
+            i, j, k = (base[a] + bits[a] for a in range(3))
+            val += w * np.array([de[k, j, i], *grad[k, j, i]])
+        return val
+
+    def D(x):
+        v = interp(x)
+        return (1.0 + v[0]) * v[1:]
+
+    pos, fwd, up = np.array(cam.pos), np.array(cam.fwd), np.array(cam.up)
+    right = np.cross(fwd, up)
+    d = ((px + 0.5 - cam.cx) / cam.fx) * right - ((py + 0.5 - cam.cy) / cam.fy) * up + fwd
+    d /= np.linalg.norm(d)
+    with np.errstate(divide="ignore"):                        # axis-parallel rays: slabs at +-inf
+        t0 = (o - pos) / d
+        t1 = (o + np.array(g.extent) - pos) / d
+    t_in, t_out = np.max(np.minimum(t0, t1)), np.min(np.maximum(t0, t1))
+    nw, wo = np.array(wall.normal), np.array(wall.origin)
+    t_w = np.dot(wo - pos, nw) / np.dot(d, nw)
+    ell = min(t_out, t_w) - t_in
+    N = int(math.ceil(ell / (0.5 * h.min())))
+    r = pos + t_in * d
+    eta_in = 1.0 + interp(r)[0]
+    v = eta_in * d
+    dt = (ell / N) / eta_in
+    length = t_in
+    for _ in range(N):
+        A = dt * D(r)
+        B = dt * D(r + 0.5 * dt * v + 0.125 * dt * A)
+        C = dt * D(r + dt * v + 0.5 * dt * B)
+        r_next = r + dt * (v + (A + 2.0 * B) / 6.0)
+        v = v + (A + 4.0 * B + C) / 6.0
+        length += np.linalg.norm(r_next - r)
+        r = r_next
+    t_star = np.dot(wo - r, nw) / np.dot(v, nw)
+    x_w = r + t_star * v
+    length += t_star * np.linalg.norm(v)
+    c = np.dot(nw, v) / np.linalg.norm(v)
+    x_ref = pos + t_w * d
+    eu, ev = np.array(wall.eu), np.array(wall.ev)
+    hit = np.array([np.dot(x_w - wo, eu), np.dot(x_w - wo, ev)])
+    hit_ref = np.array([np.dot(x_ref - wo, eu), np.dot(x_ref - wo, ev)])
+    return dict(I=c / length, hit=hit, disp=hit - hit_ref, N=N)
+
+
+def test_one_ray_on_a_tiny_grid_matches_an_independent_python_trace(orc):
+    # a 3 x 4 x 3 grid with a refractivity 100x that of air, so that rays bend visibly,
+    # and a wall of constant luminance 1; pixels at the centre, edges and corners
+    grid = S.Grid(n=(3, 4, 3), origin=(0.0, 0.0, 0.0), extent=(1.0, 1.2, 0.9), G=2.26e-2)
+    T = (280.0 + 60.0 * np.random.default_rng(5).random((3, 4, 3))).astype(np.float32)
+    cam = S.Camera(pos=(0.5, -1.5, 0.45), fwd=(0.0, 1.0, 0.0), up=(0.0, 0.0, 1.0),
+                   fx=20.0, fy=20.0, cx=2.5, cy=2.5, width=5, height=5)   # all hits well inside the wall
+    sc = S.Scene("tiny", grid, T, cam, S.back_wall(grid), S.Light(0, np.ones((8, 8), np.float32)),
+                 S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=0))
+    pix = [0, 4, 7, 12, 17, 20, 24]
+    got = orc.render(sc, pix=pix, nsteps=True)
+    for q, p in enumerate(pix):
+        want = _py_trace_pixel(sc, p % 5, p // 5)
+        assert got["nsteps"][q, 0] == want["N"]
+        assert abs(got["I"][q] - want["I"]) <= 1e-12 * abs(want["I"])
+        assert np.abs(got["hit"][q] - want["hit"]).max() <= 1e-12
+        assert np.abs(got["disp"][q] - want["disp"]).max() <= 1e-12
+    # the field bends the rays well beyond rounding, so the comparison is not vacuous
+    assert np.abs(got["disp"]).max() > 1e-4
