@@ -133,7 +133,8 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--workload", default="room_adj", choices=sorted(WORKLOADS) + ["serving", "precision", "recon"])
+    p.add_argument("--workload", default="room_adj",
+                   choices=sorted(WORKLOADS) + ["serving", "precision", "recon", "oracle"])
     p.add_argument("--prec", default="fp32_comp", choices=sorted(BYTES_PER_STEP))
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
@@ -147,13 +148,13 @@ def parse():
 
 # ------------------------------------------------------------------ oracle (CPU) arm
 
-def oracle_rate(scene, adjoint: bool, seconds: float, seed: int = 0):
-    """Time the FP64 oracle on a pixel sample sized for ~`seconds` on all host cores.
-    Returns (ray-steps/s, threads, sample description)."""
+def oracle_rate(scene, adjoint: bool, seconds: float, seed: int = 0, threads: int = 0):
+    """Time the FP64 oracle on a pixel sample sized for ~`seconds` on all host cores (or on
+    `threads` of them).  Returns (ray-steps/s, threads, sample description)."""
     from oracle import oracle as O
 
     O.build()
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     field = O.field_from_T(scene.grid, scene.T)
     rng = np.random.default_rng(seed)
     npix = scene.pixels
@@ -178,6 +179,53 @@ def oracle_rate(scene, adjoint: bool, seconds: float, seed: int = 0):
     steps, t = run(pix, adjoint)
     kind = "forward + adjoint" if adjoint else "forward"
     return steps / t, threads, f"{m} of {npix} pixels ({kind}), {steps} ray-steps in {t:.1f} s"
+
+
+def oracle_arm(args):
+    """The FP64 oracle's own rates on this machine's host cores, per configuration (no GPU
+    work): the 32^3 blob cube's whole image (all cores and one thread), pixel samples of the
+    128^2x96 forward and of the 256^2x192 forward and forward + adjoint scenes (one thread
+    too for the forward), and the gradient of the 32^3 crop (whole image)."""
+    import platform
+
+    from oracle import oracle as O
+
+    O.build()
+    threads = os.cpu_count() or 1
+    out = {}
+    sc = S.blob_cube()
+    field = O.field_from_T(sc.grid, sc.T)
+    for nthr, tag in ((threads, "all_cores"), (1, "one_thread")):
+        t0 = time.perf_counter()
+        r = O.render(sc, field=field, threads=nthr, nsteps=True)
+        t = time.perf_counter() - t0
+        steps = int(r["nsteps"].sum())
+        out[f"blob_cube_32_forward_{tag}"] = {"ray_steps_per_s": steps / t, "threads": nthr,
+                                              "sample": f"all {sc.pixels} pixels, {steps} ray-steps in {t:.2f} s"}
+    cases = (("room_128x128x96_forward", S.room_forward, False, 10.0, 0),
+             ("room_256x256x192_forward", S.room_adjoint, False, 10.0, 0),
+             ("room_256x256x192_forward_one_thread", S.room_adjoint, False, 5.0, 1),
+             ("room_256x256x192_forward_adjoint", S.room_adjoint, True, 15.0, 0))
+    for name, make, adj, secs, nthr in cases:
+        r, thr, desc = oracle_rate(make(), adj, secs, threads=nthr)
+        out[name] = {"ray_steps_per_s": r, "threads": thr, "sample": desc}
+    big = S.room_adjoint()
+    k, j, i = np.unravel_index(np.argmax(big.T), big.T.shape)
+    lo = [int(np.clip(c - 16, 0, n - 32)) for c, n in zip((i, j, k), big.grid.n)]
+    crop = S.crop(big, lo, 32, 256, 256, 1)
+    w = np.random.default_rng(13).standard_normal((crop.camera.height, crop.camera.width))
+    steps = int(O.render(crop, threads=threads, nsteps=True)["nsteps"].sum())
+    t0 = time.perf_counter()
+    O.grad(crop, w, threads=threads)
+    t = time.perf_counter() - t0
+    out["crop_32_gradient"] = {"ray_steps_per_s": steps / t, "threads": threads,
+                               "sample": f"all {crop.pixels} pixels, {steps} ray-steps, gradient in {t:.2f} s"}
+    print(json.dumps({
+        "metric": "FP64 oracle ray-steps/s per configuration (host cores)",
+        "value": out["room_256x256x192_forward_adjoint"]["ray_steps_per_s"], "unit": "ray-steps/s",
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic (seeded plume fields and speckle patterns)",
+        "config": {"workload": "oracle", "cores": threads, "machine": platform.machine()},
+        "oracle": out}))
 
 
 def reference_arm(args):
@@ -815,6 +863,8 @@ def main():
         precision_arm(args)
     elif args.workload == "recon":
         recon_arm(args)
+    elif args.workload == "oracle":
+        oracle_arm(args)
     else:
         gpu_arm(args)
 
