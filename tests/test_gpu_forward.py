@@ -162,6 +162,23 @@ def test_room_adjoint_scene_full_size_sampled(bos, orc):
     assert e["I_abs"] <= I_ABS_TOL and e["disp_rel"] <= DISP_REL_TOL, e
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["bf16_comp", "fp64"])
+def test_precision_variants_full_size_sampled(bos, orc, prec):
+    # the precision configuration: the 256x256x192 scene with the BF16 store (held to the
+    # bar against the oracle on the dequantised field, which isolates the integrator) and
+    # with the plain float64 tracer
+    sc = S.room_adjoint()
+    g = gpu_render(sc, bos.PRECISIONS[prec])
+    pix = np.random.default_rng(11).choice(sc.pixels, 400, replace=False)
+    field = None
+    if prec == "bf16_comp":
+        de = orc.deta_from_T(sc.grid, sc.T.astype(np.float64))
+        field = orc.NodeField(bf16_round(de), bf16_round(orc.grad_from_deta(sc.grid, de)))
+    e = errors(g, orc.render(sc, field=field, pix=pix), pix)
+    assert e["I_abs"] <= I_ABS_TOL and e["disp_rel"] <= (2e-7 if prec == "fp64" else DISP_REL_TOL), e
+
+
 # ------------------------------------------------------------------ quasi-linear tracing (Sec. 2.2)
 
 @pytest.mark.parametrize("prec", ["fp32_comp", "fp64", "bf16_comp"])
