@@ -157,6 +157,40 @@ def test_adjoint_full_size_against_oracle_finite_differences(bos, orc):
 
 # ------------------------------------------------------------------ quasi-linear tracing (Sec. 2.2)
 
+@pytest.mark.slow
+def test_quasi_linear_adjoint_full_size_against_oracle_finite_differences(bos, orc):
+    # the benchmarked quasi-linear launch (256x256x192, 2048^2, 1 spp; the 128-register
+    # form of the adjoint): dL/dT_v by central differences of the oracle at 64 seeded
+    # plume voxels, over the pixels whose rays pass within 3 cells of each voxel
+    sc = S.room_adjoint()
+    sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=2))
+    rng = np.random.default_rng(65)
+    w = rng.standard_normal((sc.camera.height, sc.camera.width))
+    g_gpu = gpu_grad(bos, sc, w)
+    hot = np.argwhere(sc.T > 300.0)
+    vox = hot[rng.choice(len(hot), 64, replace=False)]
+    hgrid = np.array(sc.grid.spacing())
+    eps = 1e-2
+    T64 = sc.T.astype(np.float64)
+    fd, gp = [], []
+    for k, j, i in vox:
+        center = np.array(sc.grid.origin) + (np.array([i, j, k]) + 0.5) * hgrid
+        pix = _pixels_near(sc, center, 3.0 * hgrid + 1e-3)
+        vals = []
+        for sgn in (1.0, -1.0):
+            T = T64.copy()
+            T[k, j, i] += sgn * eps
+            I = orc.render(sc.replace(T=T), pix=pix)["I"]
+            vals.append(float((w.reshape(-1)[pix] * I).sum()))
+        fd.append((vals[0] - vals[1]) / (2 * eps))
+        gp.append(g_gpu[k, j, i])
+    fd, gp = np.array(fd), np.array(gp)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    bad = np.abs(gp - fd) > 1e-3 * np.abs(fd) + 1e-3 * scale
+    assert bad.sum() == 0, (np.flatnonzero(bad), gp[bad], fd[bad])
+
+
 @pytest.mark.parametrize("spp", [1, 3])
 def test_quasi_linear_adjoint_matches_oracle(bos, orc, spp):
     sc = S.room((40, 40, 30), 61, 47, spp, 3400 + spp)
