@@ -79,6 +79,10 @@ BYTES_PER_STEP = {"fp32_comp": 384, "fp32": 384, "bf16_comp": 192, "fp64": 768}
 # tracing samples 2 new points per step: 256 B forward; its one-sweep adjoint gathers and
 # scatters those 2 points: 512 B.)
 ADJ_BYTES_PER_STEP = {"fp32_comp": 3 * 384, "bf16_comp": 2 * 192 + 384}
+# Bytes the gathers load through L1 per ray-step (the scatter of the adjoint goes to shared
+# memory and atomics instead): forward 3 x 8 corners x 16 B; adjoint recompute + reverse.
+L1_BYTES_PER_STEP = {"fp32_comp": 384, "fp32": 384, "bf16_comp": 192, "fp64": 768}
+ADJ_L1_BYTES_PER_STEP = {"fp32_comp": 2 * 384, "bf16_comp": 2 * 192}
 L2_BYTES = 129 * 2 ** 20
 # Algorithmic floating-point operations of one ray-step (an FMA counts 2), counted from the
 # method's formulas, not from the kernels (which add the compensation of the fixed-point
@@ -346,6 +350,26 @@ def l2_read_peak(torch, dev, bos):
     return nbytes * reps / (best * 1e-3) / 1e9
 
 
+def l1_read_peak(torch, dev, bos):
+    """L1 read bandwidth of 256-bit loads (GB/s): a 64 KiB buffer every block re-reads, best
+    of 10 launches of 200 passes."""
+    nbytes = 64 * 2 ** 10
+    buf = torch.ones(nbytes // 4, dtype=torch.float32, device=dev)
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    sp = torch.cuda.current_stream().cuda_stream
+    reps = 200
+    bos.bos_probe_read_l1(buf.data_ptr(), nbytes, reps, sink.data_ptr(), sp)
+    best, nread = 1e30, 0.0
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        nread = bos.bos_probe_read_l1(buf.data_ptr(), nbytes, reps, sink.data_ptr(), sp)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return nread / (best * 1e-3) / 1e9
+
+
 def fma_peaks(torch, dev, bos):
     """FMA throughput of this GPU (TFLOP/s): float32, packed float32 pairs and float64, each
     the best of 5 launches of the probe (about 2-4 ms each)."""
@@ -511,6 +535,7 @@ def gpu_arm(args):
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     l2_peak = l2_read_peak(torch, dev, bos)
+    l1_peak = l1_read_peak(torch, dev, bos)
     probe = fma_peaks(torch, dev, bos)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clock_mhz = float(peaks.get("sm_max_mhz") or 2070.0)
@@ -530,19 +555,26 @@ def gpu_arm(args):
     fwd_b = wl.get("fwd_bytes", BYTES_PER_STEP[args.prec])
     adj_b = wl.get("adj_bytes", ADJ_BYTES_PER_STEP.get(args.prec, 0))
 
-    def kernel_entry(ms, flops_per_step, bytes_per_step, name):
+    # quasi-linear tracing loads 2 new line samples per step (forward and one-sweep adjoint)
+    fwd_l1 = wl.get("fwd_bytes", L1_BYTES_PER_STEP[args.prec])
+    adj_l1 = wl.get("fwd_bytes", ADJ_L1_BYTES_PER_STEP.get(args.prec, 0))
+
+    def kernel_entry(ms, flops_per_step, bytes_per_step, l1_bytes_per_step, name):
         tflops = flops_per_step * steps_per_frame / (ms * 1e-3) / 1e12 if flops_per_step else None
         gbs = bytes_per_step * steps_per_frame / (ms * 1e-3) / 1e9
+        l1_gbs = l1_bytes_per_step * steps_per_frame / (ms * 1e-3) / 1e9
         return {"ms": ms, "flops_per_ray_step": flops_per_step, "achieved_tflops": tflops,
                 "frac": tflops / alu_peak if tflops is not None else None,
                 "bytes_per_ray_step": bytes_per_step, "achieved_gbs": gbs, "l2_frac": gbs / l2_peak,
+                "l1_bytes_per_ray_step": l1_bytes_per_step, "l1_achieved_gbs": l1_gbs, "l1_frac": l1_gbs / l1_peak,
                 "traffic": kernel_traffic(args.workload, name)}
 
-    kernels = {"render_kernel": kernel_entry(render_avg_ms, FLOPS_PER_STEP.get(integ), fwd_b, "render_kernel")}
+    kernels = {"render_kernel": kernel_entry(render_avg_ms, FLOPS_PER_STEP.get(integ), fwd_b, fwd_l1,
+                                             "render_kernel")}
     dominant = "render_kernel"
     if wl["adjoint"]:
         kernels["adjoint_kernel"] = kernel_entry(statistics.mean(back_ms), ADJ_FLOPS_PER_STEP.get(integ), adj_b,
-                                                 "adjoint_kernel")
+                                                 adj_l1, "adjoint_kernel")
         kernels["adjoint_kernel"]["timed"] = "bos_backward: accumulator clear + adjoint_kernel + gradient_kernel"
         dominant = "adjoint_kernel"
     dk = kernels[dominant]
@@ -560,6 +592,11 @@ def gpu_arm(args):
                        "peak_source": "in-run L2 read probe (bos_probe_read, 24 MiB x 50 passes, best of 10)",
                        "note": ("gather roofline R = L2 read bandwidth / algorithmic gathered bytes per ray-step; "
                                 "the gathers hit L1, so a kernel can exceed R")},
+                "l1": {"achieved": dk["l1_achieved_gbs"], "peak": l1_peak, "unit": "GB/s", "frac": dk["l1_frac"],
+                       "bytes_per_ray_step": dk["l1_bytes_per_ray_step"],
+                       "peak_source": "in-run L1 read probe (bos_probe_read_l1, 256-bit loads, 64 KiB x 200 passes "
+                                      "per block, best of 10)",
+                       "note": "the gathers' bytes loaded through L1 per ray-step over the L1 read bandwidth"},
                 "hbm_peak_gbs": peaks.get("hbm_gbs")}
     if dk["traffic"] is not None and peaks.get("hbm_gbs"):
         # the same kernel against the HBM roofline: measured DRAM bytes per launch over its time

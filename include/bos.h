@@ -266,6 +266,16 @@ bos_status_t bos_probe_read(const void* buf_dev, uint64_t bytes, int repeats, fl
  * Errors: BOS_ERR_INVALID_ARG for another kind, repeats < 1 or a NULL sink. */
 bos_status_t bos_probe_fma(int kind, int repeats, float* sink_dev, double* flops_out, void* stream);
 
+/* Measurement probe, no counterpart in the paper: the L1 read bandwidth of the 256-bit
+ * non-coherent loads (ld.global.nc.v8.f32) the tracer's gathers use.  Launches 4 blocks of
+ * 256 threads per SM; every block reads all of buf_dev (32 B .. 64 KiB, a multiple of 32,
+ * 32-byte aligned, so it stays resident in each SM's L1) `repeats` times.  The caller
+ * times the launch on `stream`; *bytes_out (host, may be NULL) receives the bytes read.
+ * sink_dev (1 float) is written only to keep the loads alive.
+ * Errors: BOS_ERR_INVALID_ARG for another size or alignment, repeats < 1 or a NULL pointer. */
+bos_status_t bos_probe_read_l1(const void* buf_dev, uint64_t bytes, int repeats, float* sink_dev, double* bytes_out,
+                               void* stream);
+
 /* Forward render that allocates nothing, for callers that must not call cudaMalloc
  * (a latency-critical loop, where allocation and freeing can synchronise the device, or
  * a host whose device memory is already handed out by another allocator).  No

@@ -105,6 +105,7 @@ SIGNATURES = {
     "bos_export_nodes": (_i, [_v, _v, _v]),
     "bos_probe_read": (_i, [_v, _u64, _i, _v, _v]),
     "bos_probe_fma": (_i, [_i, _i, _v, _P(_d), _v]),
+    "bos_probe_read_l1": (_i, [_v, _u64, _i, _v, _P(_d), _v]),
     "bos_render_noalloc": (_i, [_P(bos_grid_desc), _v, _P(bos_camera_desc), _P(bos_wall_desc), _P(bos_light_desc),
                                 _v, _P(bos_integrator_desc), _v, _v, _v]),
     "bos_status": (_i, [_v]),
@@ -280,6 +281,13 @@ def bos_probe_fma(kind: int, repeats: int, sink_dev, stream) -> float:
     flops = C.c_double(0.0)
     check(lib().bos_probe_fma(kind, repeats, sink_dev, C.byref(flops), stream), "bos_probe_fma")
     return flops.value
+
+
+def bos_probe_read_l1(buf_dev, nbytes: int, repeats: int, sink_dev, stream) -> float:
+    """Launch the L1 read-bandwidth probe; returns the bytes the launch reads."""
+    nread = C.c_double(0.0)
+    check(lib().bos_probe_read_l1(buf_dev, nbytes, repeats, sink_dev, C.byref(nread), stream), "bos_probe_read_l1")
+    return nread.value
 
 
 def bos_render_noalloc(grid: bos_grid_desc, T_dev, cam: bos_camera_desc, wall: bos_wall_desc,

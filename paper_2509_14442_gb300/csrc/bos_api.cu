@@ -621,6 +621,18 @@ bos_status_t bos_probe_fma(int kind, int repeats, float* sink, double* flops, vo
     return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_probe_fma");
 }
 
+bos_status_t bos_probe_read_l1(const void* buf, uint64_t bytes, int repeats, float* sink, double* bytes_read,
+                               void* stream) {
+    if (!buf || !sink || bytes < 32 || bytes > (64u << 10) || (bytes & 31) || repeats < 1 || ((uintptr_t)buf & 31))
+        return fail(BOS_ERR_INVALID_ARG,
+                    "bos_probe_read_l1: need a 32-byte aligned buffer of 32 B .. 64 KiB in multiples of 32 bytes");
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = launch_probe_read_l1(buf, (long long)bytes, repeats, sink, sms, bytes_read, (cudaStream_t)stream);
+    return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_probe_read_l1");
+}
+
 bos_status_t bos_status(bos_ctx* c) {
     if (!c) return fail(BOS_ERR_INVALID_ARG, "bos_status: NULL context");
     DeviceGuard dg(c->device);

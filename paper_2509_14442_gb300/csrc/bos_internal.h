@@ -71,6 +71,8 @@ cudaError_t launch_loss_l2(const float* I, const float* target, long long n, dou
 cudaError_t launch_probe_read(const void* buf, long long bytes, int repeats, float* sink, int num_sms,
                               cudaStream_t st);
 cudaError_t launch_probe_fma(int kind, int repeats, float* sink, int num_sms, double* flops, cudaStream_t st);
+cudaError_t launch_probe_read_l1(const void* buf, long long bytes, int repeats, float* sink, int num_sms,
+                                 double* bytes_read, cudaStream_t st);
 cudaError_t launch_backward(int mode, const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
                             const float* T, float* dLdT, int num_sms, cudaStream_t st);
 

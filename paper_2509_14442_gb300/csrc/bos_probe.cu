@@ -1,6 +1,6 @@
-// Arithmetic-throughput probe (no counterpart in the paper): the FP32 and FP64 fused
-// multiply-add rates of this GPU, measured in the same run as the tracer so that its
-// arithmetic roofline is stated against this device and clock.
+// Throughput probes (no counterpart in the paper), measured in the same run as the tracer
+// so that its rooflines are stated against this device and clock: the FP32 and FP64 fused
+// multiply-add rates, and the L1 read bandwidth of the 256-bit loads the gathers use.
 //
 // Every thread runs eight independent recurrences x <- x * a + b for `repeats` x 16
 // rounds; a and b are kernel arguments, so nothing folds at compile time, and the sum of
@@ -86,6 +86,44 @@ cudaError_t launch_probe_fma(int kind, int repeats, float* sink, int num_sms, do
     if (flops)
         *flops = 2.0 * (kind == 1 ? 2.0 : 1.0) * (double)blocks * kProbeThreads * (double)repeats * kProbeUnroll *
                  kProbeChains;
+    return cudaGetLastError();
+}
+
+// L1 read bandwidth: every block streams the same small buffer (it stays resident in each
+// SM's L1) `repeats` times with the 256-bit non-coherent loads the tracer's gathers use,
+// eight per thread in flight, and folds the values into a register.
+__global__ void __launch_bounds__(kProbeThreads) probe_read_l1_kernel(const float* __restrict__ buf, int n8,
+                                                                      int repeats, float* sink) {
+    float acc = 0.0f;
+    for (int r = 0; r < repeats; ++r) {
+        for (int i = threadIdx.x; i < n8; i += 8 * kProbeThreads) {
+            float v[8][8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = i + u * kProbeThreads;
+                const float* p = buf + 8 * (size_t)(j < n8 ? j : i);
+                asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                             : "=f"(v[u][0]), "=f"(v[u][1]), "=f"(v[u][2]), "=f"(v[u][3]), "=f"(v[u][4]),
+                               "=f"(v[u][5]), "=f"(v[u][6]), "=f"(v[u][7])
+                             : "l"(p));
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                acc += ((v[u][0] + v[u][1]) + (v[u][2] + v[u][3])) + ((v[u][4] + v[u][5]) + (v[u][6] + v[u][7]));
+        }
+    }
+    if (acc == 1234.5678f) sink[0] = acc;
+}
+
+cudaError_t launch_probe_read_l1(const void* buf, long long bytes, int repeats, float* sink, int num_sms,
+                                 double* bytes_read, cudaStream_t st) {
+    const unsigned blocks = (unsigned)num_sms * kProbeBlocksPerSm;
+    const int n8 = (int)(bytes / 32);
+    probe_read_l1_kernel<<<blocks, kProbeThreads, 0, st>>>((const float*)buf, n8, repeats, sink);
+    // each block issues 8 x 256 loads per round (lanes past the end re-read their first
+    // element), ceil(n8 / 2048) rounds per pass
+    const long long rounds = (n8 + 8 * kProbeThreads - 1) / (8 * kProbeThreads);
+    if (bytes_read) *bytes_read = (double)blocks * (double)repeats * (double)rounds * (8.0 * kProbeThreads) * 32.0;
     return cudaGetLastError();
 }
 

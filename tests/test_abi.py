@@ -52,6 +52,7 @@ def test_null_arguments_are_rejected_without_touching_the_gpu():
     assert b"NULL" in L.bos_last_error() or b"bad argument" in L.bos_last_error()
     assert L.bos_probe_fma(3, 1, None, None, None) == bos.BOS_ERR_INVALID_ARG
     assert L.bos_probe_fma(0, 0, None, None, None) == bos.BOS_ERR_INVALID_ARG
+    assert L.bos_probe_read_l1(None, 65536, 1, None, None, None) == bos.BOS_ERR_INVALID_ARG
     assert L.bos_destroy(None) == bos.BOS_OK
 
 

@@ -226,3 +226,32 @@ def test_fma_probe_rates_are_physical(bos):
     assert 0.3 * fp32_units < rates[1] <= 2.1 * fp32_units
     assert 0.0 < rates[2] < rates[0]
     assert sink.item() == 0.0
+
+
+def test_l1_probe_is_faster_than_l2_and_counts_its_bytes(bos):
+    """The L1 gather-roofline probe: its byte count matches its launch shape, and reading a
+    64 KiB L1-resident buffer is faster than streaming a 24 MiB buffer from L2."""
+    sp = torch.cuda.current_stream().cuda_stream
+    sink = torch.zeros(1, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+
+    def timed(fn):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        e1.synchronize()
+        return out, e0.elapsed_time(e1) * 1e-3
+
+    small = torch.ones(16384, device="cuda")
+    nread, t1 = timed(lambda: bos.bos_probe_read_l1(small.data_ptr(), 65536, 100, sink.data_ptr(), sp))
+    assert nread == sms * 4 * 100 * 65536
+    big = torch.ones(6 * 2 ** 20, device="cuda")
+    _, t2 = timed(lambda: bos.bos_probe_read(big.data_ptr(), 24 * 2 ** 20, 20, sink.data_ptr(), sp))
+    l1, l2 = nread / t1, 24 * 2 ** 20 * 20 / t2
+    assert l1 > l2
+    assert l1 < 4 * 128 * sms * 2.2e9            # far above any per-SM load path of this part
+    with pytest.raises(bos.BosError):
+        bos.bos_probe_read_l1(small.data_ptr(), 65536 + 32, 1, sink.data_ptr(), sp)
+    assert sink.item() == 0.0
