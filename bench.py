@@ -70,6 +70,9 @@ WORKLOADS = {
                            make=lambda seed: S.room((128, 128, 96), 256, 256, 4, seed), adjoint=False),
     "room_adj_small": dict(desc="room 256x256x192 plume, 512^2 camera, 1 spp, forward + adjoint (K=16)",
                            make=lambda seed: S.room((256, 256, 192), 512, 512, 1, seed), adjoint=True),
+    "room_adj_quasi_small": dict(desc="room 256x256x192 plume, 512^2 camera, 1 spp, quasi-linear forward + adjoint",
+                                 make=lambda seed: quasi(S.room((256, 256, 192), 512, 512, 1, seed)), adjoint=True,
+                                 fwd_bytes=256, adj_bytes=512),
 }
 # Algorithmic bytes of one Sharma ray-step of the forward tracer: 3 field evaluations x 8
 # trilinear corners x one (deta, grad eta) record (16 B in float32).

@@ -207,6 +207,41 @@ __device__ __forceinline__ void accumulate(float* rows, bool act, uint32_t cell,
     }
 }
 
+// Warp-collective: add w_c(cf) Q and, where `dual`, then w_c(cf2) Q2 (a second sample in
+// the same cell) to the lane's cell row: the same two FMAs per value, in the same order, as
+// two calls of `accumulate`, with one read and one write of the row.
+__device__ __forceinline__ void accumulate_dual(float* rows, bool act, uint32_t cell, const float cf[3], float4 Q,
+                                                bool dual, const float cf2[3], float4 Q2, CellAcc& ca, float* acc,
+                                                int nx, int nxy) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t key = act ? cell : kNoKey;
+    flush_rows(rows, act && ca.key != kNoKey && ca.key != key, ca, acc, nx, nxy);
+    if (act) {
+        ca.key = key;
+        float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
+        const float g0 = 1.0f - cf[0], g1 = 1.0f - cf[1], g2 = 1.0f - cf[2];
+        const float h0 = 1.0f - cf2[0], h1 = 1.0f - cf2[1], h2 = 1.0f - cf2[2];
+        const f32x2 qlo = pack2(Q.x, Q.y), qhi = pack2(Q.z, Q.w);
+        const f32x2 q2lo = pack2(Q2.x, Q2.y), q2hi = pack2(Q2.z, Q2.w);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float w = ((c & 1) ? cf[0] : g0) * ((c & 2) ? cf[1] : g1) * ((c & 4) ? cf[2] : g2);
+            const f32x2 ww = pack2(w, w);
+            float4 r = row[c];
+            f32x2 lo = fma2(ww, qlo, pack2(r.x, r.y)), hi = fma2(ww, qhi, pack2(r.z, r.w));
+            if (dual) {
+                const float v = ((c & 1) ? cf2[0] : h0) * ((c & 2) ? cf2[1] : h1) * ((c & 4) ? cf2[2] : h2);
+                const f32x2 vv = pack2(v, v);
+                lo = fma2(vv, q2lo, lo);
+                hi = fma2(vv, q2hi, hi);
+            }
+            unpack2(lo, r.x, r.y);
+            unpack2(hi, r.z, r.w);
+            row[c] = r;
+        }
+    }
+}
+
 // Adjoint of the wall epilogue for seed Ib = dL/dI of this ray: returns the adjoints of
 // (r_N, v_N) and of the path length (which the per-step lengths feed).
 // With the refracted projector connection the luminance is read at xl (not at x_w) and
@@ -777,11 +812,15 @@ __global__ void __launch_bounds__(kAdjWarps * 32, MINB)
                         A[a] = C[a];
                     }
                 }
-                float4 Q = make_float4(0, 0, 0, 0);
-                if (a_) Q = line_corner_record(p0.v, Db0);
-                accumulate(rows, a_, p0.key, p0.cf, Q, ca, acc, nx, nxy);
-                if (a_) Q = line_corner_record(pm.v, Dbm);
-                accumulate(rows, a_, pm.key, pm.cf, Q, ca, acc, nx, nxy);
+                float4 Q = make_float4(0, 0, 0, 0), Qm = make_float4(0, 0, 0, 0);
+                if (a_) {
+                    Q = line_corner_record(p0.v, Db0);
+                    Qm = line_corner_record(pm.v, Dbm);
+                }
+                // the step's two samples share a cell more often than not: one row update
+                const bool same = a_ && pm.key == p0.key;
+                accumulate_dual(rows, a_, p0.key, p0.cf, Q, same, pm.cf, Qm, ca, acc, nx, nxy);
+                accumulate(rows, a_ && !same, pm.key, pm.cf, Qm, ca, acc, nx, nxy);
                 if (a_) p0 = pe;
             }
             // the end sample of the last step, then eta_in = 1 + deta(r_in)
