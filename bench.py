@@ -115,8 +115,8 @@ FP64_NOMINAL_FLOPS = 1.25e12
 # from one ncu capture of the default workload (profiles/adjoint_kernel_room_adj.md).  It is
 # reported only while the kernel sources still hash to what was captured.
 TRAFFIC_SOURCES = ("bos_forward.cu", "bos_adjoint.cu", "bos_comp.cuh", "bos_device.cuh")
-KERNEL_TRAFFIC = {"workload": "room_adj", "sha256": "6806fe47d7c0089532af839abcf38abeadb027231f34a4469d88f931508cf48e",
-                  "render_kernel": 970397952 + 7275392768, "adjoint_kernel": 7074277632 + 503452928}
+KERNEL_TRAFFIC = {"workload": "room_adj", "sha256": "cec8cb7ca436b3e03645b5bd3b27bd6bc2bd7b77b291011fac19e31fd69755e3",
+                  "render_kernel": 970890240 + 7275419904, "adjoint_kernel": 7071544064 + 502734336}
 
 
 def kernel_sources_sha256() -> str:
