@@ -57,3 +57,23 @@ def test_per_ray_step_tables_follow_their_counts():
     assert bench.ADJ_BYTES_PER_STEP["fp32_comp"] == 3 * bench.BYTES_PER_STEP["fp32_comp"]
     assert bench.L1_BYTES_PER_STEP["fp32_comp"] == 3 * 8 * 16
     assert bench.ADJ_L1_BYTES_PER_STEP["fp32_comp"] == 2 * bench.L1_BYTES_PER_STEP["fp32_comp"]
+
+
+def test_profile_commands_name_existing_workloads():
+    # every command recorded under profiles/ runs committed files: bench.py with a workload
+    # that bench.py still defines
+    import re
+
+    import bench
+
+    names = set(bench.WORKLOADS) | {"serving", "precision", "recon", "oracle"}
+    found = 0
+    pdir = os.path.join(ROOT, "profiles")
+    for fn in sorted(os.listdir(pdir)):
+        with open(os.path.join(pdir, fn)) as f:
+            text = f.read()
+        for w in re.findall(r"bench\.py --workload (\S+)", text):
+            assert w in names, (fn, w)
+            found += 1
+        assert "bench.py" in text, fn
+    assert found > 0
