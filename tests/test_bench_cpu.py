@@ -72,7 +72,7 @@ def test_profile_commands_name_existing_workloads():
     for fn in sorted(os.listdir(pdir)):
         with open(os.path.join(pdir, fn)) as f:
             text = f.read()
-        for w in re.findall(r"bench\.py --workload (\S+)", text):
+        for w in re.findall(r"bench\.py --workload ([A-Za-z0-9_]+)", text):
             assert w in names, (fn, w)
             found += 1
         assert "bench.py" in text, fn
