@@ -66,8 +66,6 @@ CamDev to_dev(const bos_camera_desc& c) {
     d.fy = c.fy;
     d.cx = c.cx;
     d.cy = c.cy;
-    d.inv_fx = 1.0 / c.fx;
-    d.inv_fy = 1.0 / c.fy;
     d.width = c.width;
     d.height = c.height;
     d.spp = c.spp;

@@ -30,7 +30,6 @@ struct GridDev {
 struct CamDev {
     double pos[3], fwd[3], up[3];
     double fx, fy, cx, cy;
-    double inv_fx, inv_fy;   // 1/fx, 1/fy (IEEE division on the host)
     int width, height, spp;
     unsigned long long seed;
 };
@@ -97,8 +96,6 @@ __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
-// 1/a rounded to nearest: the same double as ddiv(1.0, a)
-__device__ __forceinline__ double drcp(double a) { return __drcp_rn(a); }
 __device__ __forceinline__ double ddot(const double a[3], const double b[3]) {
     return dadd(dadd(dmul(a[0], b[0]), dmul(a[1], b[1])), dmul(a[2], b[2]));
 }
@@ -364,12 +361,11 @@ __device__ __forceinline__ void image_point(const CamDev& c, int px, int py, int
 
 __device__ __forceinline__ void pinhole_direction(const CamDev& c, const double right[3], double x, double y,
                                                   double d[3]) {
-    double a = dmul(dsub(x, c.cx), c.inv_fx);
-    double b = dmul(dsub(y, c.cy), c.inv_fy);
+    double a = ddiv(dsub(x, c.cx), c.fx);
+    double b = ddiv(dsub(y, c.cy), c.fy);
     for (int i = 0; i < 3; ++i) d[i] = dadd(dsub(dmul(a, right[i]), dmul(b, c.up[i])), c.fwd[i]);
     double n = dsqrt(ddot(d, d));
-    double inv_n = drcp(n);
-    for (int i = 0; i < 3; ++i) d[i] = dmul(d[i], inv_n);
+    for (int i = 0; i < 3; ++i) d[i] = ddiv(d[i], n);
 }
 
 struct Ray {
@@ -408,9 +404,8 @@ __device__ __forceinline__ void ray_segment(const SceneDev& S, const double rs[3
             if (rs[a] < S.g.origin[a] || rs[a] > dadd(S.g.origin[a], S.g.extent[a])) inside = false;
             continue;
         }
-        double inv = drcp(R.d[a]);
-        double t0 = dmul(lo_m[a], inv);
-        double t1 = dmul(hi_m[a], inv);
+        double t0 = ddiv(lo_m[a], R.d[a]);
+        double t1 = ddiv(hi_m[a], R.d[a]);
         if (t0 > t1) {
             double t = t0;
             t0 = t1;
@@ -462,8 +457,8 @@ __device__ __forceinline__ Ray projector_setup(const SceneDev& S, const double b
     const double* P = S.L.proj.pos;
     double q[3];
     for (int a = 0; a < 3; ++a) q[a] = dadd(dsub(base[a], P[a]), (double)e[a]);
-    double inv_n = drcp(dsqrt(ddot(q, q)));
-    for (int a = 0; a < 3; ++a) R.d[a] = dmul(q[a], inv_n);
+    double nq = dsqrt(ddot(q, q));
+    for (int a = 0; a < 3; ++a) R.d[a] = ddiv(q[a], nq);
     ray_segment(S, P, S.rc.plo_m, S.rc.phi_m, S.rc.pqn, R);
     return R;
 }
