@@ -319,13 +319,11 @@ void pinhole_dir(const orc_camera& cam, double x, double y, double d[3]) {
     double right[3] = {cam.fwd[1] * cam.up[2] - cam.fwd[2] * cam.up[1],
                        cam.fwd[2] * cam.up[0] - cam.fwd[0] * cam.up[2],
                        cam.fwd[0] * cam.up[1] - cam.fwd[1] * cam.up[0]};
-    double inv_fx = 1.0 / cam.fx, inv_fy = 1.0 / cam.fy;
-    double a = (x - cam.cx) * inv_fx;
-    double b = (y - cam.cy) * inv_fy;
+    double a = (x - cam.cx) / cam.fx;
+    double b = (y - cam.cy) / cam.fy;
     for (int i = 0; i < 3; ++i) d[i] = a * right[i] - b * cam.up[i] + cam.fwd[i];
     double n = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    double inv_n = 1.0 / n;
-    for (int i = 0; i < 3; ++i) d[i] = d[i] * inv_n;
+    for (int i = 0; i < 3; ++i) d[i] = d[i] / n;
 }
 
 struct RayGeom {
@@ -363,9 +361,8 @@ RayGeom ray_geometry(const orc_grid& g, const orc_wall& w, const orc_integ& it,
             if (rs[a] < lo || rs[a] > hi) inside = false;
             continue;
         }
-        double inv = 1.0 / d[a];
-        double t0 = (lo - rs[a]) * inv;
-        double t1 = (hi - rs[a]) * inv;
+        double t0 = (lo - rs[a]) / d[a];
+        double t1 = (hi - rs[a]) / d[a];
         if (t0 > t1) std::swap(t0, t1);
         if (t0 > t_in) t_in = t0;
         if (t1 < t_out) t_out = t1;
@@ -478,8 +475,7 @@ ProjGeom<S> projector_geometry(const Scene& sc, const S aim[3]) {
     ProjGeom<S> G;
     for (int a = 0; a < 3; ++a) G.q[a] = aim[a] - P[a];
     G.nq = norm3(G.q);
-    S inv_n = 1.0 / G.nq;
-    for (int a = 0; a < 3; ++a) G.d[a] = G.q[a] * inv_n;
+    for (int a = 0; a < 3; ++a) G.d[a] = G.q[a] / G.nq;
     S den = G.d[0] * w.normal[0] + G.d[1] * w.normal[1] + G.d[2] * w.normal[2];
     G.wall = re(den) > 0.0;
     G.traced = false;
@@ -499,8 +495,7 @@ ProjGeom<S> projector_geometry(const Scene& sc, const S aim[3]) {
             if (P[a] < lo || P[a] > hi) inside = false;
             continue;
         }
-        S inv = 1.0 / G.d[a];
-        S t0 = (lo - P[a]) * inv, t1 = (hi - P[a]) * inv;
+        S t0 = (lo - P[a]) / G.d[a], t1 = (hi - P[a]) / G.d[a];
         if (re(t0) > re(t1)) std::swap(t0, t1);
         if (re(t0) > re(t_in)) { t_in = t0; ia = a; }
         if (re(t1) < re(t_out)) { t_out = t1; oa = a; }
