@@ -90,7 +90,8 @@ typedef struct {
 
 /* Pinhole camera (and projector): position, unit viewing direction `fwd`, unit
  * `up` orthogonal to it; right = fwd x up.  Image point (x, y) in pixels (y down)
- * looks along normalise(((x - cx)/fx) right - ((y - cy)/fy) up + fwd).
+ * looks along normalise(((x - cx)/fx) right - ((y - cy)/fy) up + fwd).  At most 2^40
+ * rays (width*height*spp) and 2^30 warp tiles of 32 rays (8x4 pixels at spp = 1).
  * spp rays per pixel: one ray through the pixel centre if spp == 1, otherwise
  * tent-filter (radius 1 px) offsets drawn from splitmix64 output k = 1 + (pixel*spp + s)
  * for `seed` (Sec. 2.3: triangular filter, Monte Carlo over the pixel). */
@@ -125,10 +126,12 @@ typedef struct {
     int connect_iters;
 } bos_light_desc;
 
-/* Integrator: fixed_steps > 0 gives every ray that many steps, otherwise
- * N = ceil(ell / (max_step_vox * min h)) for the straight in-box segment of
- * length ell.  integrator 0 = Sharma's Runge-Kutta-Nystrom, 1 = classic RK4
- * (forward only).  ckpt_every = K: the adjoint keeps the ray state every K steps. */
+/* Integrator: fixed_steps in [1, 2^24] gives every ray that many steps; fixed_steps = 0
+ * gives N = ceil(ell / (max_step_vox * min h)) for the straight in-box segment of
+ * length ell, max_step_vox in (1e-3, 1e6).  integrator 0 = Sharma's Runge-Kutta-Nystrom,
+ * 1 = classic RK4 (forward only), 2 = quasi-linear (the index field sampled on the
+ * straight line, Sec. 2.2).  ckpt_every = K in [1, 4096]: the adjoint keeps the ray state
+ * every K steps. */
 typedef struct {
     int fixed_steps;
     double max_step_vox;
@@ -169,13 +172,13 @@ bos_status_t bos_set_geometry(bos_ctx* ctx, const bos_camera_desc* cam, const bo
  *            hit from the straight (no-flow) hit of the same ray, metres along (eu, ev),
  *   hit_dev  (height*width*2 float64, nullable): mean wall coordinates of the hits.
  * Rays that never reach the wall plane contribute zero.  save_for_backward != 0
- * stores the ray state every ckpt_every steps for bos_backward (Sharma RKN, and the
- * FP32_COMP / BF16_COMP / FP64 precisions). */
+ * stores the ray state every ckpt_every steps for bos_backward (Sharma RKN or quasi-linear
+ * tracing, FP32_COMP or BF16_COMP precision; otherwise BOS_ERR_UNIMPLEMENTED). */
 bos_status_t bos_render(bos_ctx* ctx, float* I_dev, float* disp_dev, double* hit_dev, int save_for_backward,
                         void* stream);
 
 /* Steps a2-a5 for a subset of the pixels (the paper's reconstruction draws 5000 random
- * pixels of the BOS image per iteration, Sec. 3.2): pix_dev holds npix flat pixel indices
+ * pixels of the BOS image per iteration, Sec. 3.2): pix_dev holds npix (1 .. 2^30) flat pixel indices
  * y*width + x (any order, repeats allowed; indices outside the image are skipped and
  * flagged in bos_status).  I_dev receives npix float32 values and disp_dev (nullable)
  * npix*2, entry k belonging to pix_dev[k].  With save_for_backward, the next
@@ -238,12 +241,13 @@ bos_status_t bos_counter_add(uint64_t* counter_dev, uint64_t inc, void* stream);
 
 /* Step a6 (Sec. 2.4): given dL/dI (height*width float32, or npix values after
  * bos_render_pixels) for the most recent render with save_for_backward=1, write dL/dT
- * (nz*ny*nx float32).  Needs the
- * FP32_COMP or BF16_COMP precision, Sharma RKN and ckpt_every <= 64 (else
- * BOS_ERR_UNIMPLEMENTED).  dLdI_dev must not alias the accumulators.  Reverses the
- * Sharma steps of every ray from its checkpoints, scatters d L / d(deta, grad eta)
- * into the grid with warp-aggregated atomics, then applies the transpose of the
- * difference stencil and d deta/dT = -rho0 G T0 / T^2. */
+ * (nz*ny*nx float32).  Needs the FP32_COMP or BF16_COMP precision and Sharma RKN with
+ * ckpt_every <= 64, or quasi-linear tracing (integrator 2) (else BOS_ERR_UNIMPLEMENTED).
+ * dLdI_dev must not alias the accumulators.  Sharma RKN: reverses the steps of every ray
+ * from its checkpoints; quasi-linear: one forward-order sweep per ray from its final
+ * state (its field samples lie on the straight line, Sec. 2.2).  Both scatter
+ * d L / d(deta, grad eta) into the grid with warp-aggregated atomics, then apply the
+ * transpose of the difference stencil and d deta/dT = -rho0 G T0 / T^2. */
 bos_status_t bos_backward(bos_ctx* ctx, const float* dLdI_dev, float* dLdT_dev, void* stream);
 
 /* Copy the stored node values back in grid order: out_dev receives nz*ny*nx*4
@@ -280,20 +284,30 @@ bos_status_t bos_probe_read_l1(const void* buf_dev, uint64_t bytes, int repeats,
  * (a latency-critical loop, where allocation and freeing can synchronise the device, or
  * a host whose device memory is already handed out by another allocator).  No
  * counterpart in the paper: it runs the same field build and render as bos_set_grid +
- * bos_render (no displacement-free shortcut, no checkpoints), with the field store and
- * the work counters in one file-scope device array of 128 MiB that the library reserves
- * on every GPU it is loaded on, until the process exits.  The caller passes the inputs
- * (T_dev, pattern_dev) and outputs (I_dev, disp_dev nullable) as in bos_render.
+ * bos_set_geometry + bos_render (any precision, light mode and integrator those accept;
+ * no checkpoints), with the field store and the work counters in one file-scope device
+ * array of 128 MiB that the library reserves on every GPU it is loaded on, until the
+ * process exits.  The caller passes the inputs (T_dev, pattern_dev) and outputs (I_dev,
+ * disp_dev nullable) as in bos_render.  The descriptors are checked exactly as
+ * bos_set_grid and bos_set_geometry check them (BOS_ERR_INVALID_ARG).
  * Grids whose field store exceeds the array (128 MiB - 256 B; e.g. 128x128x96 cells
  * fit in float32, 256x256x192 do not) are rejected with BOS_ERR_INVALID_ARG and a
  * message in bos_last_error().  The first call on a device looks up the array's
  * address with that device current; make that first call before any stream capture.
  * Every call shares the array: calls whose work overlaps on the GPU race and must be
- * serialised by the caller.  Each call clears the counters and rebuilds the store, so
- * leftovers of the previous call do not matter.  Asynchronous on `stream`. */
+ * serialised by the caller.  Each call clears the counters and the error word and
+ * rebuilds the store, so leftovers of the previous call do not matter.  Errors the
+ * kernels detect are read with bos_noalloc_status.  Asynchronous on `stream`. */
 bos_status_t bos_render_noalloc(const bos_grid_desc* grid, const float* T_dev, const bos_camera_desc* cam,
                                 const bos_wall_desc* wall, const bos_light_desc* light, const float* pattern_dev,
                                 const bos_integrator_desc* integ, float* I_dev, float* disp_dev, void* stream);
+
+/* Device-detected errors of the most recent bos_render_noalloc on the current device
+ * (the kernels' sticky error word inside the shared array): BOS_OK, or
+ * BOS_ERR_DEVICE_CHECK with a message in bos_last_error().  Call it after synchronising
+ * that render's stream; like the array, it races with a bos_render_noalloc still running.
+ * Allocates nothing (one 4-byte device-to-host copy). */
+bos_status_t bos_noalloc_status(void);
 
 /* Sticky device-side status of the context (call after synchronising). */
 bos_status_t bos_status(bos_ctx* ctx);

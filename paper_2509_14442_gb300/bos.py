@@ -108,6 +108,7 @@ SIGNATURES = {
     "bos_probe_read_l1": (_i, [_v, _u64, _i, _v, _P(_d), _v]),
     "bos_render_noalloc": (_i, [_P(bos_grid_desc), _v, _P(bos_camera_desc), _P(bos_wall_desc), _P(bos_light_desc),
                                 _v, _P(bos_integrator_desc), _v, _v, _v]),
+    "bos_noalloc_status": (_i, []),
     "bos_status": (_i, [_v]),
     "bos_error_string": (C.c_char_p, [_i]),
     "bos_last_error": (C.c_char_p, []),
@@ -294,6 +295,11 @@ def bos_render_noalloc(grid: bos_grid_desc, T_dev, cam: bos_camera_desc, wall: b
                        light: bos_light_desc, pattern_dev, integ: bos_integrator_desc, I_dev, disp_dev, stream) -> None:
     check(lib().bos_render_noalloc(C.byref(grid), T_dev, C.byref(cam), C.byref(wall), C.byref(light), pattern_dev,
                                    C.byref(integ), I_dev, disp_dev, stream), "bos_render_noalloc")
+
+
+def bos_noalloc_status() -> None:
+    """Raise if the most recent bos_render_noalloc on the current device flagged an error."""
+    check(lib().bos_noalloc_status(), "bos_noalloc_status")
 
 
 def bos_status(ctx) -> None:

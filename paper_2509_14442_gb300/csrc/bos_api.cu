@@ -49,6 +49,12 @@ bos_status_t check_camera(const bos_camera_desc* c, const char* who) {
         return fail(BOS_ERR_INVALID_ARG, "%s: width, height and spp must be > 0", who);
     if ((long long)c->width * c->height * c->spp > (1LL << 40))
         return fail(BOS_ERR_INVALID_ARG, "%s: too many rays", who);
+    // the warp-tile index and the tile queue are 32-bit: keep the tile count (plus the
+    // warps of a grid that overshoot it) far below INT_MAX
+    const TileShape ts = tile_shape(c->width, c->height, c->spp);
+    if ((long long)ts.tiles_x * ts.tiles_y > kMaxTiles)
+        return fail(BOS_ERR_INVALID_ARG, "%s: %lld warp tiles of %d x %d pixels, at most %lld", who,
+                    (long long)ts.tiles_x * ts.tiles_y, ts.TW, ts.TH, kMaxTiles);
     return BOS_OK;
 }
 
@@ -211,6 +217,56 @@ namespace bos {
 
 void set_last_error(const char* msg) { g_last_error = msg; }
 
+bos_status_t check_grid_desc(const bos_grid_desc* d, const char* who) {
+    if (!d) return fail(BOS_ERR_INVALID_ARG, "%s: NULL grid", who);
+    if (d->nx < 2 || d->ny < 2 || d->nz < 2 || d->nx > 8192 || d->ny > 8192 || d->nz > 8192)
+        return fail(BOS_ERR_INVALID_ARG, "%s: need 2 <= n <= 8192 cells per axis, got %d x %d x %d", who, d->nx,
+                    d->ny, d->nz);
+    if ((long long)d->nx * d->ny * d->nz >= (1LL << 31))
+        return fail(BOS_ERR_INVALID_ARG, "%s: at most 2^31 - 1 cells", who);
+    if (!finite3(d->origin) || !finite3(d->extent) || !(d->extent[0] > 0) || !(d->extent[1] > 0) ||
+        !(d->extent[2] > 0))
+        return fail(BOS_ERR_INVALID_ARG, "%s: origin must be finite and extent > 0", who);
+    if (!(d->T0 > 0) || !(d->rho0 > 0) || !(d->G > 0) || !isfinite(d->T0 * d->rho0 * d->G))
+        return fail(BOS_ERR_INVALID_ARG, "%s: T0, rho0 and G must be > 0", who);
+    if (d->prec < BOS_PREC_FP64 || d->prec > BOS_PREC_BF16_COMP)
+        return fail(BOS_ERR_INVALID_ARG, "%s: unknown precision %d", who, d->prec);
+    return BOS_OK;
+}
+
+bos_status_t check_geometry_desc(const bos_camera_desc* cam, const bos_wall_desc* wall, const bos_light_desc* light,
+                                 const float* pattern_dev, const bos_integrator_desc* it, const char* who) {
+    char w[96];
+    if (!wall || !light || !it) return fail(BOS_ERR_INVALID_ARG, "%s: NULL argument", who);
+    snprintf(w, sizeof w, "%s: camera", who);
+    bos_status_t s = check_camera(cam, w);
+    if (s != BOS_OK) return s;
+    if (!finite3(wall->origin) || !unit3(wall->eu) || !unit3(wall->ev) || !unit3(wall->normal) ||
+        !(wall->size_u > 0) || !(wall->size_v > 0) || !isfinite(wall->size_u) || !isfinite(wall->size_v))
+        return fail(BOS_ERR_INVALID_ARG, "%s: wall needs a finite origin, unit axes and finite sizes > 0", who);
+    if (light->mode < 0 || light->mode > 2) return fail(BOS_ERR_INVALID_ARG, "%s: light mode %d", who, light->mode);
+    if (light->tw <= 0 || light->th <= 0 || !pattern_dev)
+        return fail(BOS_ERR_INVALID_ARG, "%s: pattern size must be > 0 and pattern non-NULL", who);
+    if ((long long)light->tw * light->th >= (1LL << 31))
+        return fail(BOS_ERR_INVALID_ARG, "%s: pattern of more than 2^31 - 1 texels", who);
+    if (light->mode == 2 && (light->connect_iters < 1 || light->connect_iters > 16))
+        return fail(BOS_ERR_INVALID_ARG, "%s: connect_iters must be in [1, 16]", who);
+    if (light->mode >= 1) {
+        snprintf(w, sizeof w, "%s: projector", who);
+        s = check_camera(&light->proj, w);
+        if (s != BOS_OK) return s;
+    }
+    if (it->fixed_steps < 0 || it->fixed_steps > kMaxFixedSteps)
+        return fail(BOS_ERR_INVALID_ARG, "%s: fixed_steps must be in [0, %d]", who, kMaxFixedSteps);
+    if (it->fixed_steps == 0 && !(it->max_step_vox > 1e-3 && it->max_step_vox < 1e6))
+        return fail(BOS_ERR_INVALID_ARG, "%s: max_step_vox must be in (1e-3, 1e6)", who);
+    if (it->integrator < 0 || it->integrator > 2)
+        return fail(BOS_ERR_INVALID_ARG, "%s: integrator %d", who, it->integrator);
+    if (it->ckpt_every < 1 || it->ckpt_every > 4096)
+        return fail(BOS_ERR_INVALID_ARG, "%s: ckpt_every must be in [1, 4096]", who);
+    return BOS_OK;
+}
+
 // Host IEEE double (this file is built without FMA contraction), in the order the
 // per-ray device code used for the same terms.
 RayConst ray_const_of(const SceneDev& S) {
@@ -371,18 +427,8 @@ uint64_t bos_device_bytes(bos_ctx* c) { return c ? c->bytes : 0; }
 
 bos_status_t bos_set_grid(bos_ctx* c, const bos_grid_desc* d, const float* T_dev, void* stream) {
     if (!c || !d || !T_dev) return fail(BOS_ERR_INVALID_ARG, "bos_set_grid: NULL argument");
-    if (d->nx < 2 || d->ny < 2 || d->nz < 2 || d->nx > 8192 || d->ny > 8192 || d->nz > 8192)
-        return fail(BOS_ERR_INVALID_ARG, "bos_set_grid: need 2 <= n <= 8192 cells per axis, got %d x %d x %d", d->nx,
-                    d->ny, d->nz);
-    if ((long long)d->nx * d->ny * d->nz >= (1LL << 31))
-        return fail(BOS_ERR_INVALID_ARG, "bos_set_grid: at most 2^31 - 1 cells");
-    if (!finite3(d->origin) || !finite3(d->extent) || !(d->extent[0] > 0) || !(d->extent[1] > 0) ||
-        !(d->extent[2] > 0))
-        return fail(BOS_ERR_INVALID_ARG, "bos_set_grid: origin must be finite and extent > 0");
-    if (!(d->T0 > 0) || !(d->rho0 > 0) || !(d->G > 0) || !isfinite(d->T0 * d->rho0 * d->G))
-        return fail(BOS_ERR_INVALID_ARG, "bos_set_grid: T0, rho0 and G must be > 0");
-    if (d->prec < BOS_PREC_FP64 || d->prec > BOS_PREC_BF16_COMP)
-        return fail(BOS_ERR_INVALID_ARG, "bos_set_grid: unknown precision %d", d->prec);
+    bos_status_t s0 = check_grid_desc(d, "bos_set_grid");
+    if (s0 != BOS_OK) return s0;
     DeviceGuard dg(c->device);
     GridDev g{};
     int n[3] = {d->nx, d->ny, d->nz};
@@ -416,27 +462,8 @@ bos_status_t bos_set_grid(bos_ctx* c, const bos_grid_desc* d, const float* T_dev
 bos_status_t bos_set_geometry(bos_ctx* c, const bos_camera_desc* cam, const bos_wall_desc* wall,
                               const bos_light_desc* light, const float* pattern_dev, const bos_integrator_desc* it) {
     if (!c || !wall || !light || !it) return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: NULL argument");
-    bos_status_t s = check_camera(cam, "bos_set_geometry: camera");
+    bos_status_t s = check_geometry_desc(cam, wall, light, pattern_dev, it, "bos_set_geometry");
     if (s != BOS_OK) return s;
-    if (!finite3(wall->origin) || !unit3(wall->eu) || !unit3(wall->ev) || !unit3(wall->normal) ||
-        !(wall->size_u > 0) || !(wall->size_v > 0))
-        return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: wall needs a finite origin, unit axes and sizes > 0");
-    if (light->mode < 0 || light->mode > 2) return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: light mode");
-    if (light->tw <= 0 || light->th <= 0 || !pattern_dev)
-        return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: pattern size must be > 0 and pattern non-NULL");
-    if (light->mode == 2 && (light->connect_iters < 1 || light->connect_iters > 16))
-        return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: connect_iters must be in [1, 16]");
-    if (light->mode >= 1) {
-        s = check_camera(&light->proj, "bos_set_geometry: projector");
-        if (s != BOS_OK) return s;
-    }
-    if (it->fixed_steps < 0 || it->fixed_steps > (1 << 24))
-        return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: fixed_steps out of range");
-    if (it->fixed_steps == 0 && !(it->max_step_vox > 1e-3 && it->max_step_vox < 1e6))
-        return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: max_step_vox out of range");
-    if (it->integrator < 0 || it->integrator > 2) return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: integrator");
-    if (it->ckpt_every < 1 || it->ckpt_every > 4096)
-        return fail(BOS_ERR_INVALID_ARG, "bos_set_geometry: ckpt_every must be in [1, 4096]");
     c->cam = to_dev(*cam);
     copy3(c->wall.origin, wall->origin);
     copy3(c->wall.eu, wall->eu);
@@ -528,8 +555,8 @@ bos_status_t bos_render(bos_ctx* c, float* I, float* disp, double* hit, int save
 bos_status_t bos_render_pixels(bos_ctx* c, const int32_t* pix, int64_t npix, float* I, float* disp,
                                int save_for_backward, void* stream) {
     if (!c) return fail(BOS_ERR_INVALID_ARG, "bos_render_pixels: NULL context");
-    if (!pix || npix <= 0 || npix > (1LL << 36))
-        return fail(BOS_ERR_INVALID_ARG, "bos_render_pixels: need a pixel list of 1 .. 2^36 entries");
+    if (!pix || npix <= 0 || npix > kMaxTiles)
+        return fail(BOS_ERR_INVALID_ARG, "bos_render_pixels: need a pixel list of 1 .. 2^30 entries");
     return render_impl(c, mode_of(c->grid.prec), I, disp, nullptr, save_for_backward, stream, pix, npix);
 }
 

@@ -9,6 +9,12 @@
 namespace bos {
 
 constexpr size_t kAlign = 256;
+
+// Limits every entry point enforces: warp tiles per launch (the tile index and the tile
+// queue are 32-bit; 2^30 leaves room for the warps that overshoot the last tile) and the
+// fixed step count per ray.
+constexpr long long kMaxTiles = 1LL << 30;
+constexpr int kMaxFixedSteps = 1 << 24;
 inline size_t align_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
 
 struct RenderOut {

@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "../../include/bos.h"
+#include "bos_ctx_internal.h"
 #include "bos_internal.h"
 
 namespace {
@@ -26,6 +27,7 @@ namespace {
 // Scratch: 256 bytes of work counters, then the field store.
 constexpr size_t kScratchBytes = (size_t)128 << 20;    // 128 MiB
 constexpr size_t kCounterBytes = 256;
+constexpr size_t kErrOffset = 4;                          // int error word after the tile counter
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) static unsigned char g_scratch[kScratchBytes];
@@ -90,19 +92,11 @@ extern "C" bos_status_t bos_render_noalloc(const bos_grid_desc* grid, const floa
     using namespace bos;
     if (!grid || !T_dev || !cam || !wall || !light || !pattern_dev || !integ || !I_dev)
         return refuse(BOS_ERR_INVALID_ARG, "NULL argument");
-    if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2 || grid->nx > 8192 || grid->ny > 8192 || grid->nz > 8192 ||
-        (long long)grid->nx * grid->ny * grid->nz >= (1LL << 31))
-        return refuse(BOS_ERR_INVALID_ARG, "grid of %d x %d x %d cells out of range", grid->nx, grid->ny, grid->nz);
-    if (!finite3(grid->origin) || !(grid->extent[0] > 0) || !(grid->extent[1] > 0) || !(grid->extent[2] > 0) ||
-        !(grid->T0 > 0) || !(grid->rho0 > 0) || !(grid->G > 0) || grid->prec < BOS_PREC_FP64 ||
-        grid->prec > BOS_PREC_BF16_COMP)
-        return refuse(BOS_ERR_INVALID_ARG, "malformed grid descriptor");
-    if (cam->width <= 0 || cam->height <= 0 || cam->spp <= 0 || !(cam->fx > 0) || !(cam->fy > 0) ||
-        light->tw <= 0 || light->th <= 0 || (light->mode < 0 || light->mode > 2) ||
-        (light->mode == 2 && (light->connect_iters < 1 || light->connect_iters > 16)) || integ->ckpt_every < 1 ||
-        (integ->fixed_steps <= 0 && !(integ->max_step_vox > 1e-3)) || integ->fixed_steps < 0 ||
-        (integ->integrator != 0 && integ->integrator != 1))
-        return refuse(BOS_ERR_INVALID_ARG, "malformed camera, light or integrator descriptor");
+    // the same descriptor checks as bos_set_grid and bos_set_geometry
+    bos_status_t s0 = check_grid_desc(grid, "bos_render_noalloc");
+    if (s0 != BOS_OK) return s0;
+    s0 = check_geometry_desc(cam, wall, light, pattern_dev, integ, "bos_render_noalloc");
+    if (s0 != BOS_OK) return s0;
     if (light->mode == 2 && grid->prec != BOS_PREC_FP32_COMP && grid->prec != BOS_PREC_BF16_COMP)
         return refuse(BOS_ERR_UNIMPLEMENTED, "the refracted projector connection needs a compensated precision");
 
@@ -179,11 +173,34 @@ extern "C" bos_status_t bos_render_noalloc(const bos_grid_desc* grid, const floa
     const int mode = grid->prec == BOS_PREC_FP32_COMP ? 1 : grid->prec == BOS_PREC_BF16_COMP ? 2
                      : grid->prec == BOS_PREC_FP32     ? 3
                                                        : 4;
-    WorkDev w{(int*)scratch, (unsigned long long*)(scratch + 64), (int*)scratch + 1};
+    WorkDev w{(int*)scratch, (unsigned long long*)(scratch + 64), (int*)(scratch + kErrOffset)};
     CkptDev ck{};
     ck.every = integ->ckpt_every;
     RenderOut o{I_dev, disp_dev, nullptr};
     e = launch_render(mode, S, o, w, ck, num_sms, st);
     if (e != cudaSuccess) return refuse(BOS_ERR_CUDA, "render: %s", cudaGetErrorString(e));
     return BOS_OK;
+}
+
+// Device-detected errors of the allocation-free render live in the shared array's error
+// word (written by the kernels, cleared by the next bos_render_noalloc).  Read it on the
+// current device after synchronising the stream of the call in question; it races with any
+// bos_render_noalloc still running on the device, like the array itself.
+extern "C" bos_status_t bos_noalloc_status(void) {
+    using namespace bos;
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return refuse(BOS_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    unsigned char* scratch = nullptr;
+    bos_status_t s = scratch_on(device, &scratch);
+    if (s != BOS_OK) return s;
+    int err = 0;
+    e = cudaMemcpy(&err, scratch + kErrOffset, sizeof err, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return refuse(BOS_ERR_CUDA, "reading the error word: %s", cudaGetErrorString(e));
+    switch (err) {
+        case DEV_OK: return BOS_OK;
+        case DEV_STEP_BUDGET: return refuse(BOS_ERR_DEVICE_CHECK, "a ray needed more steps than the step bound");
+        case DEV_BAD_PIXEL: return refuse(BOS_ERR_DEVICE_CHECK, "a pixel index is outside the image");
+        default: return refuse(BOS_ERR_DEVICE_CHECK, "device error %d", err);
+    }
 }

@@ -150,14 +150,10 @@ void CUDART_CB on_done(void* arg) {
 bos_status_t validate_request(const bos_request* r) {
     if (!r || !r->T_dev || !r->pattern_dev || !r->I_dev) return BOS_ERR_INVALID_ARG;
     if (r->target_dev && (!r->loss_dev || !r->dLdT_dev)) return BOS_ERR_INVALID_ARG;
-    if (r->grid.nx < 2 || r->grid.ny < 2 || r->grid.nz < 2 || r->grid.nx > 8192 || r->grid.ny > 8192 ||
-        r->grid.nz > 8192)
-        return BOS_ERR_INVALID_ARG;
-    if (r->cam.width <= 0 || r->cam.height <= 0 || r->cam.spp <= 0) return BOS_ERR_INVALID_ARG;
-    if (r->integ.ckpt_every < 1 || (r->integ.fixed_steps <= 0 && !(r->integ.max_step_vox > 1e-3)))
-        return BOS_ERR_INVALID_ARG;
-    if (r->grid.prec < BOS_PREC_FP64 || r->grid.prec > BOS_PREC_BF16_COMP) return BOS_ERR_INVALID_ARG;
-    return BOS_OK;
+    // the checks of bos_set_grid / bos_set_geometry, at submission rather than at launch
+    bos_status_t e = bos::check_grid_desc(&r->grid, "bos_submit");
+    if (e == BOS_OK) e = bos::check_geometry_desc(&r->cam, &r->wall, &r->light, r->pattern_dev, &r->integ, "bos_submit");
+    return e;
 }
 
 }  // namespace

@@ -65,3 +65,60 @@ def test_no_device_fails_loudly():
 
     with pytest.raises(bos.BosError):
         bos.bos_create(0, 0)
+
+
+def _noalloc_args(bos, scene, prec=None):
+    """Descriptors of a scene and stand-in device pointers: the calls below must refuse
+    before any pointer is used or any CUDA call is made."""
+    p = prec if prec is not None else bos.BOS_PREC_FP32_COMP
+    return [bos.grid_desc(scene.grid, p), 16, bos.camera_desc(scene.camera), bos.wall_desc(scene.wall),
+            bos.light_desc(scene.light), 32, bos.integ_desc(scene.integ), 64, None, None]
+
+
+def _call_noalloc(bos, args):
+    import ctypes as C
+
+    g, T, cam, wall, light, pat, integ, I, D, st = args
+    return bos.lib().bos_render_noalloc(C.byref(g), T, C.byref(cam), C.byref(wall), C.byref(light), pat,
+                                        C.byref(integ), I, D, st)
+
+
+def test_noalloc_checks_descriptors_like_set_geometry_without_touching_the_gpu():
+    """The allocation-free render applies the same descriptor checks as bos_set_grid and
+    bos_set_geometry: an unbounded fixed step count, a non-unit viewing direction, a
+    non-unit wall axis and a malformed projector camera are refused with
+    BOS_ERR_INVALID_ARG before anything reaches the device."""
+    from paper_2509_14442_gb300 import bos, scenes
+
+    sc = scenes.blob_cube(n=8, width=8, height=8, steps=4)
+    a = _noalloc_args(bos, sc)
+    a[6].fixed_steps = 1 << 25
+    assert _call_noalloc(bos, a) == bos.BOS_ERR_INVALID_ARG
+    assert b"fixed_steps" in bos.lib().bos_last_error()
+    a = _noalloc_args(bos, sc)
+    a[2].fwd[0] += 0.5                                  # not a unit vector
+    assert _call_noalloc(bos, a) == bos.BOS_ERR_INVALID_ARG
+    assert b"camera" in bos.lib().bos_last_error()
+    a = _noalloc_args(bos, sc)
+    a[3].eu[0] *= 2.0
+    assert _call_noalloc(bos, a) == bos.BOS_ERR_INVALID_ARG
+    assert b"wall" in bos.lib().bos_last_error()
+    room = scenes.room((16, 16, 12), 16, 16, 1, 7, field=False)
+    a = _noalloc_args(bos, room)
+    a[4].proj.fx = -1.0                                  # projector camera of light mode 1
+    assert _call_noalloc(bos, a) == bos.BOS_ERR_INVALID_ARG
+    assert b"projector" in bos.lib().bos_last_error()
+    a = _noalloc_args(bos, sc)
+    a[6].max_step_vox, a[6].fixed_steps = 1e9, 0
+    assert _call_noalloc(bos, a) == bos.BOS_ERR_INVALID_ARG
+
+
+def test_tile_count_is_capped_below_int_max():
+    """Images whose warp tiles would overflow the 32-bit tile index are refused."""
+    from paper_2509_14442_gb300 import bos, scenes
+
+    sc = scenes.blob_cube(n=8, width=8, height=8, steps=4)
+    a = _noalloc_args(bos, sc)
+    a[2].width, a[2].height, a[2].spp = 1 << 19, 1 << 19, 1      # 2^33 tiles of 8 x 4 pixels
+    assert _call_noalloc(bos, a) == bos.BOS_ERR_INVALID_ARG
+    assert b"warp tiles" in bos.lib().bos_last_error()
