@@ -12,6 +12,13 @@ A step is one pass of the whole hot path over one frame of synthetic input:
 Metric: ray-steps per second, one ray-step = one integrator step of one ray (sum of the
 per-ray step counts N of the flow render), whole job (all ranks).
 
+The default line (room_adj, one GPU) also carries the metric's other parts as sub-records,
+each from its own timed region in the same run: `fwd` (the room_fwd forward rate and its
+roofline), `precision` (render time and error against the FP64 oracle's sample of the
+CPU-baseline leg for every store/integrator precision) and `serving` (p50/p99 latency of
+the request loop at 0.7x its saturated throughput, and that throughput).  --no-extras
+leaves them out (profiler captures).
+
 Under torchrun every rank renders its own frame (independent seeds): weak scaling, no
 collective on the data path (the barrier only brackets the timing).
 
@@ -112,11 +119,15 @@ FP32_LANES_PER_SM = 128
 FP64_NOMINAL_FLOPS = 1.25e12
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the timed kernels,
-# from one ncu capture of the default workload (profiles/adjoint_kernel_room_adj.md).  It is
-# reported only while the kernel sources still hash to what was captured.
+# captured by ncu on the small case of the same kernels (room_adj_small: the 256^2x192 field,
+# a 512^2 camera; one kernel, one launch) and reported for the timed launch scaled by the
+# ratio of the two launches' algorithmic HBM bytes (`algorithmic_hbm`: checkpoints by
+# ray count and step count, field store, accumulators, images).  Reported only while the
+# kernel sources still hash to the captured ones.
 TRAFFIC_SOURCES = ("bos_forward.cu", "bos_adjoint.cu", "bos_comp.cuh", "bos_device.cuh")
-KERNEL_TRAFFIC = {"workload": "room_adj", "sha256": "cec8cb7ca436b3e03645b5bd3b27bd6bc2bd7b77b291011fac19e31fd69755e3",
-                  "render_kernel": 970890240 + 7275419904, "adjoint_kernel": 7071544064 + 502734336}
+TRAFFIC_CAPTURE = {"workload": "room_adj_small", "sha256": None,
+                   "render_kernel": None, "adjoint_kernel": None,
+                   "algorithmic": {"render_kernel": None, "adjoint_kernel": None}}
 
 
 def kernel_sources_sha256() -> str:
@@ -129,10 +140,24 @@ def kernel_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def kernel_traffic(workload: str, name: str):
-    if KERNEL_TRAFFIC["sha256"] is None or workload != KERNEL_TRAFFIC["workload"]:
+def algorithmic_hbm(scene, ckpt_slots: int, store_bytes: int) -> dict:
+    """Algorithmic DRAM bytes of one launch of the render (with checkpoints) and of the
+    adjoint: `ckpt_slots` = sum over rays of ceil(N/K) checkpoints of 48 B, plus 4 B of
+    path-length excess per ray; the field store read once; the adjoint's float4 node
+    accumulators (read and written by the atomics, 32 B per cell) and 4 B of dL/dI per
+    pixel; the render's 4 B image per pixel."""
+    ck = ckpt_slots * 48 + scene.rays * 4
+    return {"render_kernel": ck + store_bytes + scene.pixels * 4,
+            "adjoint_kernel": ck + store_bytes + scene.grid.cells * 32 + scene.pixels * 4}
+
+
+def kernel_traffic(name: str, alg: dict):
+    c = TRAFFIC_CAPTURE
+    if c["sha256"] is None or c.get(name) is None or kernel_sources_sha256() != c["sha256"]:
         return None
-    return KERNEL_TRAFFIC[name] if kernel_sources_sha256() == KERNEL_TRAFFIC["sha256"] else None
+    return {"bytes": c[name] * alg[name] / c["algorithmic"][name], "captured_bytes": c[name],
+            "captured_on": c["workload"], "scale": alg[name] / c["algorithmic"][name],
+            "scaling": "captured DRAM bytes x (algorithmic HBM bytes of this launch / of the captured launch)"}
 
 
 def parse():
@@ -146,6 +171,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="leave out the fwd / precision / serving sub-records")
     p.add_argument("--requests", type=int, default=256, help="serving: number of requests")
     p.add_argument("--sample-pixels", type=int, default=4000, help="precision: oracle-checked pixels")
     p.add_argument("--slots", type=int, default=6, help="serving: concurrent requests")
@@ -155,9 +181,10 @@ def parse():
 
 # ------------------------------------------------------------------ oracle (CPU) arm
 
-def oracle_rate(scene, adjoint: bool, seconds: float, seed: int = 0, threads: int = 0):
+def oracle_rate(scene, adjoint: bool, seconds: float, seed: int = 0, threads: int = 0) -> dict:
     """Time the FP64 oracle on a pixel sample sized for ~`seconds` on all host cores (or on
-    `threads` of them).  Returns (ray-steps/s, threads, sample description)."""
+    `threads` of them).  Returns rate (ray-steps/s), threads, a description of the sample,
+    the measured seconds, the sample's pixel indices and the oracle's render of them."""
     from oracle import oracle as O
 
     O.build()
@@ -174,7 +201,7 @@ def oracle_rate(scene, adjoint: bool, seconds: float, seed: int = 0, threads: in
             w = np.zeros((scene.camera.height, scene.camera.width))
             w.reshape(-1)[pix] = 1.0
             O.grad(scene, w, threads=threads)
-        return steps, time.perf_counter() - t0
+        return steps, time.perf_counter() - t0, out
 
     # size the sample from the forward render's per-pixel time (the oracle's gradient
     # re-traces every ray with a tape and then reverses it: about three renders' work, plus
@@ -183,9 +210,10 @@ def oracle_rate(scene, adjoint: bool, seconds: float, seed: int = 0, threads: in
     per_pix = run(np.sort(rng.choice(npix, m0, replace=False)), False)[1] / m0
     m = int(min(npix, max(m0, seconds / (per_pix * (4.0 if adjoint else 1.0)))))
     pix = np.sort(rng.choice(npix, m, replace=False))
-    steps, t = run(pix, adjoint)
+    steps, t, out = run(pix, adjoint)
     kind = "forward + adjoint" if adjoint else "forward"
-    return steps / t, threads, f"{m} of {npix} pixels ({kind}), {steps} ray-steps in {t:.1f} s"
+    return {"rate": steps / t, "threads": threads, "seconds": t, "pix": pix, "out": out,
+            "desc": f"{m} of {npix} pixels ({kind}), {steps} ray-steps in {t:.1f} s"}
 
 
 def oracle_arm(args):
@@ -214,8 +242,8 @@ def oracle_arm(args):
              ("room_256x256x192_forward_one_thread", S.room_adjoint, False, 5.0, 1),
              ("room_256x256x192_forward_adjoint", S.room_adjoint, True, 15.0, 0))
     for name, make, adj, secs, nthr in cases:
-        r, thr, desc = oracle_rate(make(), adj, secs, threads=nthr)
-        out[name] = {"ray_steps_per_s": r, "threads": thr, "sample": desc}
+        r = oracle_rate(make(), adj, secs, threads=nthr)
+        out[name] = {"ray_steps_per_s": r["rate"], "threads": r["threads"], "sample": r["desc"]}
     big = S.room_adjoint()
     k, j, i = np.unravel_index(np.argmax(big.T), big.T.shape)
     lo = [int(np.clip(c - 16, 0, n - 32)) for c, n in zip((i, j, k), big.grid.n)]
@@ -236,6 +264,9 @@ def oracle_arm(args):
 
 
 def reference_arm(args):
+    """The FP64 oracle on the host cores, as it stands: each step is one bounded pixel
+    sample of the same workload (a short sizing pass, then the timed sample); value = the
+    mean of the timed samples' ray-steps/s, ms_per_step = their mean measured time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -246,20 +277,22 @@ def reference_arm(args):
     wl = WORKLOADS[args.workload]
     scene = wl["make"](S.BASE_SEED + 2 if wl["adjoint"] else S.BASE_SEED + 1)
     per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
-    rates = []
-    desc = ""
+    rates, secs = [], []
+    r = None
     for i in range(args.warmup + args.steps):
-        r, threads, desc = oracle_rate(scene, wl["adjoint"], per_step, seed=i)
+        r = oracle_rate(scene, wl["adjoint"], per_step, seed=i)
         if i >= args.warmup:
-            rates.append(r)
+            rates.append(r["rate"])
+            secs.append(r["seconds"])
     v = statistics.mean(rates)
     unit = "ray-steps/s"
     print(json.dumps({
         "impl": "reference", "metric": metric_name(args), "value": v, "unit": unit, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_of(args, wl, None),
-        "cpu_baseline": {"value": v, "unit": unit, "cores": threads, "kind": "oracle", "sample": desc},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(secs) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args, wl, scene),
+        "cpu_baseline": {"value": v, "unit": unit, "cores": r["threads"], "kind": "oracle",
+                         "sample": f"per step: {r['desc']} (last step)"},
         "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -290,12 +323,14 @@ class Clocks:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            import tempfile
+
+            fd, self.path = tempfile.mkstemp(prefix="bos_clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
@@ -313,6 +348,13 @@ class Clocks:
             self.f.close()
 
     def summary(self):
+        try:
+            return self._summary()
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+
+    def _summary(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, smax, reasons = [], None, set()
@@ -409,20 +451,14 @@ def aggregate(my_ms: float, units_per_rank: int, dist=None, device=None):
     return job_ms, units_per_rank * world / (job_ms * 1e-3)
 
 
-def gpu_arm(args):
-    import torch
-    import torch.distributed as dist
-
-    from paper_2509_14442_gb300 import bos
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    wl = WORKLOADS[args.workload]
+def frame_bench(args, wl_name: str, ctxs: dict, rank: int = 0, world: int = 1, dist=None, e2e: bool = False):
+    """Time `args.steps` steps (after `args.warmup`) of workload `wl_name`: each step builds
+    the field store from T, renders I_flow (with checkpoints for the adjoint workloads),
+    then either L_BOS + backward, or I_ref.  L2 is flushed between timed steps.  With e2e,
+    the same steps again with T (and the target) copied from pinned host memory and the
+    result copied back, inside the timed region."""
+    torch, bos, dev = ctxs["torch"], ctxs["bos"], ctxs["dev"]
+    wl = WORKLOADS[wl_name]
     prec = bos.PRECISIONS[args.prec]
     scene = wl["make"]((S.BASE_SEED + 2 if wl["adjoint"] else S.BASE_SEED + 1) + 1000 * rank)
     stream = torch.cuda.current_stream()
@@ -430,13 +466,14 @@ def gpu_arm(args):
 
     T_host = torch.from_numpy(np.ascontiguousarray(scene.T)).pin_memory()
     T = T_host.to(dev)
-    ctx = bos.Context(local)
+    ctx = bos.Context(dev.index)
     ctx.set_scene(scene, prec, T=T)
+    store_bytes = bos.bos_device_bytes(ctx.h) - 256
     H, W = scene.camera.height, scene.camera.width
     I = torch.empty((H, W), dtype=torch.float32, device=dev)
     Iref = torch.empty_like(I)
     disp = torch.empty((H, W, 2), dtype=torch.float32, device=dev)
-    target = None
+    target = target_host = None
     if wl["adjoint"]:
         # target image: a render of the same plume family drawn with the next seed
         Tt = torch.from_numpy(S.with_target_seed(scene, scene.camera.seed % 100000 + 1)).to(dev)
@@ -445,15 +482,15 @@ def gpu_arm(args):
         ctx.render(disp=False, out=(target, None, None))
         ctx.set_grid(scene.grid, T, prec)
         target_host = target.cpu().pin_memory()
+        del Tt
     loss = torch.empty((1,), dtype=torch.float64, device=dev)
     dLdI = torch.empty_like(I)
     dLdT = torch.empty_like(T)
     flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)   # 256 MiB > L2
     ev_r = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    launches_per_step = 0
+    launches = {"n": 0}
 
     def step(T_in, ev=None):
-        nonlocal launches_per_step
         L = bos.lib()
         bos.check(L.bos_set_grid(ctx.h, bos.C.byref(bos.grid_desc(scene.grid, prec)), T_in.data_ptr(), sp),
                   "set_grid")
@@ -473,22 +510,26 @@ def gpu_arm(args):
             bos.check(L.bos_backward(ctx.h, dLdI.data_ptr(), dLdT.data_ptr(), sp), "backward")
             if ev is not None:
                 ev[3].record(stream)
-            launches_per_step = 5          # build_store, render, loss_l2, adjoint, gradient
+            launches["n"] = 5          # build_store, render, loss_l2, adjoint, gradient
         else:
             bos.check(L.bos_render_reference(ctx.h, Iref.data_ptr(), None, None, sp), "render_ref")
-            launches_per_step = 3          # build_store, render, render (reference)
+            launches["n"] = 3          # build_store, render, render (reference)
 
     for _ in range(args.warmup):
         step(T)
     torch.cuda.synchronize()
     ctx.status()
     steps_per_frame = ctx.last_ray_steps()
+    nsteps = ctx.ray_steps().to(torch.int64)
+    K = scene.integ.ckpt_every
+    ckpt_slots = int(((nsteps + K - 1) // K).sum().item()) if wl["adjoint"] else 0
+    del nsteps
 
     # ---- timed region: device time of K steps, L2 flushed between steps
-    if world > 1:
+    if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local)
+    clocks = Clocks(dev.index)
     step_ms, render_ms, back_ms = [], [], []
     with clocks:
         for _ in range(args.steps):
@@ -503,129 +544,220 @@ def gpu_arm(args):
             if wl["adjoint"]:
                 back_ms.append(ev_r[2].elapsed_time(ev_r[3]))
         torch.cuda.synchronize()
-    if world > 1:
+    if dist is not None:
         dist.barrier()
     ctx.status()
-    total_ms, value = aggregate(sum(step_ms), steps_per_frame * args.steps, dist if world > 1 else None, dev)
+    res = dict(scene=scene, wl=wl, steps_per_frame=steps_per_frame, step_ms=step_ms, render_ms=render_ms,
+               back_ms=back_ms, clocks=clocks.summary(), launches_per_step=launches["n"], store_bytes=store_bytes,
+               ckpt_slots=ckpt_slots)
 
-    # ---- end to end through the C ABI with host buffers: H2D inputs, D2H result
-    e2e_ms = []
-    h2d = T_host.numel() * 4 + (target_host.numel() * 4 if target is not None else 0)
-    out_host = torch.empty_like(dLdT if wl["adjoint"] else I, device="cpu").pin_memory()
-    loss_host = torch.empty((1,), dtype=torch.float64).pin_memory()
-    d2h = out_host.numel() * 4 + (8 if wl["adjoint"] else 0)
-    T_dev2 = torch.empty_like(T)
-    for i in range(args.warmup + args.steps):
-        flush.fill_(0.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        T_dev2.copy_(T_host, non_blocking=True)
-        if target is not None:
-            target.copy_(target_host, non_blocking=True)
-        step(T_dev2)
-        if wl["adjoint"]:
-            out_host.copy_(dLdT, non_blocking=True)
-            loss_host.copy_(loss, non_blocking=True)
-        else:
-            out_host.copy_(I, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        if i >= args.warmup:
-            e2e_ms.append(e0.elapsed_time(e1))
-    e2e_value = steps_per_frame * args.steps / (sum(e2e_ms) * 1e-3) * world
+    if e2e:
+        # ---- end to end through the C ABI with host buffers: H2D inputs, D2H result
+        e2e_ms = []
+        h2d = T_host.numel() * 4 + (target_host.numel() * 4 if target is not None else 0)
+        out_host = torch.empty_like(dLdT if wl["adjoint"] else I, device="cpu").pin_memory()
+        loss_host = torch.empty((1,), dtype=torch.float64).pin_memory()
+        d2h = out_host.numel() * 4 + (8 if wl["adjoint"] else 0)
+        T_dev2 = torch.empty_like(T)
+        for i in range(args.warmup + args.steps):
+            flush.fill_(0.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            T_dev2.copy_(T_host, non_blocking=True)
+            if target is not None:
+                target.copy_(target_host, non_blocking=True)
+            step(T_dev2)
+            if wl["adjoint"]:
+                out_host.copy_(dLdT, non_blocking=True)
+                loss_host.copy_(loss, non_blocking=True)
+            else:
+                out_host.copy_(I, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= args.warmup:
+                e2e_ms.append(e0.elapsed_time(e1))
+        res.update(e2e_ms=e2e_ms, h2d=h2d, d2h=d2h)
+    ctx.close()
+    del flush
+    torch.cuda.empty_cache()
+    return res
 
-    # ---- roofline of the timed kernels
+
+def measure_peaks(ctxs) -> dict:
+    torch, bos, dev = ctxs["torch"], ctxs["bos"], ctxs["dev"]
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
-    l2_peak = l2_read_peak(torch, dev, bos)
-    l1_peak = l1_read_peak(torch, dev, bos)
-    probe = fma_peaks(torch, dev, bos)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    clock_mhz = float(peaks.get("sm_max_mhz") or 2070.0)
-    if args.prec == "fp64":
+    return {"file": peaks, "l2": l2_read_peak(torch, dev, bos), "l1": l1_read_peak(torch, dev, bos),
+            "fma": fma_peaks(torch, dev, bos), "sms": torch.cuda.get_device_properties(dev).multi_processor_count}
+
+
+def alu_peak_of(prec: str, P: dict):
+    clock_mhz = float(P["file"].get("sm_max_mhz") or 2070.0)
+    probe = P["fma"]
+    if prec == "fp64":
         derived = FP64_NOMINAL_FLOPS * clock_mhz / 2070.0 / 1e12
         measured = probe["fp64"]
-        alu_src = (f"float64: GB300 nominal 1.25 TFLOP/s at 2070 MHz, scaled to {clock_mhz:.0f} MHz; "
-                   f"in-run probe {measured:.2f} TFLOP/s; the larger is the peak")
+        src = (f"float64: GB300 nominal 1.25 TFLOP/s at 2070 MHz, scaled to {clock_mhz:.0f} MHz; "
+               f"in-run probe {measured:.2f} TFLOP/s; the larger is the peak")
     else:
-        derived = sms * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+        derived = P["sms"] * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
         measured = max(probe["fp32"], probe["fp32x2"])
-        alu_src = (f"float32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x {clock_mhz:.0f} MHz "
-                   f"= {derived:.1f} TFLOP/s (derived); in-run probe {measured:.1f} TFLOP/s; the larger is the peak")
-    alu_peak = max(derived, measured)
+        src = (f"float32 FMA: {P['sms']} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x {clock_mhz:.0f} MHz "
+               f"= {derived:.1f} TFLOP/s (derived); in-run probe {measured:.1f} TFLOP/s; the larger is the peak")
+    return max(derived, measured), src
+
+
+def kernel_entries(res, prec: str, P: dict) -> dict:
+    """Roofline figures of the render and (adjoint workloads) the backward of one frame
+    benchmark: arithmetic (algorithmic flops per ray-step), L1 and L2 gathered bytes."""
+    wl, scene, spf = res["wl"], res["scene"], res["steps_per_frame"]
+    alu_peak, _ = alu_peak_of(prec, P)
     integ = {0: "rkn", 2: "quasi"}.get(scene.integ.integrator)
-    render_avg_ms = statistics.mean(render_ms)
-    fwd_b = wl.get("fwd_bytes", BYTES_PER_STEP[args.prec])
-    adj_b = wl.get("adj_bytes", ADJ_BYTES_PER_STEP.get(args.prec, 0))
+    fwd_b = wl.get("fwd_bytes", BYTES_PER_STEP[prec])
+    adj_b = wl.get("adj_bytes", ADJ_BYTES_PER_STEP.get(prec, 0))
+    fwd_l1 = wl.get("fwd_bytes", L1_BYTES_PER_STEP[prec])
+    adj_l1 = wl.get("fwd_bytes", ADJ_L1_BYTES_PER_STEP.get(prec, 0))
+    alg = algorithmic_hbm(scene, res["ckpt_slots"], res["store_bytes"]) if wl["adjoint"] else None
 
-    # quasi-linear tracing loads 2 new line samples per step (forward and one-sweep adjoint)
-    fwd_l1 = wl.get("fwd_bytes", L1_BYTES_PER_STEP[args.prec])
-    adj_l1 = wl.get("fwd_bytes", ADJ_L1_BYTES_PER_STEP.get(args.prec, 0))
-
-    def kernel_entry(ms, flops_per_step, bytes_per_step, l1_bytes_per_step, name):
-        tflops = flops_per_step * steps_per_frame / (ms * 1e-3) / 1e12 if flops_per_step else None
-        gbs = bytes_per_step * steps_per_frame / (ms * 1e-3) / 1e9
-        l1_gbs = l1_bytes_per_step * steps_per_frame / (ms * 1e-3) / 1e9
+    def entry(ms, flops_per_step, bytes_per_step, l1_bytes_per_step, name):
+        tflops = flops_per_step * spf / (ms * 1e-3) / 1e12 if flops_per_step else None
+        gbs = bytes_per_step * spf / (ms * 1e-3) / 1e9
+        l1_gbs = l1_bytes_per_step * spf / (ms * 1e-3) / 1e9
         return {"ms": ms, "flops_per_ray_step": flops_per_step, "achieved_tflops": tflops,
                 "frac": tflops / alu_peak if tflops is not None else None,
-                "bytes_per_ray_step": bytes_per_step, "achieved_gbs": gbs, "l2_frac": gbs / l2_peak,
-                "l1_bytes_per_ray_step": l1_bytes_per_step, "l1_achieved_gbs": l1_gbs, "l1_frac": l1_gbs / l1_peak,
-                "traffic": kernel_traffic(args.workload, name)}
+                "bytes_per_ray_step": bytes_per_step, "achieved_gbs": gbs, "l2_frac": gbs / P["l2"],
+                "l1_bytes_per_ray_step": l1_bytes_per_step, "l1_achieved_gbs": l1_gbs, "l1_frac": l1_gbs / P["l1"],
+                "algorithmic_hbm_bytes": alg[name] if alg else None,
+                "traffic": kernel_traffic(name, alg) if alg else None}
 
-    kernels = {"render_kernel": kernel_entry(render_avg_ms, FLOPS_PER_STEP.get(integ), fwd_b, fwd_l1,
-                                             "render_kernel")}
-    dominant = "render_kernel"
+    k = {"render_kernel": entry(statistics.mean(res["render_ms"]), FLOPS_PER_STEP.get(integ), fwd_b, fwd_l1,
+                                "render_kernel")}
     if wl["adjoint"]:
-        kernels["adjoint_kernel"] = kernel_entry(statistics.mean(back_ms), ADJ_FLOPS_PER_STEP.get(integ), adj_b,
-                                                 adj_l1, "adjoint_kernel")
-        kernels["adjoint_kernel"]["timed"] = "bos_backward: accumulator clear + adjoint_kernel + gradient_kernel"
-        dominant = "adjoint_kernel"
+        k["adjoint_kernel"] = entry(statistics.mean(res["back_ms"]), ADJ_FLOPS_PER_STEP.get(integ), adj_b, adj_l1,
+                                    "adjoint_kernel")
+        k["adjoint_kernel"]["timed"] = "bos_backward: accumulator clear + adjoint_kernel + gradient_kernel"
+    return k
+
+
+def fwd_record(args, ctxs, P) -> dict:
+    """The metric's forward half: room_fwd (128^2x96 plume, 1024^2 camera, 4 jittered spp)."""
+    res = frame_bench(args, "room_fwd", ctxs)
+    k = kernel_entries(res, args.prec, P)["render_kernel"]
+    spf = res["steps_per_frame"]
+    return {"workload": "room_fwd", "description": WORKLOADS["room_fwd"]["desc"],
+            "ray_steps_per_s": spf * len(res["step_ms"]) / (sum(res["step_ms"]) * 1e-3),
+            "ms_per_step": statistics.mean(res["step_ms"]), "render_ms": k["ms"],
+            "render_ray_steps_per_s": spf / (k["ms"] * 1e-3), "ray_steps_per_frame": spf,
+            "step": "field build + I_flow (with displacement) + I_ref", "steps": args.steps,
+            "l1_frac": k["l1_frac"], "l2_frac": k["l2_frac"], "alu_frac": k["frac"], "render_kernel": k,
+            "clocks": res["clocks"]}
+
+
+def cpu_leg(scene, adjoint: bool, seconds: float, precision_pixels: int):
+    """The CPU baseline: the FP64 oracle as it stands on a bounded pixel sample of the
+    workload on all host cores.  With precision_pixels > 0, its renders of that many of the
+    sample's pixels (and the oracle's render of them on the BF16-rounded field) are kept for
+    the precision table's error columns."""
+    from oracle import oracle as O
+
+    r = oracle_rate(scene, adjoint, seconds)
+    cpu = {"value": r["rate"], "unit": "ray-steps/s", "cores": r["threads"], "kind": "oracle", "sample": r["desc"]}
+    if precision_pixels <= 0:
+        return cpu, None
+    sel = np.linspace(0, len(r["pix"]) - 1, min(precision_pixels, len(r["pix"]))).astype(np.int64)
+    pix = r["pix"][sel]
+    true = {"I": r["out"]["I"].reshape(-1)[sel], "disp": r["out"]["disp"].reshape(-1, 2)[sel]}
+    de = O.deta_from_T(scene.grid, scene.T.astype(np.float64))
+    gr = O.grad_from_deta(scene.grid, de)
+    o = O.render(scene, field=O.NodeField(bf16_round(de), bf16_round(gr)), pix=pix, threads=r["threads"])
+    return cpu, {"pix": pix, "true": true, "bf16": {"I": o["I"].reshape(-1), "disp": o["disp"].reshape(-1, 2)}}
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_14442_gb300 import bos
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctxs = {"torch": torch, "bos": bos, "dev": dev}
+    wl = WORKLOADS[args.workload]
+
+    res = frame_bench(args, args.workload, ctxs, rank, world, dist if world > 1 else None, e2e=True)
+    scene, spf = res["scene"], res["steps_per_frame"]
+    total_ms, value = aggregate(sum(res["step_ms"]), spf * args.steps, dist if world > 1 else None, dev)
+    e2e_value = spf * args.steps / (sum(res["e2e_ms"]) * 1e-3) * world
+
+    # ---- roofline of the timed kernels (peaks measured in the same run)
+    P = measure_peaks(ctxs)
+    alu_peak, alu_src = alu_peak_of(args.prec, P)
+    kernels = kernel_entries(res, args.prec, P)
+    dominant = "adjoint_kernel" if wl["adjoint"] else "render_kernel"
     dk = kernels[dominant]
+    traffic = dk["traffic"]["bytes"] if dk["traffic"] else None
     roofline = {"bound": "alu", "kernel": dominant, "achieved": dk["achieved_tflops"], "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": dk["frac"], "traffic": dk["traffic"], "peak_source": alu_src,
+                "unit": "TFLOP/s", "frac": dk["frac"], "traffic": traffic, "peak_source": alu_src,
                 "flops_per_ray_step": dk["flops_per_ray_step"],
-                "fma_probe_tflops": probe,
+                "fma_probe_tflops": P["fma"],
                 "note": ("algorithmic flops per ray-step counted from the method's formulas; the gathers are "
                          "served on chip and DRAM carries only the store, checkpoints and outputs, so the "
-                         "arithmetic roof is the one that applies; the kernels sit below it, limited by "
-                         "instruction latency at 12 (adjoint) / 24 (forward) warps per SM"),
+                         "arithmetic roof is the one that applies"),
                 "kernels": kernels,
-                "l2": {"achieved": dk["achieved_gbs"], "peak": l2_peak, "unit": "GB/s", "frac": dk["l2_frac"],
+                "l2": {"achieved": dk["achieved_gbs"], "peak": P["l2"], "unit": "GB/s", "frac": dk["l2_frac"],
                        "bytes_per_ray_step": dk["bytes_per_ray_step"],
                        "peak_source": "in-run L2 read probe (bos_probe_read, 24 MiB x 50 passes, best of 10)",
                        "note": ("gather roofline R = L2 read bandwidth / algorithmic gathered bytes per ray-step; "
                                 "the gathers hit L1, so a kernel can exceed R")},
-                "l1": {"achieved": dk["l1_achieved_gbs"], "peak": l1_peak, "unit": "GB/s", "frac": dk["l1_frac"],
+                "l1": {"achieved": dk["l1_achieved_gbs"], "peak": P["l1"], "unit": "GB/s", "frac": dk["l1_frac"],
                        "bytes_per_ray_step": dk["l1_bytes_per_ray_step"],
                        "peak_source": "in-run L1 read probe (bos_probe_read_l1, 256-bit loads, 64 KiB x 200 passes "
                                       "per block, best of 10)",
                        "note": "the gathers' bytes loaded through L1 per ray-step over the L1 read bandwidth"},
-                "hbm_peak_gbs": peaks.get("hbm_gbs")}
-    if dk["traffic"] is not None and peaks.get("hbm_gbs"):
-        # the same kernel against the HBM roofline: measured DRAM bytes per launch over its time
-        # (the backward's timed region also clears the accumulators and runs the gradient epilogue)
-        hbm_gbs = dk["traffic"] / (dk["ms"] * 1e-3) / 1e9
-        roofline["hbm"] = {"achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                           "frac": hbm_gbs / peaks["hbm_gbs"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
-    cpu = None
+                "hbm_peak_gbs": P["file"].get("hbm_gbs")}
+    if P["file"].get("hbm_gbs"):
+        # the same kernel against the HBM roofline: DRAM bytes per launch (measured on the
+        # small case and scaled, else the algorithmic bytes) over the kernel's time
+        hb = traffic if traffic is not None else dk["algorithmic_hbm_bytes"]
+        if hb is not None:
+            hbm_gbs = hb / (dk["ms"] * 1e-3) / 1e9
+            roofline["hbm"] = {"achieved": hbm_gbs, "peak": P["file"]["hbm_gbs"], "unit": "GB/s",
+                               "frac": hbm_gbs / P["file"]["hbm_gbs"],
+                               "bytes": "traffic (scaled ncu capture)" if traffic is not None else "algorithmic",
+                               "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+
+    extras = world == 1 and not args.no_extras and args.workload == "room_adj"
+    out = {}
+    if extras:
+        out["fwd"] = fwd_record(args, ctxs, P)
+    cpu, orc = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        r, threads, desc = oracle_rate(scene, wl["adjoint"], args.cpu_seconds)
-        cpu = {"value": r, "unit": "ray-steps/s", "cores": threads, "kind": "oracle", "sample": desc}
+        cpu, orc = cpu_leg(scene, wl["adjoint"], args.cpu_seconds, args.sample_pixels if extras else 0)
+    if extras:
+        out["precision"] = precision_record(args, ctxs, P, scene, orc)
+        out["serving"] = serving_record(args, ctxs, rates=(0.7,))
     if rank == 0:
-        print(json.dumps({
+        line = {
             "metric": metric_name(args), "value": value, "unit": "ray-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded plume fields and speckle patterns)",
             "config": config_of(args, wl, scene),
-            "ray_steps_per_frame": steps_per_frame,
-            "clocks": clocks.summary(),
-            "e2e": {"value": e2e_value, "unit": "ray-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches_per_step * args.steps,
+            "ray_steps_per_frame": spf,
+            "clocks": res["clocks"],
+            "e2e": {"value": e2e_value, "unit": "ray-steps/s", "h2d_bytes_per_step": res["h2d"],
+                    "d2h_bytes_per_step": res["d2h"]},
+            "gpu_launches": res["launches_per_step"] * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
-        }))
-    ctx.close()
+        }
+        line.update(out)
+        print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
 
@@ -636,16 +768,12 @@ SERVE_GRIDS = [(64, 64, 64), (128, 128, 96), (256, 256, 192)]
 SERVE_IMAGES = [256, 1024, 2048]
 
 
-def serving_arm(args):
+def serving_record(args, ctxs, rates=(0.7, 1.0)) -> dict:
     """256 requests (forward or forward + adjoint; grid and image drawn per request; plume
-    seed per request) through the continuous-batching server under a 120 GB admission
-    limit: first all at once (saturated throughput), then with Poisson arrivals at 0.7x and
-    1.0x that rate; latency = completion - submission."""
-    import torch
-
-    from paper_2509_14442_gb300 import bos
-
-    dev = torch.device("cuda", 0)
+    seed per request) through the continuous-batching server under a 120 GiB admission
+    limit: first all at once (saturated throughput), then with Poisson arrivals at the
+    given fractions of that rate; latency = completion - submission."""
+    torch, bos, dev = ctxs["torch"], ctxs["bos"], ctxs["dev"]
     rng = np.random.default_rng(S.BASE_SEED + 5)
     n = args.requests
     pattern_np = S.speckle(512, 512, S.BASE_SEED + 5000)
@@ -666,7 +794,7 @@ def serving_arm(args):
         else:
             r["disp"] = torch.empty((im, im, 2), device=dev)
         if (g, im) not in classes:
-            ctx = bos.Context(0)
+            ctx = bos.Context(dev.index)
             ctx.set_grid(sc.grid, T, bos.BOS_PREC_FP32_COMP)
             ctx.set_geometry(sc.camera, sc.wall, sc.light, sc.integ, pattern=pattern)
             steps = int(ctx.ray_steps().sum().item())
@@ -683,7 +811,7 @@ def serving_arm(args):
                                 pattern.data_ptr(), sc.integ, p("I"), p("disp"), p("target"), p("loss"), p("dLdT"))
 
     def run(rate):
-        srv = bos.Server(0, args.mem_limit_gb << 30, args.slots)
+        srv = bos.Server(dev.index, args.mem_limit_gb << 30, args.slots)
         t0 = time.perf_counter()
         gaps = np.random.default_rng(7).exponential(1.0 / rate, n) if rate else np.zeros(n)
         due = t0 + np.cumsum(gaps) - gaps[0]
@@ -712,17 +840,34 @@ def serving_arm(args):
 
     run(0)                                   # warm-up (module load, first launches)
     sat = run(0)
-    at07 = run(0.7 * sat["req_per_s"])
-    at10 = run(1.0 * sat["req_per_s"])
+    out = {"requests": n, "slots": args.slots, "admission_limit_gb": args.mem_limit_gb,
+           "mix": "fwd | fwd+adjoint x grids {64^3,128^2x96,256^2x192} x images {256^2,1024^2,2048^2}, 1 spp",
+           "saturated": sat}
+    for f in rates:
+        out[f"at_{f}x"] = run(f * sat["req_per_s"])
+    if 0.7 in rates:
+        out["latency_ms_at_0.7x"] = {"p50": out["at_0.7x"]["p50_ms"], "p99": out["at_0.7x"]["p99_ms"]}
+    del reqs
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_arm(args):
+    import torch
+
+    from paper_2509_14442_gb300 import bos
+
+    ctxs = {"torch": torch, "bos": bos, "dev": torch.device("cuda", 0)}
+    r = serving_record(args, ctxs, rates=(0.7, 1.0))
     print(json.dumps({
-        "metric": "serving p99 latency (ms), Poisson arrivals at 0.7x saturated throughput", "value": at07["p99_ms"],
-        "unit": "ms", "n_gpus": 1, "steps": n, "warmup": n, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded plume fields and speckle patterns)",
-        "config": {"workload": "serving", "requests": n, "slots": args.slots, "admission_limit_gb": args.mem_limit_gb,
-                   "mix": "fwd | fwd+adjoint x grids {64^3,128^2x96,256^2x192} x images {256^2,1024^2,2048^2}, 1 spp"},
-        "latency_ms": {"p50": at07["p50_ms"], "p99": at07["p99_ms"]},
-        "at_0.7x": at07, "at_1.0x": at10, "saturated": sat,
-    }))
+        "metric": "serving p99 latency (ms), Poisson arrivals at 0.7x saturated throughput",
+        "value": r["at_0.7x"]["p99_ms"], "unit": "ms", "n_gpus": 1, "steps": r["requests"],
+        "warmup": r["requests"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded plume fields and speckle patterns)",
+        "config": {"workload": "serving", "requests": r["requests"], "slots": r["slots"],
+                   "admission_limit_gb": r["admission_limit_gb"], "mix": r["mix"]},
+        "latency_ms": r["latency_ms_at_0.7x"], "at_0.7x": r["at_0.7x"], "at_1.0x": r["at_1.0x"],
+        "saturated": r["saturated"]}))
 
 
 # ------------------------------------------------------------------ reconstruction loop
@@ -823,41 +968,25 @@ def bf16_round(x):
     return np.ldexp(np.round(m * 256.0), e - 8)
 
 
-def precision_arm(args):
-    """The 256x256x192 / 2048^2 scene rendered by every precision: render time and, on a
-    seeded sample of pixels, displacement and intensity errors against the FP64 oracle
-    (and for BF16 also against the oracle run on the BF16-dequantised field)."""
-    import torch
-
-    from oracle import oracle as O
-    from paper_2509_14442_gb300 import bos
-
-    O.build()
-    dev = torch.device("cuda", 0)
-    scene = S.room_adjoint(S.BASE_SEED + 2)
+def precision_record(args, ctxs, P, scene, orc) -> dict:
+    """The 256^2x192 / 2048^2 scene rendered by every precision: render time, its share of
+    the arithmetic peak and, given the oracle's renders of a pixel sample (`orc`, from the
+    CPU-baseline leg; None leaves the error columns out), displacement and intensity errors
+    against the FP64 oracle (for BF16 also against the oracle on the BF16-rounded field)."""
+    torch, bos, dev = ctxs["torch"], ctxs["bos"], ctxs["dev"]
     T = torch.as_tensor(scene.T, device=dev)
-    pix = np.sort(np.random.default_rng(4).choice(scene.pixels, args.sample_pixels, replace=False))
-    threads = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    orc = O.render(scene, pix=pix, threads=threads)
-    de = O.deta_from_T(scene.grid, scene.T.astype(np.float64))
-    gr = O.grad_from_deta(scene.grid, de)
-    orc_bf16 = O.render(scene, field=O.NodeField(bf16_round(de), bf16_round(gr)), pix=pix, threads=threads)
-    t_orc = time.perf_counter() - t0
-    dmax = float(np.abs(orc["disp"]).max())
+    fp32_peak, _ = alu_peak_of("fp32_comp", P)
+    fp64_peak, _ = alu_peak_of("fp64", P)
+    dmax = float(np.abs(orc["true"]["disp"]).max()) if orc else None
 
     def err(I, D, ref):
+        pix = orc["pix"]
         return {"disp_rel": float(np.abs(D.reshape(-1, 2)[pix] - ref["disp"]).max()) / dmax,
                 "I_abs": float(np.abs(I.reshape(-1)[pix] - ref["I"]).max())}
 
-    # arithmetic peaks (as in the main bench line: the larger of the derived and the probed)
-    probe = fma_peaks(torch, dev, bos)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = max(sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12, probe["fp32"], probe["fp32x2"])
-    fp64_peak = max(FP64_NOMINAL_FLOPS / 1e12, probe["fp64"])
     out = {}
     for name in ("fp64", "fp32", "fp32_comp", "bf16_comp"):
-        ctx = bos.Context(0)
+        ctx = bos.Context(dev.index)
         ctx.set_scene(scene, bos.PRECISIONS[name], T=T)
         reps = 1 if name == "fp64" else 5
         ms = []
@@ -871,26 +1000,44 @@ def precision_arm(args):
                 ms.append(e0.elapsed_time(e1))
         ctx.status()
         steps = ctx.last_ray_steps()
-        Ih, Dh = I.cpu().numpy().astype(np.float64), D.cpu().numpy().astype(np.float64)
         rate = steps / (statistics.mean(ms) * 1e-3)
         tflops = rate * FLOPS_PER_STEP["rkn"] / 1e12
         peak = fp64_peak if name == "fp64" else fp32_peak
         r = {"render_ms": statistics.mean(ms), "ray_steps_per_s": rate,
              "alu": {"achieved_tflops": tflops, "peak_tflops": peak, "frac": tflops / peak,
-                     "dtype": "f64" if name == "fp64" else "f32"},
-             "vs_fp64_oracle": err(Ih, Dh, orc)}
-        if name == "bf16_comp":
-            r["vs_oracle_on_bf16_field"] = err(Ih, Dh, orc_bf16)
+                     "dtype": "f64" if name == "fp64" else "f32"}}
+        if orc is not None:
+            Ih, Dh = I.cpu().numpy().astype(np.float64), D.cpu().numpy().astype(np.float64)
+            r["vs_fp64_oracle"] = err(Ih, Dh, orc["true"])
+            if name == "bf16_comp":
+                r["vs_oracle_on_bf16_field"] = err(Ih, Dh, orc["bf16"])
         out[name] = r
         ctx.close()
+    del T
+    torch.cuda.empty_cache()
+    return {"grid": list(scene.grid.n), "image": [scene.camera.width, scene.camera.height], "spp": scene.camera.spp,
+            "sample_pixels": int(len(orc["pix"])) if orc else 0, "max_displacement_m": dmax,
+            "errors": "against the FP64 oracle's render of the CPU-baseline leg's pixel sample" if orc else None,
+            "precisions": out}
+
+
+def precision_arm(args):
+    import torch
+
+    from paper_2509_14442_gb300 import bos
+
+    ctxs = {"torch": torch, "bos": bos, "dev": torch.device("cuda", 0)}
+    scene = S.room_adjoint(S.BASE_SEED + 2)
+    P = measure_peaks(ctxs)
+    cpu, orc = cpu_leg(scene, False, args.cpu_seconds, args.sample_pixels)
+    r = precision_record(args, ctxs, P, scene, orc)
     print(json.dumps({
-        "metric": "ray-steps/s and errors per precision (forward render)", "value": out["fp32_comp"]["ray_steps_per_s"],
-        "unit": "ray-steps/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
-        "data": "synthetic (seeded plume fields and speckle patterns)",
-        "config": {"workload": "precision", "grid": list(scene.grid.n), "image": [scene.camera.width,
-                   scene.camera.height], "spp": scene.camera.spp, "sample_pixels": args.sample_pixels,
-                   "max_displacement_m": dmax, "oracle_seconds": t_orc, "oracle_threads": threads},
-        "fma_probe_tflops": probe, "precisions": out}))
+        "metric": "ray-steps/s and errors per precision (forward render)",
+        "value": r["precisions"]["fp32_comp"]["ray_steps_per_s"], "unit": "ray-steps/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded plume fields and speckle patterns)",
+        "config": {"workload": "precision", "grid": r["grid"], "image": r["image"], "spp": r["spp"],
+                   "sample_pixels": r["sample_pixels"], "max_displacement_m": r["max_displacement_m"]},
+        "fma_probe_tflops": P["fma"], "precisions": r["precisions"], "cpu_baseline": cpu}))
 
 
 def main():

@@ -30,18 +30,51 @@ def test_reference_arm_is_silent_on_other_ranks():
 
 
 def test_traffic_is_reported_only_for_the_captured_sources():
+    """The DRAM traffic of a timed launch is the small-case capture scaled by the ratio of
+    algorithmic HBM bytes, and only while the kernel sources hash to the captured ones."""
     import bench
 
-    sha = bench.kernel_sources_sha256()
-    assert bench.kernel_traffic("room_fwd", "render_kernel") is None          # another workload
-    if bench.KERNEL_TRAFFIC["sha256"] == sha:
-        assert bench.kernel_traffic("room_adj", "adjoint_kernel") == bench.KERNEL_TRAFFIC["adjoint_kernel"]
-    saved = bench.KERNEL_TRAFFIC["sha256"]
+    from paper_2509_14442_gb300 import scenes
+
+    sc = scenes.room((16, 16, 12), 64, 32, 1, 7, field=False)
+    alg = bench.algorithmic_hbm(sc, ckpt_slots=1000, store_bytes=4096)
+    assert alg["render_kernel"] == 1000 * 48 + sc.rays * 4 + 4096 + sc.pixels * 4
+    assert alg["adjoint_kernel"] == 1000 * 48 + sc.rays * 4 + 4096 + sc.grid.cells * 32 + sc.pixels * 4
+    saved = dict(bench.TRAFFIC_CAPTURE)
     try:
-        bench.KERNEL_TRAFFIC["sha256"] = "0" * 64                         # sources changed since the capture
-        assert bench.kernel_traffic("room_adj", "adjoint_kernel") is None
+        bench.TRAFFIC_CAPTURE.update(sha256=bench.kernel_sources_sha256(), adjoint_kernel=3.0e6,
+                                     algorithmic={"render_kernel": 1.0, "adjoint_kernel": 1.5e6})
+        t = bench.kernel_traffic("adjoint_kernel", alg)
+        assert abs(t["bytes"] - 3.0e6 * alg["adjoint_kernel"] / 1.5e6) < 1e-6 * t["bytes"]
+        bench.TRAFFIC_CAPTURE["sha256"] = "0" * 64                        # sources changed since the capture
+        assert bench.kernel_traffic("adjoint_kernel", alg) is None
     finally:
-        bench.KERNEL_TRAFFIC["sha256"] = saved
+        bench.TRAFFIC_CAPTURE.clear()
+        bench.TRAFFIC_CAPTURE.update(saved)
+
+
+def test_reference_arm_reports_the_gpu_arms_config_and_its_measured_time(monkeypatch, capsys):
+    """The reference arm names the same workload keys as the GPU arm (grid, image, spp,
+    ckpt_every) and reports the measured time of its samples as ms_per_step."""
+    import argparse
+
+    import bench
+
+    def fake_rate(scene, adjoint, seconds, seed=0, threads=0):
+        return {"rate": 1.0e6, "threads": 3, "seconds": 0.25, "pix": None, "out": None, "desc": "fake sample"}
+
+    monkeypatch.setattr(bench, "oracle_rate", fake_rate)
+    monkeypatch.setenv("RANK", "0")
+    args = argparse.Namespace(workload="room_fwd_small", steps=2, warmup=1, gpus=1, prec="fp32_comp")
+    bench.reference_arm(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    wl = bench.WORKLOADS["room_fwd_small"]
+    want = bench.config_of(args, wl, wl["make"](bench.S.BASE_SEED + 1))
+    assert line["config"] == want
+    for k in ("grid", "image", "spp", "ckpt_every", "workload"):
+        assert k in line["config"]
+    assert line["ms_per_step"] == 250.0
+    assert line["cpu_baseline"]["cores"] == 3 and line["e2e"]["h2d_bytes_per_step"] == 0
 
 
 def test_per_ray_step_tables_follow_their_counts():
