@@ -654,6 +654,349 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
     flush_rows(rows, ca.key != kNoKey, ca, acc, nx, nxy);
 }
 
+// ---- software-pipelined Sharma adjoint (camera rays; light modes 0 and 1) ------------------
+//
+// The arithmetic of adjoint_kernel<E, false>, scheduled so that every warp carries two
+// independent dependency chains: in round c it reverses segment c of its rays (three
+// value-and-gradient evaluations, the adjoint algebra, the corner scatter) while it
+// recomputes segment c - 1 from its checkpoint (the forward Sharma steps whose states round
+// c - 1 reverses).  Source order interleaves the two chains stage by stage, so the gathers
+// of one are in flight while the other computes.  The segment states are double-buffered
+// per warp; the rays' float64 set-up values are parked in shared memory for the rounds.
+
+constexpr int kParkDoubles = 12;   // per lane: d[3], tw, t_in, ell, rin[3], eta_in, Ib, etab
+
+__host__ __device__ constexpr size_t pipe_warp_bytes() {
+    return (size_t)(32 * kRow + 2 * 32 * kStageStride) * sizeof(float) + (size_t)32 * kParkDoubles * sizeof(double);
+}
+
+#ifndef BOS_ADJ_PIPE_MIN_BLOCKS
+#define BOS_ADJ_PIPE_MIN_BLOCKS 5
+#endif
+
+// One forward Sharma step of the recompute (the float32 operations of comp_step, without
+// the path-length excess, which the adjoint reads from the forward's record), split at its
+// stages so that the caller can interleave it with a reverse step.
+struct FwdChain {
+    long long U[3];
+    float dr[3], cr[3], dv[3], cv[3];
+    float A[3], B[3];
+};
+
+template <class E>
+__device__ __forceinline__ float4 fwd_stage(const CompField<E>& F, const long long U[3], const float q[3], BrickCache& bc) {
+    int ci[3];
+    float cf[3];
+    return comp_eval(F, U, q, bc, ci, cf);
+}
+
+template <class E>
+__global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_PIPE_MIN_BLOCKS)
+    adjoint_pipe_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
+    extern __shared__ float4 smem4[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int K = ck.every;
+    unsigned char* wbase = reinterpret_cast<unsigned char*>(smem4) + (size_t)warp * pipe_warp_bytes();
+    float* rows = reinterpret_cast<float*>(wbase);                       // [32][kRow]
+    float* stg = rows + 32 * kRow;                                        // [2][32][kStageStride]
+    double* park = reinterpret_cast<double*>(stg + 2 * 32 * kStageStride) + lane * kParkDoubles;
+    // [2][K][6][32] segment states of this warp (two rounds in flight)
+    float* bufs = adj.seg + ((size_t)blockIdx.x * kAdjWarps + warp) * ((size_t)2 * K * 6 * 32);
+    const CompField<E> F = {static_cast<const E*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
+                            {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
+    const int nx = S.g.n[0], nxy = S.g.n[0] * S.g.n[1];
+    const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
+    const TileShape ts = tile_shape(W, H, spp);
+    const int ntiles = tile_count(S, ts);
+    float* acc = reinterpret_cast<float*>(adj.acc);
+    {
+        float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
+        for (int c = 0; c < 8; ++c) row[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    __syncwarp();
+    CellAcc ca = {kNoKey};
+
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntiles) break;
+        const int sl = lane % ts.G;
+        const TilePix tp = tile_pixel(S, ts, t, lane);
+        for (int qs = 0; qs < ts.samples_per_lane; ++qs) {
+            const int s = ts.samples_per_lane == 1 ? sl : qs;
+            const long long slot = ((long long)t * 32 + lane) * ts.samples_per_lane + qs;
+            int N = 0;
+            float dt = 0.0f;
+            CompState st0;
+            CompConst k;
+            {
+                Ray R;
+                R.N = 0;
+                R.wall = false;
+                double Ib = 0.0, eta_in = 1.0, rin[3] = {0.0, 0.0, 0.0};
+                if (tp.valid) {
+                    R = ray_setup(S, tp.px, tp.py, s);
+                    Ib = (double)adj.dLdI[(size_t)tp.out] / spp;
+                }
+                const bool act = tp.valid && R.wall && R.N > 0 && Ib != 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    st0.U[a] = 0;
+                    k.dU[a] = k.dUh[a] = 0;
+                    k.dS[a] = k.dhat[a] = 0.0f;
+                }
+                k.dt = k.step_len = 0.0f;
+                if (act) {
+                    comp_setup(S, F, S.cam.pos, R, st0, k, eta_in, rin);
+                    N = R.N;
+                    dt = k.dt;
+                }
+                for (int a = 0; a < 3; ++a) {
+                    park[a] = R.d[a];
+                    park[6 + a] = rin[a];
+                }
+                park[3] = R.tw;
+                park[4] = R.t_in;
+                park[5] = R.ell;
+                park[9] = eta_in;
+                park[10] = Ib;
+                park[11] = 0.0;                 // etab
+            }
+            const int nseg = (N + K - 1) / K;
+            const int nseg_max = __reduce_max_sync(0xffffffffu, (unsigned)nseg);
+            float rb[3] = {0, 0, 0}, vb[3] = {0, 0, 0}, dtb = 0.0f, lenb = 0.0f;
+            FwdChain fc;
+            for (int a = 0; a < 3; ++a) {
+                fc.U[a] = 0;
+                fc.dr[a] = fc.cr[a] = fc.dv[a] = fc.cv[a] = fc.A[a] = fc.B[a] = 0.0f;
+            }
+            BrickCache bcf = {kNoKey, 0u}, bcr = {kNoKey, 0u};
+            for (int c = nseg_max; c >= 0; --c) {
+                const int f = c - 1;                        // segment recomputed this round
+                const bool has_fwd = f >= 0;                // warp-uniform
+                const bool has_rev = c < nseg_max;          // warp-uniform
+                // forward chain: segment f of this lane, states stored for j < fstore, steps for j < fsteps
+                int fstore = 0, fsteps = 0;
+                if (has_fwd && f < nseg) {
+                    const int fn0 = f * K, fn1 = min(fn0 + K, N);
+                    fstore = fn1 - fn0;
+                    fsteps = f == nseg - 1 ? fstore : fstore - 1;   // the last state is the next checkpoint
+                    const float4 s0 = ck.state[((size_t)f * 3 + 0) * ck.nrays + slot];
+                    const float4 s1 = ck.state[((size_t)f * 3 + 1) * ck.nrays + slot];
+                    const float4 s2 = ck.state[((size_t)f * 3 + 2) * ck.nrays + slot];
+                    fc.dr[0] = s0.x; fc.dr[1] = s0.y; fc.dr[2] = s0.z;
+                    fc.dv[0] = s1.x; fc.dv[1] = s1.y; fc.dv[2] = s1.z;
+                    fc.cv[0] = s2.x; fc.cv[1] = s2.y; fc.cv[2] = s2.z;
+                    fc.cr[0] = s0.w; fc.cr[1] = s1.w; fc.cr[2] = s2.w;
+                    for (int a = 0; a < 3; ++a) fc.U[a] = st0.U[a] + (long long)fn0 * k.dU[a];
+                }
+                // reverse chain: segment c of this lane, local step K-1-j active while < rlen
+                int rlen = 0;
+                long long Ur[3];
+                if (has_rev && c < nseg) rlen = min(c * K + K, N) - c * K;
+                for (int a = 0; a < 3; ++a) Ur[a] = st0.U[a] + (long long)(c * K + K - 1) * k.dU[a];
+                float* fbuf = bufs + (size_t)(f & 1) * K * 6 * 32 + lane;
+                const float* rbuf = bufs + (size_t)(c & 1) * K * 6 * 32 + lane;
+                for (int j = 0; j < K; ++j) {
+                    // ================= forward: store the state, stage 1
+                    const bool fa = has_fwd && j < fsteps;
+                    float vf1[3];
+                    float4 ef;
+                    if (has_fwd) {
+                        if (j < fstore) {
+                            float* p = fbuf + (size_t)j * 6 * 32;
+                            p[0] = fc.dr[0]; p[32] = fc.dr[1]; p[64] = fc.dr[2];
+                            p[96] = fc.dv[0]; p[128] = fc.dv[1]; p[160] = fc.dv[2];
+                        }
+                        ef = fwd_stage(F, fc.U, fc.dr, bcf);
+                    }
+                    // ================= reverse: load the state, stage 1
+                    const int rl = K - 1 - j;
+                    const bool ra = has_rev && rl < rlen;
+                    float dr[3] = {0, 0, 0}, dvv[3] = {0, 0, 0};
+                    Stage s;
+                    float D1[3] = {0, 0, 0}, D2[3] = {0, 0, 0}, D3[3] = {0, 0, 0}, A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+                    long long U2[3], U3[3];
+                    if (has_rev) {
+                        if (ra) {
+                            const float* p = rbuf + (size_t)rl * 6 * 32;
+                            dr[0] = p[0]; dr[1] = p[32]; dr[2] = p[64];
+                            dvv[0] = p[96]; dvv[1] = p[128]; dvv[2] = p[160];
+                        }
+                        for (int a = 0; a < 3; ++a) {
+                            U2[a] = Ur[a] + k.dUh[a];
+                            U3[a] = Ur[a] + k.dU[a];
+                        }
+                        stage_eval(F, Ur, dr, bcr, s);
+                    }
+                    // ================= forward stage 2
+                    if (has_fwd) {
+                        rhs_of(ef, vf1);
+                        float q[3];
+                        long long Uf2[3];
+                        for (int a = 0; a < 3; ++a) {
+                            fc.A[a] = dt * vf1[a];
+                            q[a] = fc.dr[a] + (0.5f * dt) * fc.dv[a] + (0.125f * dt) * fc.A[a];
+                            Uf2[a] = fc.U[a] + k.dUh[a];
+                        }
+                        ef = fwd_stage(F, Uf2, q, bcf);
+                    }
+                    // ================= reverse stage 2
+                    if (has_rev) {
+                        rhs_from(s.ig, D1);
+                        put_stage(stg, lane, s);
+                        float q[3];
+                        for (int a = 0; a < 3; ++a) A[a] = dt * D1[a];
+                        for (int a = 0; a < 3; ++a) q[a] = dr[a] + (0.5f * dt) * dvv[a] + (0.125f * dt) * A[a];
+                        stage_eval(F, U2, q, bcr, s);
+                    }
+                    // ================= forward stage 3
+                    if (has_fwd) {
+                        float D[3], q[3];
+                        long long Uf3[3];
+                        rhs_of(ef, D);
+                        for (int a = 0; a < 3; ++a) {
+                            fc.B[a] = dt * D[a];
+                            q[a] = fc.dr[a] + dt * fc.dv[a] + (0.5f * dt) * fc.B[a];
+                            Uf3[a] = fc.U[a] + k.dU[a];
+                        }
+                        ef = fwd_stage(F, Uf3, q, bcf);
+                    }
+                    // ================= reverse stage 3
+                    if (has_rev) {
+                        rhs_from(s.ig, D2);
+                        put_stage(stg + 32 * kStageStride, lane, s);
+                        float q[3];
+                        for (int a = 0; a < 3; ++a) B[a] = dt * D2[a];
+                        for (int a = 0; a < 3; ++a) q[a] = dr[a] + dt * dvv[a] + (0.5f * dt) * B[a];
+                        stage_eval(F, U3, q, bcr, s);
+                        rhs_from(s.ig, D3);
+                    }
+                    // ================= forward update
+                    if (has_fwd) {
+                        float D[3];
+                        rhs_of(ef, D);
+                        for (int a = 0; a < 3; ++a) {
+                            const float C = dt * D[a];
+                            const float inc_r = dt * (fc.dv[a] + (fc.A[a] + 2.0f * fc.B[a]) * (1.0f / 6.0f));
+                            const float inc_v = (fc.A[a] + 4.0f * fc.B[a] + C) * (1.0f / 6.0f);
+                            float dr1 = fc.dr[a], cr1 = fc.cr[a], dv1 = fc.dv[a], cv1 = fc.cv[a];
+                            kahan_add(dr1, cr1, inc_r);
+                            kahan_add(dv1, cv1, inc_v);
+                            if (fa) {
+                                fc.dr[a] = dr1;
+                                fc.cr[a] = cr1;
+                                fc.dv[a] = dv1;
+                                fc.cv[a] = cv1;
+                                fc.U[a] += k.dU[a];
+                            }
+                        }
+                    }
+                    if (!has_rev) continue;
+                    // ================= reverse: adjoint of the step (as in adjoint_kernel)
+                    float u[3] = {0, 0, 0};
+                    {
+                        float inc[3], nn = 0.0f;
+                        for (int a = 0; a < 3; ++a) {
+                            inc[a] = k.dS[a] + dt * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
+                            nn += inc[a] * inc[a];
+                        }
+                        const float rn = rsqrtf(nn);
+                        for (int a = 0; a < 3; ++a) u[a] = ra ? inc[a] * rn : 0.0f;
+                    }
+                    float rbs[3];
+                    for (int a = 0; a < 3; ++a) rbs[a] = rb[a] + lenb * u[a];
+                    float Ab[3], Bb[3], Cb[3], rn_[3], vn_[3], dtb_s = 0.0f;
+                    for (int a = 0; a < 3; ++a) {
+                        Ab[a] = (dt * (1.0f / 6.0f)) * rbs[a] + vb[a] * (1.0f / 6.0f);
+                        Bb[a] = (dt * (1.0f / 3.0f)) * rbs[a] + vb[a] * (4.0f / 6.0f);
+                        Cb[a] = vb[a] * (1.0f / 6.0f);
+                        rn_[a] = rbs[a];
+                        vn_[a] = vb[a] + dt * rbs[a];
+                        dtb_s += rbs[a] * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
+                    }
+                    float Db[3], pb[3];
+                    float4 Q;
+                    for (int a = 0; a < 3; ++a) {
+                        dtb_s += Cb[a] * D3[a];
+                        Db[a] = dt * Cb[a];
+                    }
+                    rhs_adjoint(F, s.ig, Db, pb, Q);
+                    accumulate(rows, ra, s.key, s.cf, Q, ca, acc, nx, nxy);
+                    for (int a = 0; a < 3; ++a) {
+                        rn_[a] += pb[a];
+                        vn_[a] += dt * pb[a];
+                        Bb[a] += (0.5f * dt) * pb[a];
+                        dtb_s += pb[a] * (dvv[a] + 0.5f * B[a]);
+                    }
+                    for (int a = 0; a < 3; ++a) {
+                        dtb_s += Bb[a] * D2[a];
+                        Db[a] = dt * Bb[a];
+                    }
+                    get_stage(stg + 32 * kStageStride, lane, s);
+                    rhs_adjoint(F, s.ig, Db, pb, Q);
+                    accumulate(rows, ra, s.key, s.cf, Q, ca, acc, nx, nxy);
+                    for (int a = 0; a < 3; ++a) {
+                        rn_[a] += pb[a];
+                        vn_[a] += (0.5f * dt) * pb[a];
+                        Ab[a] += (0.125f * dt) * pb[a];
+                        dtb_s += pb[a] * (0.5f * dvv[a] + 0.125f * A[a]);
+                    }
+                    for (int a = 0; a < 3; ++a) {
+                        dtb_s += Ab[a] * D1[a];
+                        Db[a] = dt * Ab[a];
+                    }
+                    get_stage(stg, lane, s);
+                    rhs_adjoint(F, s.ig, Db, pb, Q);
+                    accumulate(rows, ra, s.key, s.cf, Q, ca, acc, nx, nxy);
+                    if (ra) {
+                        for (int a = 0; a < 3; ++a) {
+                            rb[a] = rn_[a] + pb[a] - lenb * u[a];
+                            vb[a] = vn_[a];
+                        }
+                        dtb += dtb_s;
+                    }
+                    for (int a = 0; a < 3; ++a) Ur[a] -= k.dU[a];
+                }
+                // lanes whose last segment was recomputed this round: adjoint of the wall epilogue
+                if (has_fwd && f == nseg - 1 && N > 0) {
+                    double d[3], rin[3], rN[3], vN[3], drb[3], dvb[3], lb = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        d[a] = park[a];
+                        rin[a] = park[6 + a];
+                    }
+                    const double ell = park[5], eta_in = park[9];
+                    for (int a = 0; a < 3; ++a) {
+                        rN[a] = rin[a] + ell * d[a] + ((double)fc.dr[a] - (double)fc.cr[a]);
+                        vN[a] = eta_in * d[a] + ((double)fc.dv[a] - (double)fc.cv[a]);
+                    }
+                    const double len_before = park[4] + ell + (double)ck.excess[slot];
+                    wall_adjoint(S, rN, vN, len_before, park[10], drb, dvb, lb);
+                    for (int a = 0; a < 3; ++a) {
+                        rb[a] = (float)drb[a];
+                        vb[a] = (float)dvb[a];
+                    }
+                    lenb = (float)lb;
+                    park[11] = dvb[0] * d[0] + dvb[1] * d[1] + dvb[2] * d[2];
+                }
+                __syncwarp();
+            }
+            // ---- entry: v0 = eta_in d and dt = ell / (N eta_in), eta_in = 1 + deta(r_in)
+            int ci[3] = {0, 0, 0};
+            float cf[3] = {0, 0, 0};
+            double etab = 0.0;
+            const bool act = N > 0;
+            if (act) {
+                etab = park[11] - (double)dtb * (double)dt / park[9];
+                const float zero[3] = {0, 0, 0};
+                comp_cell(F, st0.U, zero, ci, cf);
+            }
+            accumulate(rows, act, cell_key_of(F, ci), cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), ca, acc, nx, nxy);
+        }
+    }
+    flush_rows(rows, ca.key != kNoKey, ca, acc, nx, nxy);
+}
+
 // Adjoint of quasi-linear tracing (Sec. 2.2).  The stage points lie on the straight
 // line, so the outputs are linear in the sampled D values and no position adjoint flows
 // back through them.  Reversing a step leaves the position adjoint unchanged and adds
@@ -881,8 +1224,28 @@ static cudaError_t launch_adjoint_c(const SceneDev& S, const CkptDev& ck, const 
     return cudaGetLastError();
 }
 
+template <class E>
+static cudaError_t launch_adjoint_pipe(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
+                                      int num_sms, cudaStream_t st) {
+    size_t smem = (size_t)kAdjWarps * pipe_warp_bytes();
+    cudaError_t e = cudaFuncSetAttribute(adjoint_pipe_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pipe_kernel<E>, kAdjWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1 || adj.seg == nullptr) return cudaErrorInvalidConfiguration;
+    const int blocks = num_sms * per_sm < kAdjMaxBlocks ? num_sms * per_sm : kAdjMaxBlocks;
+    adjoint_pipe_kernel<E><<<blocks, kAdjWarps * 32, smem, st>>>(S, ck, adj, w);
+    return cudaGetLastError();
+}
+
+#ifndef BOS_ADJ_PIPELINE
+#define BOS_ADJ_PIPELINE 1
+#endif
+
 // The refracted projector connection (light mode 2) reverses each sample's projector ray
-// too; it has its own instantiation so that the other modes do not carry it.
+// too; it has its own instantiation so that the other modes do not carry it.  The other
+// modes take the software-pipelined kernel.
 template <class E>
 static cudaError_t launch_adjoint_t(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
                                     int num_sms, cudaStream_t st) {
@@ -890,6 +1253,7 @@ static cudaError_t launch_adjoint_t(const SceneDev& S, const CkptDev& ck, const 
         if (ck.pstate == nullptr || ck.conn == nullptr) return cudaErrorInvalidValue;
         return launch_adjoint_c<E, true>(S, ck, adj, w, num_sms, st);
     }
+    if (BOS_ADJ_PIPELINE) return launch_adjoint_pipe<E>(S, ck, adj, w, num_sms, st);
     return launch_adjoint_c<E, false>(S, ck, adj, w, num_sms, st);
 }
 

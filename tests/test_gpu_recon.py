@@ -108,9 +108,73 @@ def test_reconstruction_lowers_the_image_loss(bos):
     torch.cuda.synchronize()
     l1 = full_loss(rec.T)
     rec.close()
-    # the same loop on the oracle (full-image renders, the same minibatch sizes) falls by
-    # more than 1000x in 100 iterations
     assert l0 > 0 and l1 < 0.05 * l0, (l0, l1)
+
+
+def _adabelief_np(theta, g, m, s, t, lr, b1, b2, eps):
+    """AdaBelief (Zhuang et al., NeurIPS 2020) in float64, the update bos_adabelief_step makes."""
+    m[:] = b1 * m + (1.0 - b1) * g
+    s[:] = b2 * s + (1.0 - b2) * (g - m) ** 2 + eps
+    theta -= lr * (m / (1.0 - b1 ** t)) / (np.sqrt(s / (1.0 - b2 ** t)) + eps)
+
+
+@pytest.mark.parametrize("integrator", [0, 2])
+def test_reconstruction_iterations_match_the_oracle_loop(bos, orc, integrator):
+    """k iterations of the minibatch reconstruction (Sec. 2.4 Eq. 3 with lambda_2 = lambda_3
+    = 0, Sec. 3.2) on the GPU and on the oracle from the same inputs: the same target image
+    (rendered by the oracle), the same pixel minibatches (splitmix64 draws, computed on each
+    side from the generator's definition), the oracle's discrete-adjoint gradient of the
+    scaled minibatch L_BOS and a float64 AdaBelief.  The field after k iterations agrees
+    element by element.
+
+    Tolerance: eps is set so that sqrt(eps / (1 - beta2)) is ~1 % of the largest gradient;
+    below that AdaBelief's step is linear in the gradient, so the float32 gradient's error
+    (~1e-6 of the largest gradient) moves T by ~1e-4 lr per iteration at most; the bound is
+    2e-3 lr per iteration, summed over the k iterations."""
+    from paper_2509_14442_gb300.recon import Reconstructor
+
+    sc = S.room((12, 12, 9), 32, 32, 1, 3970, pattern_size=32)
+    sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=integrator, ckpt_every=16))
+    truth = sc.T.astype(np.float64)
+    target = orc.render(sc)["I"]                              # (H, W) float64, the measurement
+    T0 = np.full(truth.shape, S.T_AMBIENT)
+    H, W = sc.camera.height, sc.camera.width
+    k, batch, lr, b1, b2, seed = 5, 256, 0.2, 0.9, 0.999, 11
+    scale = 1e11
+
+    def draw(d):
+        return np.array([(orc.splitmix64_output(seed, d * batch + j + 1) * (H * W)) >> 64 for j in range(batch)],
+                        dtype=np.int64)
+
+    # the gradient scale of this scene fixes eps: the first iteration's largest gradient
+    def oracle_grad(T, pix):
+        s_T = sc.replace(T=T)
+        I = orc.render(s_T, pix=pix)["I"]
+        w = np.zeros(H * W)
+        np.add.at(w, pix, -2.0 * scale * (target.reshape(-1)[pix] - I))
+        return orc.grad(s_T, w.reshape(H, W)), I
+
+    g0, _ = oracle_grad(T0, draw(0))
+    eps = (0.01 * float(np.abs(g0).max())) ** 2 * (1.0 - b2)
+    T = T0.copy()
+    m, s = np.zeros_like(T), np.zeros_like(T)
+    for it in range(k):
+        g, _ = oracle_grad(T, draw(it))
+        _adabelief_np(T, g, m, s, it + 1, lr, b1, b2, eps)
+
+    rec = Reconstructor(sc, torch.as_tensor(target.astype(np.float32)), torch.as_tensor(T0.astype(np.float32)),
+                        batch=batch, lr=lr, beta1=b1, beta2=b2, eps=eps, loss_scale=scale, seed=seed)
+    for _ in range(k):
+        rec.step()
+    torch.cuda.synchronize()
+    rec.ctx.status()
+    Tg = rec.T.cpu().numpy().astype(np.float64)
+    rec.close()
+    moved = np.abs(T - T0)
+    assert moved.max() > 0.5 * lr                               # the loop did move the field
+    err = np.abs(Tg - T)
+    assert err.max() <= 2e-3 * lr * k, (err.max(), moved.max())
+    assert np.linalg.norm(Tg - T) <= 1e-3 * np.linalg.norm(T - T0)
 
 
 def test_graph_replayed_iterations_match_eager_ones(bos):

@@ -37,7 +37,7 @@ def test_footprint_counts_every_buffer(bos):
     rays = 256 * 256
     n_max = int(np.ceil(np.sqrt(4 ** 2 + 4 ** 2 + 3 ** 2) / (0.5 * 3.0 / 64))) + 2
     ck = -(-n_max // 16) * 48 * rays
-    seg = 1024 * 2 * 16 * 6 * 32 * 4          # per-warp segment states of the Sharma adjoint (K = 16)
+    seg = 2 * 1024 * 2 * 16 * 6 * 32 * 4      # two segments of step states per warp of the Sharma adjoint (K = 16)
     expect = fwd + ck + rays * 4 + 64 ** 3 * 16 + seg + rays * 4
     assert adj == expect
     # quasi-linear tracing keeps only the final state per ray
