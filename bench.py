@@ -124,7 +124,7 @@ FP64_NOMINAL_FLOPS = 1.25e12
 # ratio of the two launches' algorithmic HBM bytes (`algorithmic_hbm`: checkpoints by
 # ray count and step count, field store, accumulators, images).  Reported only while the
 # kernel sources still hash to the captured ones.
-TRAFFIC_SOURCES = ("bos_forward.cu", "bos_adjoint.cu", "bos_comp.cuh", "bos_device.cuh")
+TRAFFIC_SOURCES = ("bos_forward.cu", "bos_adjoint.cu", "bos_comp.cuh", "bos_device.cuh", "bos_full.cuh")
 TRAFFIC_CAPTURE = {"workload": "room_adj_small", "sha256": None,
                    "render_kernel": None, "adjoint_kernel": None,
                    "algorithmic": {"render_kernel": None, "adjoint_kernel": None}}

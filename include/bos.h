@@ -172,8 +172,9 @@ bos_status_t bos_set_geometry(bos_ctx* ctx, const bos_camera_desc* cam, const bo
  *            hit from the straight (no-flow) hit of the same ray, metres along (eu, ev),
  *   hit_dev  (height*width*2 float64, nullable): mean wall coordinates of the hits.
  * Rays that never reach the wall plane contribute zero.  save_for_backward != 0
- * stores the ray state every ckpt_every steps for bos_backward (Sharma RKN or quasi-linear
- * tracing, FP32_COMP or BF16_COMP precision; otherwise BOS_ERR_UNIMPLEMENTED). */
+ * stores the ray state every ckpt_every steps for bos_backward: FP32_COMP or BF16_COMP with
+ * Sharma RKN or quasi-linear tracing, or FP64 with Sharma RKN (the absolute (r, v) as six
+ * doubles); otherwise BOS_ERR_UNIMPLEMENTED. */
 bos_status_t bos_render(bos_ctx* ctx, float* I_dev, float* disp_dev, double* hit_dev, int save_for_backward,
                         void* stream);
 
@@ -241,8 +242,10 @@ bos_status_t bos_counter_add(uint64_t* counter_dev, uint64_t inc, void* stream);
 
 /* Step a6 (Sec. 2.4): given dL/dI (height*width float32, or npix values after
  * bos_render_pixels) for the most recent render with save_for_backward=1, write dL/dT
- * (nz*ny*nx float32).  Needs the FP32_COMP or BF16_COMP precision and Sharma RKN with
- * ckpt_every <= 64, or quasi-linear tracing (integrator 2) (else BOS_ERR_UNIMPLEMENTED).
+ * (nz*ny*nx float32).  Needs the FP32_COMP or BF16_COMP precision with Sharma RKN
+ * (ckpt_every <= 64) or quasi-linear tracing (integrator 2), or the FP64 precision with
+ * Sharma RKN (ckpt_every <= 64), which runs the whole adjoint in float64 (else
+ * BOS_ERR_UNIMPLEMENTED).
  * dLdI_dev must not alias the accumulators.  Sharma RKN: reverses the steps of every ray
  * from its checkpoints; quasi-linear: one forward-order sweep per ray from its final
  * state (its field samples lie on the straight line, Sec. 2.2).  Both scatter

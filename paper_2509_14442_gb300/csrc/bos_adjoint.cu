@@ -16,6 +16,7 @@
 //                      d deta/dT = -rho0 G T0 / T^2.  A gather, so it is deterministic.
 #include "bos_comp.cuh"
 #include "bos_device.cuh"
+#include "bos_full.cuh"
 #include "bos_internal.h"
 
 namespace bos {
@@ -31,7 +32,6 @@ constexpr int kAdjWarps = kAdjWarpsPerBlock;   // warps per block
 #define BOS_ADJ_QUASI_SMALL_MIN_BLOCKS 1  // the quasi-linear adjoint for few tiles (no register cap)
 #endif
 constexpr int kRow = 36;              // floats per lane row of the cell accumulators (16-byte aligned rows)
-constexpr int kStageStride = 20;      // floats per lane row of a parked stage (value + 3 derivatives, cell, fractions)
 constexpr int kConnDoubles = 20;      // per-lane shared doubles of the refracted connection's adjoint
 constexpr uint32_t kNoKey = 0xffffffffu;
 
@@ -92,30 +92,6 @@ __device__ __forceinline__ void stage_eval(const CompField<E>& F, const long lon
     s.key = cell_key_of(F, ci);
     uint32_t o = cached_offset(bc, ci[0], ci[1], ci[2]);
     s.ig = trilinear_grad2(F.store, o, s.cf[0], s.cf[1], s.cf[2]);
-}
-
-// Park / restore a stage record in the warp's shared buffer: one row of kStageStride = 20
-// floats per lane, accessed as five float4 (a stride of 20 floats puts 8 consecutive
-// lanes on distinct bank quadruples, so the 128-bit accesses are conflict-free).
-__device__ __forceinline__ void put_stage(float* b, int lane, const Stage& s) {
-    float4* row = reinterpret_cast<float4*>(b + lane * kStageStride);
-    row[0] = s.ig.v;
-    row[1] = s.ig.d0;
-    row[2] = s.ig.d1;
-    row[3] = s.ig.d2;
-    row[4] = make_float4(__uint_as_float(s.key), s.cf[0], s.cf[1], s.cf[2]);
-}
-__device__ __forceinline__ void get_stage(const float* b, int lane, Stage& s) {
-    const float4* row = reinterpret_cast<const float4*>(b + lane * kStageStride);
-    s.ig.v = row[0];
-    s.ig.d0 = row[1];
-    s.ig.d1 = row[2];
-    s.ig.d2 = row[3];
-    const float4 a = row[4];
-    s.key = __float_as_uint(a.x);
-    s.cf[0] = a.y;
-    s.cf[1] = a.z;
-    s.cf[2] = a.w;
 }
 
 // Adjoint of D = (1 + deta) grad at a stage point: given Db, the position adjoint (metres)
@@ -242,6 +218,43 @@ __device__ __forceinline__ void accumulate_dual(float* rows, bool act, uint32_t 
     }
 }
 
+// Warp-collective: add w_c(cf) Q and, where with2 / with1, w_c(cf2) Q2 and w_c(cf1) Q1 (other
+// samples in the same cell) to the lane's cell row, in one read and one write of the row.
+__device__ __forceinline__ void accumulate3(float* rows, bool act, uint32_t cell, const float cf[3], float4 Q,
+                                            bool with2, const float cf2[3], float4 Q2, bool with1, const float cf1[3],
+                                            float4 Q1, CellAcc& ca, float* acc, int nx, int nxy) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t key = act ? cell : kNoKey;
+    flush_rows(rows, act && ca.key != kNoKey && ca.key != key, ca, acc, nx, nxy);
+    if (act) {
+        ca.key = key;
+        float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
+        const f32x2 qlo = pack2(Q.x, Q.y), qhi = pack2(Q.z, Q.w);
+        const f32x2 q2lo = pack2(Q2.x, Q2.y), q2hi = pack2(Q2.z, Q2.w);
+        const f32x2 q1lo = pack2(Q1.x, Q1.y), q1hi = pack2(Q1.z, Q1.w);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float w = ((c & 1) ? cf[0] : 1.0f - cf[0]) * ((c & 2) ? cf[1] : 1.0f - cf[1]) *
+                            ((c & 4) ? cf[2] : 1.0f - cf[2]);
+            const float w2 = with2 ? ((c & 1) ? cf2[0] : 1.0f - cf2[0]) * ((c & 2) ? cf2[1] : 1.0f - cf2[1]) *
+                                         ((c & 4) ? cf2[2] : 1.0f - cf2[2])
+                                   : 0.0f;
+            const float w1 = with1 ? ((c & 1) ? cf1[0] : 1.0f - cf1[0]) * ((c & 2) ? cf1[1] : 1.0f - cf1[1]) *
+                                         ((c & 4) ? cf1[2] : 1.0f - cf1[2])
+                                   : 0.0f;
+            float4 r = row[c];
+            f32x2 lo = fma2(pack2(w, w), qlo, pack2(r.x, r.y)), hi = fma2(pack2(w, w), qhi, pack2(r.z, r.w));
+            lo = fma2(pack2(w2, w2), q2lo, lo);
+            hi = fma2(pack2(w2, w2), q2hi, hi);
+            lo = fma2(pack2(w1, w1), q1lo, lo);
+            hi = fma2(pack2(w1, w1), q1hi, hi);
+            unpack2(lo, r.x, r.y);
+            unpack2(hi, r.z, r.w);
+            row[c] = r;
+        }
+    }
+}
+
 // Adjoint of the wall epilogue for seed Ib = dL/dI of this ray: returns the adjoints of
 // (r_N, v_N) and of the path length (which the per-step lengths feed).
 // With the refracted projector connection the luminance is read at xl (not at x_w) and
@@ -310,8 +323,11 @@ __device__ __forceinline__ void straight_aim_adjoint(const SceneDev& S, const Ra
 }
 
 __host__ __device__ constexpr size_t adj_warp_floats(int K) {
-    return (size_t)32 * kRow + 2 * 32 * kStageStride;   // K is carried by the global segment states
+    return (size_t)32 * kRow;   // K is carried by the global segment states
 }
+
+// Floats per lane and step of the recomputed segment: (dr, dv, A, B) of Sharma's step.
+constexpr int kSegFloats = 12;
 
 template <class E, bool CONN_T>
 __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
@@ -332,9 +348,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
     double* const nqp = xlum + 18;
     const int K = ck.every;
     float* rows = reinterpret_cast<float*>(smem4) + (size_t)warp * adj_warp_floats(K);      // [32][kRow]
-    // [K][6][32] step states of the segment being reversed (this warp's slice)
-    float* st_buf = adj.seg + ((size_t)blockIdx.x * kAdjWarps + warp) * ((size_t)K * 6 * 32);
-    float* stg = rows + 32 * kRow;                                                          // [2][32][kStageStride]
+    // [K][12][32] step states and stage terms (dr, dv, A, B) of the segment being reversed
+    // (this warp's slice)
+    float* st_buf = adj.seg + ((size_t)blockIdx.x * kAdjWarps + warp) * ((size_t)K * kSegFloats * 32);
     const CompField<E> F = {static_cast<const E*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
                             {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
     const int nx = S.g.n[0], nxy = S.g.n[0] * S.g.n[1];
@@ -447,13 +463,12 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                     st.excess = 0.0f;
                     for (int a = 0; a < 3; ++a) st.U[a] = st0.U[a] + (long long)n0 * k.dU[a];
                     for (int n = n0; n < n1; ++n) {
-                        float* p = st_buf + (size_t)(n - n0) * 6 * 32 + lane;
+                        float* p = st_buf + (size_t)(n - n0) * kSegFloats * 32 + lane;
                         p[0] = st.dr[0]; p[32] = st.dr[1]; p[64] = st.dr[2];
                         p[96] = st.dv[0]; p[128] = st.dv[1]; p[160] = st.dv[2];
-                        // the state after the segment's last step is needed only at the
-                        // ray's end (the wall adjoint); elsewhere the next checkpoint holds it
-                        if (n + 1 == n1 && c != nseg - 1) break;
-                        comp_step<E, 0>(F, st, k, bc);
+                        float AB[6];
+                        comp_step<E, 0>(F, st, k, bc, AB);
+                        for (int q = 0; q < 6; ++q) p[192 + 32 * q] = AB[q];
                     }
                     if (c == nseg - 1) {
                         // the lane's last segment: start from the adjoint of the wall epilogue
@@ -488,36 +503,21 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                 float tps[3] = {0.0f, 0.0f, 0.0f};   // sum over the segment's stages of (t / dt_step) pb
                 for (int n = n_hi - 1; n >= n0; --n) {
                     const bool a_ = seg && n < n1;
-                    Stage s3;
-                    float A[3] = {0, 0, 0}, B[3] = {0, 0, 0}, dvv[3] = {0, 0, 0}, u[3] = {0, 0, 0};
-                    float dr[3] = {0, 0, 0};
-                    long long U[3], U2[3];
-                    float D1[3] = {0, 0, 0}, D2[3] = {0, 0, 0}, D3[3] = {0, 0, 0};
+                    // the step's state and stage terms from the recompute: all three stage
+                    // points are known, so each stage is evaluated (value and gradient) when
+                    // its adjoint is formed, in the order 3, 2, 1
+                    float dr[3] = {0, 0, 0}, dvv[3] = {0, 0, 0}, A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
                     if (a_) {
-                        // recompute the step's three stages (value and gradient of the field)
-                        const float* p = st_buf + (size_t)(n - n0) * 6 * 32 + lane;
+                        const float* p = st_buf + (size_t)(n - n0) * kSegFloats * 32 + lane;
                         dr[0] = p[0]; dr[1] = p[32]; dr[2] = p[64];
                         dvv[0] = p[96]; dvv[1] = p[128]; dvv[2] = p[160];
-                        long long U3[3];
-                        for (int a = 0; a < 3; ++a) {
-                            U[a] = st0.U[a] + (long long)n * k.dU[a];
-                            U2[a] = U[a] + k.dUh[a];
-                            U3[a] = U[a] + k.dU[a];
-                        }
-                        float q[3];
-                        Stage s;
-                        stage_eval(F, U, dr, bc, s);
-                        rhs_from(s.ig, D1);
-                        put_stage(stg, lane, s);
-                        for (int a = 0; a < 3; ++a) A[a] = dt * D1[a];
-                        for (int a = 0; a < 3; ++a) q[a] = dr[a] + (0.5f * dt) * dvv[a] + (0.125f * dt) * A[a];
-                        stage_eval(F, U2, q, bc, s);
-                        rhs_from(s.ig, D2);
-                        put_stage(stg + 32 * kStageStride, lane, s);
-                        for (int a = 0; a < 3; ++a) B[a] = dt * D2[a];
-                        for (int a = 0; a < 3; ++a) q[a] = dr[a] + dt * dvv[a] + (0.5f * dt) * B[a];
-                        stage_eval(F, U3, q, bc, s3);
-                        rhs_from(s3.ig, D3);
+                        A[0] = p[192]; A[1] = p[224]; A[2] = p[256];
+                        B[0] = p[288]; B[1] = p[320]; B[2] = p[352];
+                    }
+                    long long U[3];
+                    for (int a = 0; a < 3; ++a) U[a] = st0.U[a] + (long long)n * k.dU[a];
+                    float u[3] = {0, 0, 0};
+                    if (a_) {
                         float inc[3], nn = 0.0f;
                         for (int a = 0; a < 3; ++a) {
                             inc[a] = k.dS[a] + dt * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
@@ -539,15 +539,30 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                         vn_[a] = vb[a] + dt * rb[a];
                         dtb += rb[a] * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
                     }
-                    float Db[3], pb[3] = {0, 0, 0};
-                    float4 Q = make_float4(0, 0, 0, 0);
+                    float Db[3], pb[3] = {0, 0, 0}, D[3] = {0, 0, 0}, q[3];
+                    long long Us[3];
+                    Stage s;
+                    float4 Q3 = make_float4(0, 0, 0, 0), Q2 = Q3, Q1 = Q3;
+                    uint32_t key3 = kNoKey, key2 = kNoKey, key1 = kNoKey;
+                    float cf3[3] = {0, 0, 0}, cf2[3] = {0, 0, 0}, cf1[3] = {0, 0, 0};
                     // C = dt D(p3),  p3 = S(n+1) + dr + dt dv + dt/2 B
+                    if (a_) {
+                        for (int a = 0; a < 3; ++a) {
+                            q[a] = dr[a] + dt * dvv[a] + (0.5f * dt) * B[a];
+                            Us[a] = U[a] + k.dU[a];
+                        }
+                        stage_eval(F, Us, q, bc, s);
+                        rhs_from(s.ig, D);
+                    }
                     for (int a = 0; a < 3; ++a) {
-                        dtb += Cb[a] * D3[a];
+                        dtb += Cb[a] * D[a];
                         Db[a] = dt * Cb[a];
                     }
-                    if (a_) rhs_adjoint(F, s3.ig, Db, pb, Q);
-                    accumulate(rows, a_, s3.key, s3.cf, Q, ca, acc, nx, nxy);
+                    if (a_) {
+                        rhs_adjoint(F, s.ig, Db, pb, Q3);
+                        key3 = s.key;
+                        for (int a = 0; a < 3; ++a) cf3[a] = s.cf[a];
+                    }
                     if constexpr (CONN) {
                         const float tn = (float)(n + 1 - n0);
                         for (int a = 0; a < 3; ++a) tps[a] += tn * pb[a];
@@ -559,16 +574,23 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                         dtb += pb[a] * (dvv[a] + 0.5f * B[a]);
                     }
                     // B = dt D(p2),  p2 = S(n+1/2) + dr + dt/2 dv + dt/8 A
+                    if (a_) {
+                        for (int a = 0; a < 3; ++a) {
+                            q[a] = dr[a] + (0.5f * dt) * dvv[a] + (0.125f * dt) * A[a];
+                            Us[a] = U[a] + k.dUh[a];
+                        }
+                        stage_eval(F, Us, q, bc, s);
+                        rhs_from(s.ig, D);
+                    }
                     for (int a = 0; a < 3; ++a) {
-                        dtb += Bb[a] * D2[a];
+                        dtb += Bb[a] * D[a];
                         Db[a] = dt * Bb[a];
                     }
-                    Stage s2;
                     if (a_) {
-                        get_stage(stg + 32 * kStageStride, lane, s2);
-                        rhs_adjoint(F, s2.ig, Db, pb, Q);
+                        rhs_adjoint(F, s.ig, Db, pb, Q2);
+                        key2 = s.key;
+                        for (int a = 0; a < 3; ++a) cf2[a] = s.cf[a];
                     }
-                    accumulate(rows, a_, s2.key, s2.cf, Q, ca, acc, nx, nxy);
                     if constexpr (CONN) {
                         const float tn = (float)(n - n0) + 0.5f;
                         for (int a = 0; a < 3; ++a) tps[a] += tn * pb[a];
@@ -580,16 +602,19 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                         dtb += pb[a] * (0.5f * dvv[a] + 0.125f * A[a]);
                     }
                     // A = dt D(p1),  p1 = S(n) + dr
+                    if (a_) {
+                        stage_eval(F, U, dr, bc, s);
+                        rhs_from(s.ig, D);
+                    }
                     for (int a = 0; a < 3; ++a) {
-                        dtb += Ab[a] * D1[a];
+                        dtb += Ab[a] * D[a];
                         Db[a] = dt * Ab[a];
                     }
-                    Stage s1;
                     if (a_) {
-                        get_stage(stg, lane, s1);
-                        rhs_adjoint(F, s1.ig, Db, pb, Q);
+                        rhs_adjoint(F, s.ig, Db, pb, Q1);
+                        key1 = s.key;
+                        for (int a = 0; a < 3; ++a) cf1[a] = s.cf[a];
                     }
-                    accumulate(rows, a_, s1.key, s1.cf, Q, ca, acc, nx, nxy);
                     if constexpr (CONN) {
                         const float tn = (float)(n - n0);
                         for (int a = 0; a < 3; ++a) tps[a] += tn * pb[a];
@@ -600,6 +625,12 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                             vb[a] = vn_[a];
                         }
                     }
+                    // scatter the three stages: one pass over the lane's cell row for the
+                    // stages in stage 3's cell, then the others (a step that crosses a face)
+                    const bool same2 = key2 == key3, same1 = key1 == key3;
+                    accumulate3(rows, a_, key3, cf3, Q3, same2, cf2, Q2, same1, cf1, Q1, ca, acc, nx, nxy);
+                    accumulate(rows, a_ && !same2, key2, cf2, Q2, ca, acc, nx, nxy);
+                    accumulate(rows, a_ && !same1, key1, cf1, Q1, ca, acc, nx, nxy);
                 }
                 if constexpr (CONN) {
                     if (proj && seg)
@@ -649,349 +680,6 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                 }
             }
             }   // passes
-        }
-    }
-    flush_rows(rows, ca.key != kNoKey, ca, acc, nx, nxy);
-}
-
-// ---- software-pipelined Sharma adjoint (camera rays; light modes 0 and 1) ------------------
-//
-// The arithmetic of adjoint_kernel<E, false>, scheduled so that every warp carries two
-// independent dependency chains: in round c it reverses segment c of its rays (three
-// value-and-gradient evaluations, the adjoint algebra, the corner scatter) while it
-// recomputes segment c - 1 from its checkpoint (the forward Sharma steps whose states round
-// c - 1 reverses).  Source order interleaves the two chains stage by stage, so the gathers
-// of one are in flight while the other computes.  The segment states are double-buffered
-// per warp; the rays' float64 set-up values are parked in shared memory for the rounds.
-
-constexpr int kParkDoubles = 12;   // per lane: d[3], tw, t_in, ell, rin[3], eta_in, Ib, etab
-
-__host__ __device__ constexpr size_t pipe_warp_bytes() {
-    return (size_t)(32 * kRow + 2 * 32 * kStageStride) * sizeof(float) + (size_t)32 * kParkDoubles * sizeof(double);
-}
-
-#ifndef BOS_ADJ_PIPE_MIN_BLOCKS
-#define BOS_ADJ_PIPE_MIN_BLOCKS 5
-#endif
-
-// One forward Sharma step of the recompute (the float32 operations of comp_step, without
-// the path-length excess, which the adjoint reads from the forward's record), split at its
-// stages so that the caller can interleave it with a reverse step.
-struct FwdChain {
-    long long U[3];
-    float dr[3], cr[3], dv[3], cv[3];
-    float A[3], B[3];
-};
-
-template <class E>
-__device__ __forceinline__ float4 fwd_stage(const CompField<E>& F, const long long U[3], const float q[3], BrickCache& bc) {
-    int ci[3];
-    float cf[3];
-    return comp_eval(F, U, q, bc, ci, cf);
-}
-
-template <class E>
-__global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_PIPE_MIN_BLOCKS)
-    adjoint_pipe_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
-    extern __shared__ float4 smem4[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int K = ck.every;
-    unsigned char* wbase = reinterpret_cast<unsigned char*>(smem4) + (size_t)warp * pipe_warp_bytes();
-    float* rows = reinterpret_cast<float*>(wbase);                       // [32][kRow]
-    float* stg = rows + 32 * kRow;                                        // [2][32][kStageStride]
-    double* park = reinterpret_cast<double*>(stg + 2 * 32 * kStageStride) + lane * kParkDoubles;
-    // [2][K][6][32] segment states of this warp (two rounds in flight)
-    float* bufs = adj.seg + ((size_t)blockIdx.x * kAdjWarps + warp) * ((size_t)2 * K * 6 * 32);
-    const CompField<E> F = {static_cast<const E*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
-                            {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
-    const int nx = S.g.n[0], nxy = S.g.n[0] * S.g.n[1];
-    const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
-    const TileShape ts = tile_shape(W, H, spp);
-    const int ntiles = tile_count(S, ts);
-    float* acc = reinterpret_cast<float*>(adj.acc);
-    {
-        float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
-        for (int c = 0; c < 8; ++c) row[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    }
-    __syncwarp();
-    CellAcc ca = {kNoKey};
-
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= ntiles) break;
-        const int sl = lane % ts.G;
-        const TilePix tp = tile_pixel(S, ts, t, lane);
-        for (int qs = 0; qs < ts.samples_per_lane; ++qs) {
-            const int s = ts.samples_per_lane == 1 ? sl : qs;
-            const long long slot = ((long long)t * 32 + lane) * ts.samples_per_lane + qs;
-            int N = 0;
-            float dt = 0.0f;
-            CompState st0;
-            CompConst k;
-            {
-                Ray R;
-                R.N = 0;
-                R.wall = false;
-                double Ib = 0.0, eta_in = 1.0, rin[3] = {0.0, 0.0, 0.0};
-                if (tp.valid) {
-                    R = ray_setup(S, tp.px, tp.py, s);
-                    Ib = (double)adj.dLdI[(size_t)tp.out] / spp;
-                }
-                const bool act = tp.valid && R.wall && R.N > 0 && Ib != 0.0;
-                for (int a = 0; a < 3; ++a) {
-                    st0.U[a] = 0;
-                    k.dU[a] = k.dUh[a] = 0;
-                    k.dS[a] = k.dhat[a] = 0.0f;
-                }
-                k.dt = k.step_len = 0.0f;
-                if (act) {
-                    comp_setup(S, F, S.cam.pos, R, st0, k, eta_in, rin);
-                    N = R.N;
-                    dt = k.dt;
-                }
-                for (int a = 0; a < 3; ++a) {
-                    park[a] = R.d[a];
-                    park[6 + a] = rin[a];
-                }
-                park[3] = R.tw;
-                park[4] = R.t_in;
-                park[5] = R.ell;
-                park[9] = eta_in;
-                park[10] = Ib;
-                park[11] = 0.0;                 // etab
-            }
-            const int nseg = (N + K - 1) / K;
-            const int nseg_max = __reduce_max_sync(0xffffffffu, (unsigned)nseg);
-            float rb[3] = {0, 0, 0}, vb[3] = {0, 0, 0}, dtb = 0.0f, lenb = 0.0f;
-            FwdChain fc;
-            for (int a = 0; a < 3; ++a) {
-                fc.U[a] = 0;
-                fc.dr[a] = fc.cr[a] = fc.dv[a] = fc.cv[a] = fc.A[a] = fc.B[a] = 0.0f;
-            }
-            BrickCache bcf = {kNoKey, 0u}, bcr = {kNoKey, 0u};
-            for (int c = nseg_max; c >= 0; --c) {
-                const int f = c - 1;                        // segment recomputed this round
-                const bool has_fwd = f >= 0;                // warp-uniform
-                const bool has_rev = c < nseg_max;          // warp-uniform
-                // forward chain: segment f of this lane, states stored for j < fstore, steps for j < fsteps
-                int fstore = 0, fsteps = 0;
-                if (has_fwd && f < nseg) {
-                    const int fn0 = f * K, fn1 = min(fn0 + K, N);
-                    fstore = fn1 - fn0;
-                    fsteps = f == nseg - 1 ? fstore : fstore - 1;   // the last state is the next checkpoint
-                    const float4 s0 = ck.state[((size_t)f * 3 + 0) * ck.nrays + slot];
-                    const float4 s1 = ck.state[((size_t)f * 3 + 1) * ck.nrays + slot];
-                    const float4 s2 = ck.state[((size_t)f * 3 + 2) * ck.nrays + slot];
-                    fc.dr[0] = s0.x; fc.dr[1] = s0.y; fc.dr[2] = s0.z;
-                    fc.dv[0] = s1.x; fc.dv[1] = s1.y; fc.dv[2] = s1.z;
-                    fc.cv[0] = s2.x; fc.cv[1] = s2.y; fc.cv[2] = s2.z;
-                    fc.cr[0] = s0.w; fc.cr[1] = s1.w; fc.cr[2] = s2.w;
-                    for (int a = 0; a < 3; ++a) fc.U[a] = st0.U[a] + (long long)fn0 * k.dU[a];
-                }
-                // reverse chain: segment c of this lane, local step K-1-j active while < rlen
-                int rlen = 0;
-                long long Ur[3];
-                if (has_rev && c < nseg) rlen = min(c * K + K, N) - c * K;
-                for (int a = 0; a < 3; ++a) Ur[a] = st0.U[a] + (long long)(c * K + K - 1) * k.dU[a];
-                float* fbuf = bufs + (size_t)(f & 1) * K * 6 * 32 + lane;
-                const float* rbuf = bufs + (size_t)(c & 1) * K * 6 * 32 + lane;
-                for (int j = 0; j < K; ++j) {
-                    // ================= forward: store the state, stage 1
-                    const bool fa = has_fwd && j < fsteps;
-                    float vf1[3];
-                    float4 ef;
-                    if (has_fwd) {
-                        if (j < fstore) {
-                            float* p = fbuf + (size_t)j * 6 * 32;
-                            p[0] = fc.dr[0]; p[32] = fc.dr[1]; p[64] = fc.dr[2];
-                            p[96] = fc.dv[0]; p[128] = fc.dv[1]; p[160] = fc.dv[2];
-                        }
-                        ef = fwd_stage(F, fc.U, fc.dr, bcf);
-                    }
-                    // ================= reverse: load the state, stage 1
-                    const int rl = K - 1 - j;
-                    const bool ra = has_rev && rl < rlen;
-                    float dr[3] = {0, 0, 0}, dvv[3] = {0, 0, 0};
-                    Stage s;
-                    float D1[3] = {0, 0, 0}, D2[3] = {0, 0, 0}, D3[3] = {0, 0, 0}, A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
-                    long long U2[3], U3[3];
-                    if (has_rev) {
-                        if (ra) {
-                            const float* p = rbuf + (size_t)rl * 6 * 32;
-                            dr[0] = p[0]; dr[1] = p[32]; dr[2] = p[64];
-                            dvv[0] = p[96]; dvv[1] = p[128]; dvv[2] = p[160];
-                        }
-                        for (int a = 0; a < 3; ++a) {
-                            U2[a] = Ur[a] + k.dUh[a];
-                            U3[a] = Ur[a] + k.dU[a];
-                        }
-                        stage_eval(F, Ur, dr, bcr, s);
-                    }
-                    // ================= forward stage 2
-                    if (has_fwd) {
-                        rhs_of(ef, vf1);
-                        float q[3];
-                        long long Uf2[3];
-                        for (int a = 0; a < 3; ++a) {
-                            fc.A[a] = dt * vf1[a];
-                            q[a] = fc.dr[a] + (0.5f * dt) * fc.dv[a] + (0.125f * dt) * fc.A[a];
-                            Uf2[a] = fc.U[a] + k.dUh[a];
-                        }
-                        ef = fwd_stage(F, Uf2, q, bcf);
-                    }
-                    // ================= reverse stage 2
-                    if (has_rev) {
-                        rhs_from(s.ig, D1);
-                        put_stage(stg, lane, s);
-                        float q[3];
-                        for (int a = 0; a < 3; ++a) A[a] = dt * D1[a];
-                        for (int a = 0; a < 3; ++a) q[a] = dr[a] + (0.5f * dt) * dvv[a] + (0.125f * dt) * A[a];
-                        stage_eval(F, U2, q, bcr, s);
-                    }
-                    // ================= forward stage 3
-                    if (has_fwd) {
-                        float D[3], q[3];
-                        long long Uf3[3];
-                        rhs_of(ef, D);
-                        for (int a = 0; a < 3; ++a) {
-                            fc.B[a] = dt * D[a];
-                            q[a] = fc.dr[a] + dt * fc.dv[a] + (0.5f * dt) * fc.B[a];
-                            Uf3[a] = fc.U[a] + k.dU[a];
-                        }
-                        ef = fwd_stage(F, Uf3, q, bcf);
-                    }
-                    // ================= reverse stage 3
-                    if (has_rev) {
-                        rhs_from(s.ig, D2);
-                        put_stage(stg + 32 * kStageStride, lane, s);
-                        float q[3];
-                        for (int a = 0; a < 3; ++a) B[a] = dt * D2[a];
-                        for (int a = 0; a < 3; ++a) q[a] = dr[a] + dt * dvv[a] + (0.5f * dt) * B[a];
-                        stage_eval(F, U3, q, bcr, s);
-                        rhs_from(s.ig, D3);
-                    }
-                    // ================= forward update
-                    if (has_fwd) {
-                        float D[3];
-                        rhs_of(ef, D);
-                        for (int a = 0; a < 3; ++a) {
-                            const float C = dt * D[a];
-                            const float inc_r = dt * (fc.dv[a] + (fc.A[a] + 2.0f * fc.B[a]) * (1.0f / 6.0f));
-                            const float inc_v = (fc.A[a] + 4.0f * fc.B[a] + C) * (1.0f / 6.0f);
-                            float dr1 = fc.dr[a], cr1 = fc.cr[a], dv1 = fc.dv[a], cv1 = fc.cv[a];
-                            kahan_add(dr1, cr1, inc_r);
-                            kahan_add(dv1, cv1, inc_v);
-                            if (fa) {
-                                fc.dr[a] = dr1;
-                                fc.cr[a] = cr1;
-                                fc.dv[a] = dv1;
-                                fc.cv[a] = cv1;
-                                fc.U[a] += k.dU[a];
-                            }
-                        }
-                    }
-                    if (!has_rev) continue;
-                    // ================= reverse: adjoint of the step (as in adjoint_kernel)
-                    float u[3] = {0, 0, 0};
-                    {
-                        float inc[3], nn = 0.0f;
-                        for (int a = 0; a < 3; ++a) {
-                            inc[a] = k.dS[a] + dt * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
-                            nn += inc[a] * inc[a];
-                        }
-                        const float rn = rsqrtf(nn);
-                        for (int a = 0; a < 3; ++a) u[a] = ra ? inc[a] * rn : 0.0f;
-                    }
-                    float rbs[3];
-                    for (int a = 0; a < 3; ++a) rbs[a] = rb[a] + lenb * u[a];
-                    float Ab[3], Bb[3], Cb[3], rn_[3], vn_[3], dtb_s = 0.0f;
-                    for (int a = 0; a < 3; ++a) {
-                        Ab[a] = (dt * (1.0f / 6.0f)) * rbs[a] + vb[a] * (1.0f / 6.0f);
-                        Bb[a] = (dt * (1.0f / 3.0f)) * rbs[a] + vb[a] * (4.0f / 6.0f);
-                        Cb[a] = vb[a] * (1.0f / 6.0f);
-                        rn_[a] = rbs[a];
-                        vn_[a] = vb[a] + dt * rbs[a];
-                        dtb_s += rbs[a] * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
-                    }
-                    float Db[3], pb[3];
-                    float4 Q;
-                    for (int a = 0; a < 3; ++a) {
-                        dtb_s += Cb[a] * D3[a];
-                        Db[a] = dt * Cb[a];
-                    }
-                    rhs_adjoint(F, s.ig, Db, pb, Q);
-                    accumulate(rows, ra, s.key, s.cf, Q, ca, acc, nx, nxy);
-                    for (int a = 0; a < 3; ++a) {
-                        rn_[a] += pb[a];
-                        vn_[a] += dt * pb[a];
-                        Bb[a] += (0.5f * dt) * pb[a];
-                        dtb_s += pb[a] * (dvv[a] + 0.5f * B[a]);
-                    }
-                    for (int a = 0; a < 3; ++a) {
-                        dtb_s += Bb[a] * D2[a];
-                        Db[a] = dt * Bb[a];
-                    }
-                    get_stage(stg + 32 * kStageStride, lane, s);
-                    rhs_adjoint(F, s.ig, Db, pb, Q);
-                    accumulate(rows, ra, s.key, s.cf, Q, ca, acc, nx, nxy);
-                    for (int a = 0; a < 3; ++a) {
-                        rn_[a] += pb[a];
-                        vn_[a] += (0.5f * dt) * pb[a];
-                        Ab[a] += (0.125f * dt) * pb[a];
-                        dtb_s += pb[a] * (0.5f * dvv[a] + 0.125f * A[a]);
-                    }
-                    for (int a = 0; a < 3; ++a) {
-                        dtb_s += Ab[a] * D1[a];
-                        Db[a] = dt * Ab[a];
-                    }
-                    get_stage(stg, lane, s);
-                    rhs_adjoint(F, s.ig, Db, pb, Q);
-                    accumulate(rows, ra, s.key, s.cf, Q, ca, acc, nx, nxy);
-                    if (ra) {
-                        for (int a = 0; a < 3; ++a) {
-                            rb[a] = rn_[a] + pb[a] - lenb * u[a];
-                            vb[a] = vn_[a];
-                        }
-                        dtb += dtb_s;
-                    }
-                    for (int a = 0; a < 3; ++a) Ur[a] -= k.dU[a];
-                }
-                // lanes whose last segment was recomputed this round: adjoint of the wall epilogue
-                if (has_fwd && f == nseg - 1 && N > 0) {
-                    double d[3], rin[3], rN[3], vN[3], drb[3], dvb[3], lb = 0.0;
-                    for (int a = 0; a < 3; ++a) {
-                        d[a] = park[a];
-                        rin[a] = park[6 + a];
-                    }
-                    const double ell = park[5], eta_in = park[9];
-                    for (int a = 0; a < 3; ++a) {
-                        rN[a] = rin[a] + ell * d[a] + ((double)fc.dr[a] - (double)fc.cr[a]);
-                        vN[a] = eta_in * d[a] + ((double)fc.dv[a] - (double)fc.cv[a]);
-                    }
-                    const double len_before = park[4] + ell + (double)ck.excess[slot];
-                    wall_adjoint(S, rN, vN, len_before, park[10], drb, dvb, lb);
-                    for (int a = 0; a < 3; ++a) {
-                        rb[a] = (float)drb[a];
-                        vb[a] = (float)dvb[a];
-                    }
-                    lenb = (float)lb;
-                    park[11] = dvb[0] * d[0] + dvb[1] * d[1] + dvb[2] * d[2];
-                }
-                __syncwarp();
-            }
-            // ---- entry: v0 = eta_in d and dt = ell / (N eta_in), eta_in = 1 + deta(r_in)
-            int ci[3] = {0, 0, 0};
-            float cf[3] = {0, 0, 0};
-            double etab = 0.0;
-            const bool act = N > 0;
-            if (act) {
-                etab = park[11] - (double)dtb * (double)dt / park[9];
-                const float zero[3] = {0, 0, 0};
-                comp_cell(F, st0.U, zero, ci, cf);
-            }
-            accumulate(rows, act, cell_key_of(F, ci), cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), ca, acc, nx, nxy);
         }
     }
     flush_rows(rows, ca.key != kNoKey, ca, acc, nx, nxy);
@@ -1182,29 +870,283 @@ __global__ void __launch_bounds__(kAdjWarps * 32, MINB)
     flush_rows(rows, ca.key != kNoKey, ca, acc, nx, nxy);
 }
 
+// ---- float64 adjoint (FP64 store and tracer, Sharma RKN) -------------------------------------
+//
+// The same discrete adjoint in float64 throughout, for the plain float64 tracer: the state
+// is the absolute (r, v), kept every K steps by the forward render (six doubles); each
+// segment is recomputed into this warp's slice of global memory and reversed; every stage's
+// corner sensitivities go to float64 node accumulators.  GB300 runs float64 at 1/64 of the
+// float32 rate, so this path is for accuracy, not speed: it separates the method's own error
+// from float32 rounding.
+
+struct D4Grad {
+    D4 v, d0, d1, d2;   // value and derivatives with respect to the three fractions
+};
+
+__device__ __forceinline__ D4 dsub4(D4 a, D4 b) {
+    D4 r;
+    r.x = a.x - b.x;
+    r.y = a.y - b.y;
+    r.z = a.z - b.z;
+    r.w = a.w - b.w;
+    return r;
+}
+
+// Value (the operations of trilinear_d, so bit-identical) and fraction derivatives.
+__device__ __forceinline__ D4Grad trilinear_grad_d(const D4* s, uint32_t o, double f0, double f1, double f2) {
+    const D4 c000 = load_d4(s, o), c100 = load_d4(s, o + 1), c010 = load_d4(s, o + 9), c110 = load_d4(s, o + 10);
+    const D4 c001 = load_d4(s, o + 81), c101 = load_d4(s, o + 82), c011 = load_d4(s, o + 90), c111 = load_d4(s, o + 91);
+    const D4 a0 = dlerp(c000, c100, f0), a1 = dlerp(c010, c110, f0), a2 = dlerp(c001, c101, f0),
+             a3 = dlerp(c011, c111, f0);
+    const D4 b0 = dlerp(a0, a1, f1), b1 = dlerp(a2, a3, f1);
+    D4Grad r;
+    r.v = dlerp(b0, b1, f2);
+    r.d2 = dsub4(b1, b0);
+    r.d1 = dlerp(dsub4(a1, a0), dsub4(a3, a2), f2);
+    r.d0 = dlerp(dlerp(dsub4(c100, c000), dsub4(c110, c010), f1), dlerp(dsub4(c101, c001), dsub4(c111, c011), f1), f2);
+    return r;
+}
+
+struct DStage {
+    int i[3];       // base cell
+    double f[3];    // fractions (unclamped at the edge cells)
+    D4Grad g;
+};
+
+// Field value and gradient at absolute position x: the cell and fractions of field_at.
+__device__ __forceinline__ void dstage_eval(const GridDev& g, const double x[3], DStage& s) {
+    for (int a = 0; a < 3; ++a) {
+        const double u = (x[a] - g.origin[a]) / g.h[a] - 0.5;
+        split_coord(u, g.n[a], s.i[a], s.f[a]);
+    }
+    s.g = trilinear_grad_d(static_cast<const D4*>(g.store), brick_offset(s.i[0], s.i[1], s.i[2]), s.f[0], s.f[1],
+                           s.f[2]);
+}
+
+__device__ __forceinline__ void drhs(const DStage& s, double D[3]) {
+    const double eta = 1.0 + s.g.v.x;
+    D[0] = eta * s.g.v.y;
+    D[1] = eta * s.g.v.z;
+    D[2] = eta * s.g.v.w;
+}
+
+// Adjoint of D = (1 + deta) grad at a stage for Db: the position adjoint pb, and the
+// record adjoint Q scattered to the 8 corners with the trilinear weights.
+__device__ __forceinline__ void drhs_adjoint_scatter(const GridDev& g, const DStage& s, const double Db[3], double pb[3],
+                                                     double* acc, bool act) {
+    const double eta = 1.0 + s.g.v.x;
+    const double Dg = Db[0] * s.g.v.y + Db[1] * s.g.v.z + Db[2] * s.g.v.w;
+    const D4 dv[3] = {s.g.d0, s.g.d1, s.g.d2};
+    for (int a = 0; a < 3; ++a)
+        pb[a] = g.inv_h[a] * (dv[a].x * Dg + eta * (Db[0] * dv[a].y + Db[1] * dv[a].z + Db[2] * dv[a].w));
+    if (!act) return;
+    const double Q[4] = {Dg, eta * Db[0], eta * Db[1], eta * Db[2]};
+    const size_t nx = (size_t)g.n[0], nxy = (size_t)g.n[0] * g.n[1];
+    const size_t base = (size_t)s.i[0] + (size_t)s.i[1] * nx + (size_t)s.i[2] * nxy;
+    for (int c = 0; c < 8; ++c) {
+        const double w = ((c & 1) ? s.f[0] : 1.0 - s.f[0]) * ((c & 2) ? s.f[1] : 1.0 - s.f[1]) *
+                         ((c & 4) ? s.f[2] : 1.0 - s.f[2]);
+        const size_t node = base + (size_t)(c & 1) + (size_t)((c >> 1) & 1) * nx + (size_t)(c >> 2) * nxy;
+        for (int ch = 0; ch < 4; ++ch) atomicAdd(acc + node * 4 + ch, w * Q[ch]);
+    }
+}
+
+__global__ void __launch_bounds__(kAdjWarps * 32) adjoint_fp64_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int K = ck.every;
+    // [K][6][32] step states (r, v) of the segment being reversed (this warp's slice)
+    double* buf = reinterpret_cast<double*>(adj.seg) + ((size_t)blockIdx.x * kAdjWarps + warp) * ((size_t)K * 6 * 32);
+    const double* ckd = reinterpret_cast<const double*>(ck.state);
+    double* acc = reinterpret_cast<double*>(adj.acc);
+    const GridDev& g = S.g;
+    const FullField<double> F = {S.g};
+    const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
+    const TileShape ts = tile_shape(W, H, spp);
+    const int ntiles = tile_count(S, ts);
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntiles) break;
+        const int sl = lane % ts.G;
+        const TilePix tp = tile_pixel(S, ts, t, lane);
+        for (int qs = 0; qs < ts.samples_per_lane; ++qs) {
+            const int s = ts.samples_per_lane == 1 ? sl : qs;
+            const long long slot = ((long long)t * 32 + lane) * ts.samples_per_lane + qs;
+            Ray R;
+            R.N = 0;
+            R.wall = false;
+            double Ib = 0.0;
+            if (tp.valid) {
+                R = ray_setup(S, tp.px, tp.py, s);
+                Ib = (double)adj.dLdI[(size_t)tp.out] / spp;
+            }
+            const bool act = tp.valid && R.wall && R.N > 0 && Ib != 0.0;
+            // entry state as the forward forms it: r_in, eta_in, v0 = eta_in d, dt = ell / (N eta_in)
+            double rin[3] = {0.0, 0.0, 0.0}, eta_in = 1.0, dt = 0.0;
+            if (act) {
+                for (int a = 0; a < 3; ++a) rin[a] = S.cam.pos[a] + R.t_in * R.d[a];
+                eta_in = F.eta(rin);
+                dt = R.ell / ((double)R.N * eta_in);
+            }
+            const int N = act ? R.N : 0;
+            const int nseg = (N + K - 1) / K;
+            const int nseg_max = __reduce_max_sync(0xffffffffu, (unsigned)nseg);
+            double rb[3] = {0, 0, 0}, vb[3] = {0, 0, 0}, dtb = 0.0, lenb = 0.0;
+            for (int c = nseg_max - 1; c >= 0; --c) {
+                const int n0 = c * K, n1 = min(n0 + K, N);
+                const bool seg = act && n0 < N;
+                if (seg) {
+                    // ---- recompute the segment from its checkpoint (full_step's operations)
+                    double r[3], v[3];
+                    for (int q = 0; q < 3; ++q) {
+                        r[q] = ckd[((size_t)c * 6 + q) * ck.nrays + slot];
+                        v[q] = ckd[((size_t)c * 6 + 3 + q) * ck.nrays + slot];
+                    }
+                    for (int n = n0; n < n1; ++n) {
+                        double* p = buf + (size_t)(n - n0) * 6 * 32 + lane;
+                        for (int q = 0; q < 3; ++q) {
+                            p[32 * q] = r[q];
+                            p[32 * (3 + q)] = v[q];
+                        }
+                        full_step<double, 0>(F, r, v, dt);
+                    }
+                    if (c == nseg - 1) {
+                        double lb = 0.0;
+                        const double len_before = R.t_in + reinterpret_cast<const double*>(ck.excess)[slot];
+                        wall_adjoint(S, r, v, len_before, Ib, rb, vb, lb);
+                        lenb = lb;
+                    }
+                }
+                __syncwarp();
+                // ---- reverse the segment's steps
+                const int n_hi = __reduce_max_sync(0xffffffffu, (unsigned)(seg ? n1 : 0));
+                for (int n = n_hi - 1; n >= n0; --n) {
+                    const bool a_ = seg && n < n1;
+                    if (!a_) continue;
+                    const double* p = buf + (size_t)(n - n0) * 6 * 32 + lane;
+                    double r[3], v[3], A[3], B[3], D1[3], D2[3], D3[3], q[3];
+                    for (int a = 0; a < 3; ++a) {
+                        r[a] = p[32 * a];
+                        v[a] = p[32 * (3 + a)];
+                    }
+                    DStage s1, s2, s3;
+                    dstage_eval(g, r, s1);
+                    drhs(s1, D1);
+                    for (int a = 0; a < 3; ++a) A[a] = dt * D1[a];
+                    for (int a = 0; a < 3; ++a) q[a] = r[a] + (dt * 0.5) * v[a] + (dt * 0.125) * A[a];
+                    dstage_eval(g, q, s2);
+                    drhs(s2, D2);
+                    for (int a = 0; a < 3; ++a) B[a] = dt * D2[a];
+                    for (int a = 0; a < 3; ++a) q[a] = r[a] + dt * v[a] + (dt * 0.5) * B[a];
+                    dstage_eval(g, q, s3);
+                    drhs(s3, D3);
+                    // r' = r + dt (v + (A + 2B)/6), |r' - r| enters the path length
+                    double inc[3], nn = 0.0, u[3];
+                    for (int a = 0; a < 3; ++a) {
+                        inc[a] = dt * (v[a] + (A[a] + 2.0 * B[a]) / 6.0);
+                        nn += inc[a] * inc[a];
+                    }
+                    const double rn = 1.0 / sqrt(nn);
+                    double rbs[3], Ab[3], Bb[3], Cb[3], rn_[3], vn_[3], Db[3], pb[3];
+                    for (int a = 0; a < 3; ++a) {
+                        u[a] = inc[a] * rn;
+                        rbs[a] = rb[a] + lenb * u[a];
+                    }
+                    for (int a = 0; a < 3; ++a) {
+                        Ab[a] = (dt / 6.0) * rbs[a] + vb[a] / 6.0;
+                        Bb[a] = (dt / 3.0) * rbs[a] + vb[a] * (4.0 / 6.0);
+                        Cb[a] = vb[a] / 6.0;
+                        rn_[a] = rbs[a];
+                        vn_[a] = vb[a] + dt * rbs[a];
+                        dtb += rbs[a] * (v[a] + (A[a] + 2.0 * B[a]) / 6.0);
+                    }
+                    // C = dt D(p3), p3 = r + dt v + dt/2 B
+                    for (int a = 0; a < 3; ++a) {
+                        dtb += Cb[a] * D3[a];
+                        Db[a] = dt * Cb[a];
+                    }
+                    drhs_adjoint_scatter(g, s3, Db, pb, acc, true);
+                    for (int a = 0; a < 3; ++a) {
+                        rn_[a] += pb[a];
+                        vn_[a] += dt * pb[a];
+                        Bb[a] += (0.5 * dt) * pb[a];
+                        dtb += pb[a] * (v[a] + 0.5 * B[a]);
+                    }
+                    // B = dt D(p2), p2 = r + dt/2 v + dt/8 A
+                    for (int a = 0; a < 3; ++a) {
+                        dtb += Bb[a] * D2[a];
+                        Db[a] = dt * Bb[a];
+                    }
+                    drhs_adjoint_scatter(g, s2, Db, pb, acc, true);
+                    for (int a = 0; a < 3; ++a) {
+                        rn_[a] += pb[a];
+                        vn_[a] += (0.5 * dt) * pb[a];
+                        Ab[a] += (0.125 * dt) * pb[a];
+                        dtb += pb[a] * (0.5 * v[a] + 0.125 * A[a]);
+                    }
+                    // A = dt D(p1), p1 = r
+                    for (int a = 0; a < 3; ++a) {
+                        dtb += Ab[a] * D1[a];
+                        Db[a] = dt * Ab[a];
+                    }
+                    drhs_adjoint_scatter(g, s1, Db, pb, acc, true);
+                    for (int a = 0; a < 3; ++a) {
+                        rb[a] = rn_[a] + pb[a] - lenb * u[a];
+                        vb[a] = vn_[a];
+                    }
+                }
+                __syncwarp();
+            }
+            // ---- entry: v0 = eta_in d, dt = ell / (N eta_in), eta_in = 1 + deta(r_in)
+            if (act) {
+                const double etab = vb[0] * R.d[0] + vb[1] * R.d[1] + vb[2] * R.d[2] - dtb * dt / eta_in;
+                DStage se;
+                dstage_eval(g, rin, se);
+                const size_t nx = (size_t)g.n[0], nxy = (size_t)g.n[0] * g.n[1];
+                const size_t base = (size_t)se.i[0] + (size_t)se.i[1] * nx + (size_t)se.i[2] * nxy;
+                for (int c = 0; c < 8; ++c) {
+                    const double w = ((c & 1) ? se.f[0] : 1.0 - se.f[0]) * ((c & 2) ? se.f[1] : 1.0 - se.f[1]) *
+                                     ((c & 4) ? se.f[2] : 1.0 - se.f[2]);
+                    const size_t node = base + (size_t)(c & 1) + (size_t)((c >> 1) & 1) * nx + (size_t)(c >> 2) * nxy;
+                    atomicAdd(acc + node * 4, w * etab);
+                }
+            }
+        }
+    }
+}
+
 // dL/dT per node: transpose of the difference stencil of grad eta, plus d L/d deta, times
 // d deta/dT = -K / T^2.
-__global__ void gradient_kernel(GridDev g, const float4* __restrict__ acc, const float* __restrict__ T,
+__device__ __forceinline__ double acc_channel(const float4* acc, long long m, int ch) {
+    const float4 v = acc[m];
+    return (double)(ch == 0 ? v.x : ch == 1 ? v.y : ch == 2 ? v.z : v.w);
+}
+__device__ __forceinline__ double acc_channel(const double* acc, long long m, int ch) { return acc[m * 4 + ch]; }
+
+template <class A>
+__global__ void gradient_kernel(GridDev g, const A* __restrict__ acc, const float* __restrict__ T,
                                 float* __restrict__ dLdT) {
     const long long n = (long long)g.n[0] * g.n[1] * g.n[2];
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int idx[3] = {(int)(c % g.n[0]), (int)((c / g.n[0]) % g.n[1]), (int)(c / ((long long)g.n[0] * g.n[1]))};
         const long long stride[3] = {1, g.n[0], (long long)g.n[0] * g.n[1]};
-        double tot = (double)acc[c].x;
+        double tot = acc_channel(acc, c, 0);
         for (int a = 0; a < 3; ++a) {
             const int i = idx[a], na = g.n[a];
             const double ih = g.inv_h[a], ih2 = 0.5 * g.inv_h[a];
-            auto gch = [&](long long m) {
-                float4 v = acc[m];
-                return (double)(a == 0 ? v.y : a == 1 ? v.z : v.w);
-            };
-            if (i - 1 >= 0) tot += gch(c - stride[a]) * (i - 1 == 0 ? ih : ih2);        // node i-1 reads i as hi
-            if (i + 1 <= na - 1) tot -= gch(c + stride[a]) * (i + 1 == na - 1 ? ih : ih2);  // node i+1 reads i as lo
-            if (i == 0) tot -= gch(c) * ih;                                             // one-sided at the faces
-            if (i == na - 1) tot += gch(c) * ih;
+            if (i - 1 >= 0) tot += acc_channel(acc, c - stride[a], 1 + a) * (i - 1 == 0 ? ih : ih2);        // node i-1 reads i as hi
+            if (i + 1 <= na - 1) tot -= acc_channel(acc, c + stride[a], 1 + a) * (i + 1 == na - 1 ? ih : ih2);  // node i+1 reads i as lo
+            if (i == 0) tot -= acc_channel(acc, c, 1 + a) * ih;                                             // one-sided at the faces
+            if (i == na - 1) tot += acc_channel(acc, c, 1 + a) * ih;
         }
-        const float Tc = T[c];
-        dLdT[c] = (float)tot * (-(float)g.K / (Tc * Tc));
+        if constexpr (sizeof(A) == 8) {
+            const double Tc = (double)T[c];
+            dLdT[c] = (float)(tot * (-g.K / (Tc * Tc)));
+        } else {
+            const float Tc = T[c];
+            dLdT[c] = (float)tot * (-(float)g.K / (Tc * Tc));
+        }
     }
 }
 
@@ -1224,28 +1166,8 @@ static cudaError_t launch_adjoint_c(const SceneDev& S, const CkptDev& ck, const 
     return cudaGetLastError();
 }
 
-template <class E>
-static cudaError_t launch_adjoint_pipe(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
-                                      int num_sms, cudaStream_t st) {
-    size_t smem = (size_t)kAdjWarps * pipe_warp_bytes();
-    cudaError_t e = cudaFuncSetAttribute(adjoint_pipe_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_pipe_kernel<E>, kAdjWarps * 32, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1 || adj.seg == nullptr) return cudaErrorInvalidConfiguration;
-    const int blocks = num_sms * per_sm < kAdjMaxBlocks ? num_sms * per_sm : kAdjMaxBlocks;
-    adjoint_pipe_kernel<E><<<blocks, kAdjWarps * 32, smem, st>>>(S, ck, adj, w);
-    return cudaGetLastError();
-}
-
-#ifndef BOS_ADJ_PIPELINE
-#define BOS_ADJ_PIPELINE 1
-#endif
-
 // The refracted projector connection (light mode 2) reverses each sample's projector ray
-// too; it has its own instantiation so that the other modes do not carry it.  The other
-// modes take the software-pipelined kernel.
+// too; it has its own instantiation so that the other modes do not carry it.
 template <class E>
 static cudaError_t launch_adjoint_t(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
                                     int num_sms, cudaStream_t st) {
@@ -1253,7 +1175,6 @@ static cudaError_t launch_adjoint_t(const SceneDev& S, const CkptDev& ck, const 
         if (ck.pstate == nullptr || ck.conn == nullptr) return cudaErrorInvalidValue;
         return launch_adjoint_c<E, true>(S, ck, adj, w, num_sms, st);
     }
-    if (BOS_ADJ_PIPELINE) return launch_adjoint_pipe<E>(S, ck, adj, w, num_sms, st);
     return launch_adjoint_c<E, false>(S, ck, adj, w, num_sms, st);
 }
 
@@ -1287,13 +1208,22 @@ cudaError_t launch_backward(int mode, const SceneDev& S, const CkptDev& ck, cons
     const bool quasi = S.it.integrator == 2;
     if (!quasi && ck.every > 64) return cudaErrorNotSupported;
     cudaError_t e;
+    if (mode == 4) {   // float64 store and tracer: Sharma RKN, float64 accumulators
+        if (S.it.integrator != 0 || S.L.mode == 2 || adj.seg == nullptr) return cudaErrorNotSupported;
+        adjoint_fp64_kernel<<<num_sms * 8 < kAdjMaxBlocks ? num_sms * 8 : kAdjMaxBlocks, kAdjWarps * 32, 0, st>>>(
+            S, ck, adj, w);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        gradient_kernel<double><<<num_sms * 8, 256, 0, st>>>(S.g, reinterpret_cast<const double*>(adj.acc), T, dLdT);
+        return cudaGetLastError();
+    }
     if (mode == 1) e = quasi ? launch_adjoint_quasi_t<F4P>(S, ck, adj, w, num_sms, st)
                              : launch_adjoint_t<F4P>(S, ck, adj, w, num_sms, st);
     else if (mode == 2) e = quasi ? launch_adjoint_quasi_t<B4P>(S, ck, adj, w, num_sms, st)
                                   : launch_adjoint_t<B4P>(S, ck, adj, w, num_sms, st);
     else return cudaErrorNotSupported;
     if (e != cudaSuccess) return e;
-    gradient_kernel<<<num_sms * 8, 256, 0, st>>>(S.g, adj.acc, T, dLdT);
+    gradient_kernel<float4><<<num_sms * 8, 256, 0, st>>>(S.g, adj.acc, T, dLdT);
     return cudaGetLastError();
 }
 

@@ -343,12 +343,12 @@ size_t request_bytes(const bos_grid_desc& g, const bos_camera_desc& cam, const b
         }
         size_t max_ckpt = it.integrator == 2 ? 1 : (size_t)((bound + it.ckpt_every - 1) / it.ckpt_every);
         bytes += align_up(max_ckpt * 3 * nslots * sizeof(float4));
-        bytes += align_up(nslots * sizeof(float));
+        bytes += align_up(nslots * (g.prec == BOS_PREC_FP64 ? 8 : 4));
         if (light.mode == 2) {   // the projector rays' checkpoints and the connection records
             bytes += align_up(max_ckpt * 3 * nslots * sizeof(float4));
             bytes += align_up(2 * nslots * sizeof(float4));
         }
-        bytes += align_up((size_t)g.nx * g.ny * g.nz * sizeof(float4));
+        bytes += align_up((size_t)g.nx * g.ny * g.nz * (g.prec == BOS_PREC_FP64 ? 32 : 16));
         if (it.integrator != 2) bytes += align_up(adjoint_segment_bytes(it.ckpt_every));
     }
     return bytes;
@@ -506,16 +506,20 @@ static bos_status_t render_impl(bos_ctx* c, int mode, float* I, float* disp, dou
         ck.nrays = tiles * 32 * ts.samples_per_lane;
     }
     if (save) {
-        if (mode != 1 && mode != 2)
-            return fail(BOS_ERR_UNIMPLEMENTED, "bos_render: save_for_backward needs FP32_COMP or BF16_COMP");
+        if (mode != 1 && mode != 2 && mode != 4)
+            return fail(BOS_ERR_UNIMPLEMENTED, "bos_render: save_for_backward needs FP32_COMP, BF16_COMP or FP64");
         if (c->integ.integrator == 1)
             return fail(BOS_ERR_UNIMPLEMENTED, "bos_render: no adjoint for the RK4 integrator");
+        if (mode == 4 && c->integ.integrator != 0)
+            return fail(BOS_ERR_UNIMPLEMENTED, "bos_render: the FP64 adjoint needs Sharma RKN");
         // quasi-linear tracing keeps only the final state (one-sweep adjoint)
         ck.max_ckpt = c->integ.integrator == 2 ? 1 : (c->integ.max_steps + ck.every - 1) / ck.every;
         size_t want = (size_t)ck.max_ckpt * 3 * (size_t)ck.nrays * sizeof(float4);
         bos_status_t s = dev_alloc(c, (void**)&c->ckpt, &c->ckpt_bytes, want, "bos_render: checkpoints");
         if (s != BOS_OK) return s;
-        s = dev_alloc(c, (void**)&c->excess, &c->excess_bytes, (size_t)ck.nrays * sizeof(float), "bos_render: excess");
+        // path-length record per ray: the float32 excess over ell, or (FP64) the float64 length
+        s = dev_alloc(c, (void**)&c->excess, &c->excess_bytes, (size_t)ck.nrays * (mode == 4 ? 8 : 4),
+                      "bos_render: excess");
         if (s != BOS_OK) return s;
         ck.state = c->ckpt;
         ck.excess = c->excess;
@@ -597,7 +601,8 @@ bos_status_t bos_backward(bos_ctx* c, const float* dLdI, float* dLdT, void* stre
     if (!c->saved) return fail(BOS_ERR_NOT_READY, "bos_backward: needs a bos_render with save_for_backward=1");
     DeviceGuard dg(c->device);
     size_t cells = (size_t)c->g.n[0] * c->g.n[1] * c->g.n[2];
-    bos_status_t s = dev_alloc(c, (void**)&c->acc, &c->acc_bytes, cells * sizeof(float4), "bos_backward: accumulators");
+    const size_t acc_bytes = cells * (c->saved_mode == 4 ? 32 : 16);   // float4, or four doubles (FP64) per node
+    bos_status_t s = dev_alloc(c, (void**)&c->acc, &c->acc_bytes, acc_bytes, "bos_backward: accumulators");
     if (s != BOS_OK) return s;
     if (c->integ.integrator != 2) {   // the quasi-linear adjoint keeps no segment states
         s = dev_alloc(c, (void**)&c->seg, &c->seg_bytes, adjoint_segment_bytes(c->saved_ck.every),
@@ -605,7 +610,7 @@ bos_status_t bos_backward(bos_ctx* c, const float* dLdI, float* dLdT, void* stre
         if (s != BOS_OK) return s;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(c->acc, 0, cells * sizeof(float4), st);
+    cudaError_t e = cudaMemsetAsync(c->acc, 0, acc_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->small, 0, 4, st);
     if (e != cudaSuccess) return cuda_fail(e, "bos_backward: memset");
     AdjDev adj{c->acc, dLdI, c->err, c->seg};

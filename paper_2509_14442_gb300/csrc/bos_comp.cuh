@@ -94,8 +94,11 @@ struct CompConst {
     float dt;
 };
 
+// One step; with AB != nullptr (Sharma RKN) the step's A and B are also written to AB[0..5]
+// (the adjoint's recompute keeps them, so its reverse step knows all three stage points).
 template <class E, int INTEG>
-__device__ __forceinline__ void comp_step(const CompField<E>& F, CompState& st, const CompConst& k, BrickCache& bc) {
+__device__ __forceinline__ void comp_step(const CompField<E>& F, CompState& st, const CompConst& k, BrickCache& bc,
+                                          float* AB = nullptr) {
     int ci[3];
     float cf[3], D[3];
     float inc_r[3], inc_v[3];
@@ -121,6 +124,11 @@ __device__ __forceinline__ void comp_step(const CompField<E>& F, CompState& st, 
             inc_r[a] = dt * (st.dv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
             inc_v[a] = (A[a] + 4.0f * B[a] + C[a]) * (1.0f / 6.0f);
         }
+        if (AB != nullptr)
+            for (int a = 0; a < 3; ++a) {
+                AB[a] = A[a];
+                AB[3 + a] = B[a];
+            }
     } else {
         // classic RK4 on (r, v): k1v..k4v are D at the four stage positions
         float k1[3], k2[3], k3[3], k4[3], q[3];

@@ -6,6 +6,7 @@
 //   loss_l2       -- L_BOS and its seed dL/dI                                 (Sec. 2.4)
 #include "bos_comp.cuh"
 #include "bos_device.cuh"
+#include "bos_full.cuh"
 #include "bos_internal.h"
 
 namespace bos {
@@ -121,83 +122,6 @@ __global__ void __launch_bounds__(256) build_store_kernel(GridDev g, const float
 }
 
 // ===================================================================== a3: integrators
-
-// ---- full-state integration in T = float (plain FP32) or double (FP64) ------------
-
-template <class T>
-struct FullField;
-
-template <>
-struct FullField<double> {
-    GridDev g;
-    __device__ __forceinline__ void rhs(const double x[3], double D[3]) const {
-        double eta, gr[3];
-        field_at(g, x, eta, gr);
-        for (int a = 0; a < 3; ++a) D[a] = eta * gr[a];
-    }
-    __device__ __forceinline__ double eta(const double x[3]) const {
-        double e, gr[3];
-        field_at(g, x, e, gr);
-        return e;
-    }
-};
-
-template <>
-struct FullField<float> {
-    GridDev g;
-    __device__ __forceinline__ float4 at(const float x[3]) const {
-        int i[3];
-        float f[3];
-        for (int a = 0; a < 3; ++a) {
-            float u = (x[a] - (float)g.origin[a]) * g.inv_hf[a] - 0.5f;
-            split_coord(u, g.n[a], i[a], f[a]);
-        }
-        return trilinear(static_cast<const F4P*>(g.store), brick_offset(i[0], i[1], i[2]), f[0], f[1], f[2]);
-    }
-    __device__ __forceinline__ void rhs(const float x[3], float D[3]) const { rhs_of(at(x), D); }
-    __device__ __forceinline__ float eta(const float x[3]) const { return 1.0f + at(x).x; }
-};
-
-template <class T, int INTEG>
-__device__ __forceinline__ void full_step(const FullField<T>& F, T r[3], T v[3], T dt) {
-    if (INTEG == 0) {
-        T A[3], B[3], C[3], p[3], D[3];
-        F.rhs(r, D);
-        for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
-        for (int a = 0; a < 3; ++a) p[a] = r[a] + (dt * T(0.5)) * v[a] + (dt * T(0.125)) * A[a];
-        F.rhs(p, D);
-        for (int a = 0; a < 3; ++a) B[a] = dt * D[a];
-        for (int a = 0; a < 3; ++a) p[a] = r[a] + dt * v[a] + (dt * T(0.5)) * B[a];
-        F.rhs(p, D);
-        for (int a = 0; a < 3; ++a) C[a] = dt * D[a];
-        for (int a = 0; a < 3; ++a) {
-            r[a] = r[a] + dt * (v[a] + (A[a] + T(2) * B[a]) / T(6));
-            v[a] = v[a] + (A[a] + T(4) * B[a] + C[a]) / T(6);
-        }
-    } else {
-        T k1v[3], k2v[3], k3v[3], k4v[3], k2r[3], k3r[3], k4r[3], p[3];
-        F.rhs(r, k1v);
-        for (int a = 0; a < 3; ++a) {
-            k2r[a] = v[a] + (dt * T(0.5)) * k1v[a];
-            p[a] = r[a] + (dt * T(0.5)) * v[a];
-        }
-        F.rhs(p, k2v);
-        for (int a = 0; a < 3; ++a) {
-            k3r[a] = v[a] + (dt * T(0.5)) * k2v[a];
-            p[a] = r[a] + (dt * T(0.5)) * k2r[a];
-        }
-        F.rhs(p, k3v);
-        for (int a = 0; a < 3; ++a) {
-            k4r[a] = v[a] + dt * k3v[a];
-            p[a] = r[a] + dt * k3r[a];
-        }
-        F.rhs(p, k4v);
-        for (int a = 0; a < 3; ++a) {
-            r[a] = r[a] + dt / T(6) * (v[a] + T(2) * k2r[a] + T(2) * k3r[a] + k4r[a]);
-            v[a] = v[a] + dt / T(6) * (k1v[a] + T(2) * k2v[a] + T(2) * k3v[a] + k4v[a]);
-        }
-    }
-}
 
 // ===================================================================== a2-a5: render
 
@@ -410,10 +334,16 @@ __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const 
     return comp_finish(S, R, h, e, want_hit);
 }
 
+// Plain FP32 / FP64 tracer.  For the float64 adjoint (T = double, Sharma RKN) the state
+// (r, v) is kept every K steps as six doubles, plane q of checkpoint c at
+// ((c * 6 + q) * nrays + ray) of ck.state, and the path length of the traced steps per ray
+// in ck.excess (as a double).
 template <class T, int INTEG>
-__device__ RayResult trace_full(const SceneDev& S, const FullField<T>& F, const Ray& R) {
+__device__ RayResult trace_full(const SceneDev& S, const FullField<T>& F, const Ray& R, const CkptDev& ck,
+                                long long ray) {
     T r[3], v[3];
     double rin[3];
+    double* const save = (sizeof(T) == 8 && INTEG == 0) ? reinterpret_cast<double*>(ck.state) : nullptr;
     for (int a = 0; a < 3; ++a) {
         rin[a] = S.cam.pos[a] + R.t_in * R.d[a];
         r[a] = (T)rin[a];
@@ -424,6 +354,13 @@ __device__ RayResult trace_full(const SceneDev& S, const FullField<T>& F, const 
     T lensum = 0;
     const T rl[3] = {r[0], r[1], r[2]}, v0[3] = {v[0], v[1], v[2]};
     for (int n = 0; n < R.N; ++n) {
+        if (save != nullptr && n % ck.every == 0) {
+            const size_t c = (size_t)(n / ck.every);
+            for (int q = 0; q < 3; ++q) {
+                save[(c * 6 + q) * ck.nrays + ray] = (double)r[q];
+                save[(c * 6 + 3 + q) * ck.nrays + ray] = (double)v[q];
+            }
+        }
         T r0[3] = {r[0], r[1], r[2]};
         if constexpr (INTEG == 2) {
             // quasi-linear: the field on the straight line at the start, middle and end of the step
@@ -447,6 +384,7 @@ __device__ RayResult trace_full(const SceneDev& S, const FullField<T>& F, const 
         T d0 = r[0] - r0[0], d1 = r[1] - r0[1], d2 = r[2] - r0[2];
         lensum += sqrt(d0 * d0 + d1 * d1 + d2 * d2);
     }
+    if (save != nullptr) reinterpret_cast<double*>(ck.excess)[ray] = (double)lensum;
     double rN[3] = {(double)r[0], (double)r[1], (double)r[2]};
     double vN[3] = {(double)v[0], (double)v[1], (double)v[2]};
     return wall_epilogue(S, S.cam.pos, R, rN, vN, R.t_in + (double)lensum);
@@ -471,11 +409,11 @@ __device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, 
     } else if constexpr (MODE == 3) {
         FullField<float> F = {S.g};
         steps += (unsigned long long)R.N;
-        return trace_full<float, INTEG>(S, F, R);
+        return trace_full<float, INTEG>(S, F, R, ck, ray);
     } else {
         FullField<double> F = {S.g};
         steps += (unsigned long long)R.N;
-        return trace_full<double, INTEG>(S, F, R);
+        return trace_full<double, INTEG>(S, F, R, ck, ray);
     }
 }
 
@@ -519,7 +457,10 @@ __global__ void __launch_bounds__(128, FEW ? 1 : INTEG == 2 ? BOS_FWD_QUASI_MIN_
                 RayResult r;
                 if (MODE == 0 || (R.N == 0 && !CONN)) {
                     r = straight_epilogue(S, R, out.hit != nullptr);
-                    if (R.N == 0 && ck.state != nullptr) ck.excess[ray] = 0.0f;
+                    if (R.N == 0 && ck.state != nullptr) {
+                        if (MODE == 4) reinterpret_cast<double*>(ck.excess)[ray] = 0.0;
+                        else ck.excess[ray] = 0.0f;
+                    }
                 } else {
                     r = trace_ray<MODE, INTEG, CONN>(S, R, ck, ray, out.hit != nullptr, my_steps);
                 }

@@ -51,15 +51,14 @@ struct AdjDev {
     float* seg;          // per-warp segment states of the Sharma adjoint (adjoint_segment_bytes)
 };
 
-// The Sharma adjoint keeps each recomputed segment's K step states (6 floats per lane and
-// step; two segments per warp, the one being reversed and the one being recomputed) in a
-// per-warp slice of global memory (L1/L2-resident while the segment is reversed)
+// The Sharma adjoint keeps each recomputed segment's K steps (state and stage terms
+// (dr, dv, A, B): 12 floats per lane and step) in a per-warp slice of global memory (L1/L2-resident while the segment is reversed)
 // rather than in shared memory, which would cap the kernel at fewer resident warps.  Its
 // grid is capped at kAdjMaxBlocks blocks of kAdjWarpsPerBlock warps.
 constexpr int kAdjMaxBlocks = 1024;
 constexpr int kAdjWarpsPerBlock = 2;
-inline size_t adjoint_segment_bytes(int K) {   // two rounds in flight per warp
-    return (size_t)2 * kAdjMaxBlocks * kAdjWarpsPerBlock * (size_t)K * 6 * 32 * sizeof(float);
+inline size_t adjoint_segment_bytes(int K) {
+    return (size_t)kAdjMaxBlocks * kAdjWarpsPerBlock * (size_t)K * 12 * 32 * sizeof(float);
 }
 
 // Message returned by bos_last_error() on the calling thread.

@@ -67,6 +67,42 @@ def test_adjoint_matches_oracle_on_32cube_crop(bos, orc):
     assert rel_l2(g_gpu, g_orc) <= GRAD_REL_L2
 
 
+# Float64 GPU adjoint against the oracle's float64 discrete adjoint: the same
+# discretisation in the same precision, so only the order of float64 roundings differs
+# (FMA contraction on the GPU, the atomics' summation order): ~1e-12 relative, far inside
+# 1e-9, while any wrong term of the adjoint shows up at O(1).
+GRAD_REL_L2_FP64 = 1e-9
+
+
+def test_fp64_adjoint_matches_oracle_on_32cube_crop(bos, orc):
+    sc = crop_scene()
+    w = np.random.default_rng(11).standard_normal((sc.camera.height, sc.camera.width))
+    g_orc = orc.grad(sc, w)
+    g_gpu = gpu_grad(bos, sc, w, bos.BOS_PREC_FP64)
+    assert np.abs(g_orc).max() > 0
+    assert rel_l2(g_gpu, g_orc) <= GRAD_REL_L2_FP64
+
+
+@pytest.mark.parametrize("K", [1, 7, 16])
+def test_fp64_adjoint_matches_oracle_small_room(bos, orc, K):
+    sc = S.room((40, 40, 30), 61, 47, 2, 3150 + K)
+    sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, ckpt_every=K))   # ragged segments
+    w = np.random.default_rng(K).standard_normal((sc.camera.height, sc.camera.width))
+    assert rel_l2(gpu_grad(bos, sc, w, bos.BOS_PREC_FP64), orc.grad(sc, w)) <= GRAD_REL_L2_FP64
+
+
+def test_fp64_adjoint_refuses_the_integrators_it_does_not_reverse(bos):
+    sc = S.room((16, 16, 12), 16, 16, 1, 3160)
+    for integ in (1, 2):
+        ctx = bos.Context(0)
+        ctx.set_scene(sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=integ)),
+                      bos.BOS_PREC_FP64)
+        with pytest.raises(bos.BosError) as e:
+            ctx.render(disp=False, save_for_backward=True)
+        assert e.value.status == bos.BOS_ERR_UNIMPLEMENTED
+        ctx.close()
+
+
 @pytest.mark.parametrize("spp", [1, 2, 3])
 def test_adjoint_matches_oracle_small_room(bos, orc, spp):
     sc = S.room((40, 40, 30), 61, 47, spp, 3100 + spp)

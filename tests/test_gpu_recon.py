@@ -127,20 +127,27 @@ def test_reconstruction_iterations_match_the_oracle_loop(bos, orc, integrator):
     scaled minibatch L_BOS and a float64 AdaBelief.  The field after k iterations agrees
     element by element.
 
+    The target is the oracle's render of the true field with 10 % seeded multiplicative
+    noise: the residuals target - I are then ~1e-3, a thousand times the float32 render's
+    intensity rounding (~1e-6), whereas the noise-free residual of this small scene
+    (~3e-6) is at that rounding and would make dL/dI differ at O(1) between the two sides.
+
     Tolerance: eps is set so that sqrt(eps / (1 - beta2)) is ~1 % of the largest gradient;
     below that AdaBelief's step is linear in the gradient, so the float32 gradient's error
-    (~1e-6 of the largest gradient) moves T by ~1e-4 lr per iteration at most; the bound is
+    (~1e-4 of the largest gradient here) moves T by ~1e-2 lr per iteration at most; in the
+    saturated regime the step depends only on the gradient's sign history.  The bound is
     2e-3 lr per iteration, summed over the k iterations."""
     from paper_2509_14442_gb300.recon import Reconstructor
 
     sc = S.room((12, 12, 9), 32, 32, 1, 3970, pattern_size=32)
     sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=integrator, ckpt_every=16))
     truth = sc.T.astype(np.float64)
-    target = orc.render(sc)["I"]                              # (H, W) float64, the measurement
+    I_true = orc.render(sc)["I"]                              # (H, W) float64
+    target = I_true * (1.0 + 0.1 * np.random.default_rng(3971).standard_normal(I_true.shape))
     T0 = np.full(truth.shape, S.T_AMBIENT)
     H, W = sc.camera.height, sc.camera.width
     k, batch, lr, b1, b2, seed = 5, 256, 0.2, 0.9, 0.999, 11
-    scale = 1e11
+    scale = 1e8
 
     def draw(d):
         return np.array([(orc.splitmix64_output(seed, d * batch + j + 1) * (H * W)) >> 64 for j in range(batch)],
