@@ -253,6 +253,14 @@ bos_status_t bos_counter_add(uint64_t* counter_dev, uint64_t inc, void* stream);
  * transpose of the difference stencil and d deta/dT = -rho0 G T0 / T^2. */
 bos_status_t bos_backward(bos_ctx* ctx, const float* dLdI_dev, float* dLdT_dev, void* stream);
 
+/* Step a6 for the FP64 precision with a float64 seed and result (Sec. 2.4): as
+ * bos_backward, for the most recent FP64 render with save_for_backward=1 (Sharma RKN,
+ * ckpt_every <= 64), with dL/dI given as float64 (height*width, or npix after
+ * bos_render_pixels) and dL/dT written as float64 (nz*ny*nx), so that the float64 adjoint's
+ * result is not rounded to float32 at the boundary.  BOS_ERR_UNIMPLEMENTED for a render of
+ * another precision. */
+bos_status_t bos_backward_f64(bos_ctx* ctx, const double* dLdI_dev, double* dLdT_dev, void* stream);
+
 /* Copy the stored node values back in grid order: out_dev receives nz*ny*nx*4
  * values (deta, d eta/dx, d eta/dy, d eta/dz) of the store type (float32, bf16 as
  * uint16 bit patterns, or float64), read through the brick addressing. */

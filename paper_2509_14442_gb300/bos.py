@@ -97,6 +97,7 @@ SIGNATURES = {
     "bos_last_ray_steps": (_i, [_v, _P(_u64)]),
     "bos_loss_l2": (_i, [_v, _v, _i64, _v, _v, _v]),
     "bos_backward": (_i, [_v, _v, _v, _v]),
+    "bos_backward_f64": (_i, [_v, _v, _v, _v]),
     "bos_loss_l2_pixels": (_i, [_v, _v, _v, _i64, C.c_float, _v, _v, _v]),
     "bos_sample_pixels": (_i, [_v, _i64, _i64, _u64, _u64, _v, _v]),
     "bos_adabelief_step": (_i, [_v, _v, _v, _v, _i64, C.c_float, C.c_float, C.c_float, C.c_float, _i64, _v, _v]),
@@ -269,6 +270,10 @@ def bos_backward(ctx, dLdI_dev, dLdT_dev, stream) -> None:
     check(lib().bos_backward(ctx, dLdI_dev, dLdT_dev, stream), "bos_backward")
 
 
+def bos_backward_f64(ctx, dLdI_dev, dLdT_dev, stream) -> None:
+    check(lib().bos_backward_f64(ctx, dLdI_dev, dLdT_dev, stream), "bos_backward_f64")
+
+
 def bos_export_nodes(ctx, out_dev, stream) -> None:
     check(lib().bos_export_nodes(ctx, out_dev, stream), "bos_export_nodes")
 
@@ -429,6 +434,15 @@ class Context:
         assert dLdI.is_cuda and dLdI.dtype == torch.float32 and dLdI.is_contiguous()
         dT = torch.empty_like(self.T)
         bos_backward(self.h, dLdI.data_ptr(), dT.data_ptr(), _stream(stream))
+        return dT
+
+    def backward_f64(self, dLdI, stream=None):
+        """dL/dT in float64 from a float64 dL/dI (FP64 renders)."""
+        import torch
+
+        assert dLdI.is_cuda and dLdI.dtype == torch.float64 and dLdI.is_contiguous()
+        dT = torch.empty(self.T.shape, dtype=torch.float64, device=self.torch_device)
+        bos_backward_f64(self.h, dLdI.data_ptr(), dT.data_ptr(), _stream(stream))
         return dT
 
     def status(self):

@@ -951,6 +951,8 @@ __device__ __forceinline__ void drhs_adjoint_scatter(const GridDev& g, const DSt
     }
 }
 
+// G = the seed's type: float (bos_backward) or double (bos_backward_f64).
+template <class G>
 __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_fp64_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int K = ck.every;
@@ -979,7 +981,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_fp64_kernel(SceneDev S
             double Ib = 0.0;
             if (tp.valid) {
                 R = ray_setup(S, tp.px, tp.py, s);
-                Ib = (double)adj.dLdI[(size_t)tp.out] / spp;
+                Ib = (double)reinterpret_cast<const G*>(adj.dLdI)[(size_t)tp.out] / spp;
             }
             const bool act = tp.valid && R.wall && R.N > 0 && Ib != 0.0;
             // entry state as the forward forms it: r_in, eta_in, v0 = eta_in d, dt = ell / (N eta_in)
@@ -1124,9 +1126,9 @@ __device__ __forceinline__ double acc_channel(const float4* acc, long long m, in
 }
 __device__ __forceinline__ double acc_channel(const double* acc, long long m, int ch) { return acc[m * 4 + ch]; }
 
-template <class A>
+template <class A, class O = float>
 __global__ void gradient_kernel(GridDev g, const A* __restrict__ acc, const float* __restrict__ T,
-                                float* __restrict__ dLdT) {
+                                O* __restrict__ dLdT) {
     const long long n = (long long)g.n[0] * g.n[1] * g.n[2];
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         const int idx[3] = {(int)(c % g.n[0]), (int)((c / g.n[0]) % g.n[1]), (int)(c / ((long long)g.n[0] * g.n[1]))};
@@ -1142,7 +1144,7 @@ __global__ void gradient_kernel(GridDev g, const A* __restrict__ acc, const floa
         }
         if constexpr (sizeof(A) == 8) {
             const double Tc = (double)T[c];
-            dLdT[c] = (float)(tot * (-g.K / (Tc * Tc)));
+            dLdT[c] = (O)(tot * (-g.K / (Tc * Tc)));
         } else {
             const float Tc = T[c];
             dLdT[c] = (float)tot * (-(float)g.K / (Tc * Tc));
@@ -1203,20 +1205,28 @@ static cudaError_t launch_adjoint_quasi_t(const SceneDev& S, const CkptDev& ck, 
     return launch_adjoint_quasi_b<E, BOS_ADJ_QUASI_SMALL_MIN_BLOCKS>(S, ck, adj, w, num_sms, st);
 }
 
+// Float64 store and tracer: Sharma RKN, float64 accumulators; seed and dL/dT in float32 or
+// (f64) float64.
+cudaError_t launch_backward_fp64(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
+                                 const float* T, void* dLdT, bool f64, int num_sms, cudaStream_t st) {
+    if (S.it.integrator != 0 || S.L.mode == 2 || adj.seg == nullptr || ck.every > 64) return cudaErrorNotSupported;
+    const int blocks = num_sms * 8 < kAdjMaxBlocks ? num_sms * 8 : kAdjMaxBlocks;
+    if (f64) adjoint_fp64_kernel<double><<<blocks, kAdjWarps * 32, 0, st>>>(S, ck, adj, w);
+    else adjoint_fp64_kernel<float><<<blocks, kAdjWarps * 32, 0, st>>>(S, ck, adj, w);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const double* acc = reinterpret_cast<const double*>(adj.acc);
+    if (f64) gradient_kernel<double, double><<<num_sms * 8, 256, 0, st>>>(S.g, acc, T, static_cast<double*>(dLdT));
+    else gradient_kernel<double, float><<<num_sms * 8, 256, 0, st>>>(S.g, acc, T, static_cast<float*>(dLdT));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_backward(int mode, const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
                             const float* T, float* dLdT, int num_sms, cudaStream_t st) {
     const bool quasi = S.it.integrator == 2;
     if (!quasi && ck.every > 64) return cudaErrorNotSupported;
     cudaError_t e;
-    if (mode == 4) {   // float64 store and tracer: Sharma RKN, float64 accumulators
-        if (S.it.integrator != 0 || S.L.mode == 2 || adj.seg == nullptr) return cudaErrorNotSupported;
-        adjoint_fp64_kernel<<<num_sms * 8 < kAdjMaxBlocks ? num_sms * 8 : kAdjMaxBlocks, kAdjWarps * 32, 0, st>>>(
-            S, ck, adj, w);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        gradient_kernel<double><<<num_sms * 8, 256, 0, st>>>(S.g, reinterpret_cast<const double*>(adj.acc), T, dLdT);
-        return cudaGetLastError();
-    }
+    if (mode == 4) return launch_backward_fp64(S, ck, adj, w, T, dLdT, false, num_sms, st);
     if (mode == 1) e = quasi ? launch_adjoint_quasi_t<F4P>(S, ck, adj, w, num_sms, st)
                              : launch_adjoint_t<F4P>(S, ck, adj, w, num_sms, st);
     else if (mode == 2) e = quasi ? launch_adjoint_quasi_t<B4P>(S, ck, adj, w, num_sms, st)

@@ -596,9 +596,11 @@ bos_status_t bos_loss_l2(const float* I, const float* target, int64_t n, double*
     return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_loss_l2");
 }
 
-bos_status_t bos_backward(bos_ctx* c, const float* dLdI, float* dLdT, void* stream) {
+static bos_status_t backward_impl(bos_ctx* c, const void* dLdI, void* dLdT, bool f64, void* stream) {
     if (!c || !dLdI || !dLdT) return fail(BOS_ERR_INVALID_ARG, "bos_backward: NULL argument");
     if (!c->saved) return fail(BOS_ERR_NOT_READY, "bos_backward: needs a bos_render with save_for_backward=1");
+    if (f64 && c->saved_mode != 4)
+        return fail(BOS_ERR_UNIMPLEMENTED, "bos_backward_f64: needs a render of the FP64 precision");
     DeviceGuard dg(c->device);
     size_t cells = (size_t)c->g.n[0] * c->g.n[1] * c->g.n[2];
     const size_t acc_bytes = cells * (c->saved_mode == 4 ? 32 : 16);   // float4, or four doubles (FP64) per node
@@ -613,14 +615,23 @@ bos_status_t bos_backward(bos_ctx* c, const float* dLdI, float* dLdT, void* stre
     cudaError_t e = cudaMemsetAsync(c->acc, 0, acc_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->small, 0, 4, st);
     if (e != cudaSuccess) return cuda_fail(e, "bos_backward: memset");
-    AdjDev adj{c->acc, dLdI, c->err, c->seg};
+    AdjDev adj{c->acc, static_cast<const float*>(dLdI), c->err, c->seg};
     WorkDev w{c->tile_counter, c->steps, c->err};
     SceneDev S = scene_of(c);
     S.pix = c->saved_pix;
     S.npix = c->saved_npix;
-    e = launch_backward(c->saved_mode, S, c->saved_ck, adj, w, c->T, dLdT, c->num_sms, st);
+    e = f64 ? launch_backward_fp64(S, c->saved_ck, adj, w, c->T, dLdT, true, c->num_sms, st)
+            : launch_backward(c->saved_mode, S, c->saved_ck, adj, w, c->T, static_cast<float*>(dLdT), c->num_sms, st);
     if (e == cudaErrorNotSupported) return fail(BOS_ERR_UNIMPLEMENTED, "bos_backward: not available for this mode");
     return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_backward: launch");
+}
+
+bos_status_t bos_backward(bos_ctx* c, const float* dLdI, float* dLdT, void* stream) {
+    return backward_impl(c, dLdI, dLdT, false, stream);
+}
+
+bos_status_t bos_backward_f64(bos_ctx* c, const double* dLdI, double* dLdT, void* stream) {
+    return backward_impl(c, dLdI, dLdT, true, stream);
 }
 
 bos_status_t bos_export_nodes(bos_ctx* c, void* out, void* stream) {

@@ -45,8 +45,8 @@ struct CkptDev {
 
 // Grid adjoint accumulators: per node (d L/d deta, d L/d grad eta) in float32.
 struct AdjDev {
-    float4* acc;
-    const float* dLdI;
+    float4* acc;                    // float64 precision: four doubles per node
+    const float* dLdI;              // bos_backward_f64: points at doubles
     int* err;
     float* seg;          // per-warp segment states of the Sharma adjoint (adjoint_segment_bytes)
 };
@@ -79,6 +79,8 @@ cudaError_t launch_probe_read(const void* buf, long long bytes, int repeats, flo
 cudaError_t launch_probe_fma(int kind, int repeats, float* sink, int num_sms, double* flops, cudaStream_t st);
 cudaError_t launch_probe_read_l1(const void* buf, long long bytes, int repeats, float* sink, int num_sms,
                                  double* bytes_read, cudaStream_t st);
+cudaError_t launch_backward_fp64(const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
+                                 const float* T, void* dLdT, bool f64, int num_sms, cudaStream_t st);
 cudaError_t launch_backward(int mode, const SceneDev& S, const CkptDev& ck, const AdjDev& adj, const WorkDev& w,
                             const float* T, float* dLdT, int num_sms, cudaStream_t st);
 

@@ -59,3 +59,58 @@ def errors(gpu, orc, pix=None):
 
 def with_camera(scene, **kw):
     return scene.replace(camera=dataclasses.replace(scene.camera, **kw))
+
+
+# Finite-difference check of a full-size adjoint (the survey's A16 reading): dL/dT_v by
+# central differences of the oracle, L(T) = sum_j w_j I_j(T), at voxels of the plume that
+# some camera (or projector) ray reaches.  Each difference sums over the pixels whose rays
+# pass within 3 cells of the voxel (the only ones its value reaches).  A voxel is a kink
+# (a ray's stage point crosses a cell face within the step, where the trilinear field's
+# derivative jumps) when its difference at h and at h/2 disagree by more than 1e-5; kinks
+# are skipped, as A16 allows.  Bar: |adjoint - FD| <= 1e-4 |FD| + 1e-6 max|FD| (the second
+# term is the float32 accumulation floor of voxels whose gradient is a near-cancelling sum).
+FD_REL_TOL = 1e-4
+FD_FLOOR = 1e-6
+FD_KINK = 1e-5
+
+
+def fd_check(orc, scene, g_gpu, w, nvox, rng, near):
+    """Returns (adjoint, fd, kept) at nvox sampled plume voxels; asserts the A16 bar."""
+    hg = np.array(scene.grid.spacing())
+    origin = np.array(scene.grid.origin)
+    hot = np.argwhere(scene.T > 300.0)
+    rng.shuffle(hot)
+    vox, pixs = [], []
+    for k, j, i in hot:                       # plume voxels that some ray reaches
+        c = origin + (np.array([i, j, k]) + 0.5) * hg
+        pix = near(scene, c, 3.0 * hg + 1e-3)
+        if len(pix):
+            vox.append((k, j, i))
+            pixs.append(pix)
+        if len(vox) == nvox:
+            break
+    assert len(vox) == nvox
+    T64 = scene.T.astype(np.float64)
+
+    def fd_at(k, j, i, pix, h):
+        vals = []
+        for sgn in (1.0, -1.0):
+            T = T64.copy()
+            T[k, j, i] += sgn * h
+            I = orc.render(scene.replace(T=T), pix=pix)["I"]
+            vals.append(float((w.reshape(-1)[pix] * I).sum()))
+        return (vals[0] - vals[1]) / (2 * h)
+
+    fd, fd2, gp = [], [], []
+    for (k, j, i), pix in zip(vox, pixs):
+        fd.append(fd_at(k, j, i, pix, 1e-2))
+        fd2.append(fd_at(k, j, i, pix, 5e-3))
+        gp.append(g_gpu[k, j, i])
+    fd, fd2, gp = np.array(fd), np.array(fd2), np.array(gp)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    kept = np.abs(fd - fd2) <= FD_KINK * np.maximum(np.abs(fd), 1e-3 * scale)
+    assert kept.sum() >= 0.75 * nvox, kept.sum()
+    bad = kept & (np.abs(gp - fd) > FD_REL_TOL * np.abs(fd) + FD_FLOOR * scale)
+    assert bad.sum() == 0, (np.flatnonzero(bad), gp[bad], fd[bad])
+    return gp, fd, kept

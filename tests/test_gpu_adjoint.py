@@ -67,20 +67,37 @@ def test_adjoint_matches_oracle_on_32cube_crop(bos, orc):
     assert rel_l2(g_gpu, g_orc) <= GRAD_REL_L2
 
 
-# Float64 GPU adjoint against the oracle's float64 discrete adjoint: the same
-# discretisation in the same precision, so only the order of float64 roundings differs
-# (FMA contraction on the GPU, the atomics' summation order): ~1e-12 relative, far inside
-# 1e-9, while any wrong term of the adjoint shows up at O(1).
+# Float64 GPU adjoint against the oracle's float64 discrete adjoint, seed and result in
+# float64 (bos_backward_f64): the same discretisation in the same precision, so only the
+# order of float64 roundings differs (FMA contraction and the lerp form of the trilinear
+# interpolant on the GPU, the atomics' summation order): far inside 1e-9, while any wrong
+# term of the adjoint shows up at O(1).  Through the float32 boundary (bos_backward: float32
+# dL/dI in, float32 dL/dT out) the floor is the float32 rounding of seed and result,
+# 2^-24 per element.
 GRAD_REL_L2_FP64 = 1e-9
+GRAD_REL_L2_FP64_F32_IO = 2e-7
+
+
+def gpu_grad64(bos, scene, w):
+    ctx = bos.Context(0)
+    ctx.set_scene(scene, bos.BOS_PREC_FP64)
+    ctx.render(disp=False, save_for_backward=True)
+    dT = ctx.backward_f64(torch.as_tensor(np.ascontiguousarray(w, dtype=np.float64), device="cuda"))
+    torch.cuda.synchronize()
+    ctx.status()
+    out = dT.cpu().numpy()
+    ctx.close()
+    return out
 
 
 def test_fp64_adjoint_matches_oracle_on_32cube_crop(bos, orc):
     sc = crop_scene()
     w = np.random.default_rng(11).standard_normal((sc.camera.height, sc.camera.width))
     g_orc = orc.grad(sc, w)
-    g_gpu = gpu_grad(bos, sc, w, bos.BOS_PREC_FP64)
     assert np.abs(g_orc).max() > 0
-    assert rel_l2(g_gpu, g_orc) <= GRAD_REL_L2_FP64
+    assert rel_l2(gpu_grad64(bos, sc, w), g_orc) <= GRAD_REL_L2_FP64
+    # the float32 entry point of the same adjoint: only the boundary's rounding remains
+    assert rel_l2(gpu_grad(bos, sc, w, bos.BOS_PREC_FP64), g_orc) <= GRAD_REL_L2_FP64_F32_IO
 
 
 @pytest.mark.parametrize("K", [1, 7, 16])
@@ -88,7 +105,18 @@ def test_fp64_adjoint_matches_oracle_small_room(bos, orc, K):
     sc = S.room((40, 40, 30), 61, 47, 2, 3150 + K)
     sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, ckpt_every=K))   # ragged segments
     w = np.random.default_rng(K).standard_normal((sc.camera.height, sc.camera.width))
-    assert rel_l2(gpu_grad(bos, sc, w, bos.BOS_PREC_FP64), orc.grad(sc, w)) <= GRAD_REL_L2_FP64
+    assert rel_l2(gpu_grad64(bos, sc, w), orc.grad(sc, w)) <= GRAD_REL_L2_FP64
+
+
+def test_backward_f64_needs_an_fp64_render(bos):
+    sc = S.room((16, 16, 12), 16, 16, 1, 3161)
+    ctx = bos.Context(0)
+    ctx.set_scene(sc, bos.BOS_PREC_FP32_COMP)
+    ctx.render(disp=False, save_for_backward=True)
+    with pytest.raises(bos.BosError) as e:
+        ctx.backward_f64(torch.zeros((16, 16), dtype=torch.float64, device="cuda"))
+    assert e.value.status == bos.BOS_ERR_UNIMPLEMENTED
+    ctx.close()
 
 
 def test_fp64_adjoint_refuses_the_integrators_it_does_not_reverse(bos):
@@ -160,71 +188,29 @@ def _pixels_near(scene, center, margin):
 @pytest.mark.slow
 def test_adjoint_full_size_against_oracle_finite_differences(bos, orc):
     # 256x256x192 plume, 2048^2 camera, 1 spp, checkpoints every 16 steps: the benchmarked
-    # launch.  L(T) = sum_j w_j I_j(T) with seeded w; dL/dT_v by central differences of the
-    # oracle (h = 0.01 K) at 64 seeded voxels in the plume, each over the pixels whose rays
-    # pass within 3 cells of the voxel (the only ones its value reaches).
+    # launch, against central differences of the oracle at 64 seeded plume voxels that the
+    # camera sees (helpers.fd_check: A16's bar, kinks skipped)
+    from helpers import fd_check
+
     sc = S.room_adjoint()
     rng = np.random.default_rng(64)
     w = rng.standard_normal((sc.camera.height, sc.camera.width))
-    g_gpu = gpu_grad(bos, sc, w)
-    hot = np.argwhere(sc.T > 300.0)
-    vox = hot[rng.choice(len(hot), 64, replace=False)]
-    hgrid = np.array(sc.grid.spacing())
-    eps = 1e-2
-    T64 = sc.T.astype(np.float64)
-    fd, gp = [], []
-    for k, j, i in vox:
-        center = np.array(sc.grid.origin) + (np.array([i, j, k]) + 0.5) * hgrid
-        pix = _pixels_near(sc, center, 3.0 * hgrid + 1e-3)
-        vals = []
-        for sgn in (1.0, -1.0):
-            T = T64.copy()
-            T[k, j, i] += sgn * eps
-            I = orc.render(sc.replace(T=T), pix=pix)["I"]
-            vals.append(float((w.reshape(-1)[pix] * I).sum()))
-        fd.append((vals[0] - vals[1]) / (2 * eps))
-        gp.append(g_gpu[k, j, i])
-    fd, gp = np.array(fd), np.array(gp)
-    scale = np.abs(fd).max()
-    assert scale > 0
-    bad = np.abs(gp - fd) > 1e-3 * np.abs(fd) + 1e-3 * scale
-    assert bad.sum() == 0, (np.flatnonzero(bad), gp[bad], fd[bad])
+    fd_check(orc, sc, gpu_grad(bos, sc, w), w, 64, rng, _pixels_near)
 
 
 # ------------------------------------------------------------------ quasi-linear tracing (Sec. 2.2)
 
 @pytest.mark.slow
 def test_quasi_linear_adjoint_full_size_against_oracle_finite_differences(bos, orc):
-    # the benchmarked quasi-linear launch (256x256x192, 2048^2, 1 spp; the 128-register
-    # form of the adjoint): dL/dT_v by central differences of the oracle at 64 seeded
-    # plume voxels, over the pixels whose rays pass within 3 cells of each voxel
+    # the benchmarked quasi-linear launch (256x256x192, 2048^2, 1 spp; the 128-register form
+    # of the adjoint) against central differences of the oracle at 64 seeded plume voxels
+    from helpers import fd_check
+
     sc = S.room_adjoint()
     sc = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=2))
     rng = np.random.default_rng(65)
     w = rng.standard_normal((sc.camera.height, sc.camera.width))
-    g_gpu = gpu_grad(bos, sc, w)
-    hot = np.argwhere(sc.T > 300.0)
-    vox = hot[rng.choice(len(hot), 64, replace=False)]
-    hgrid = np.array(sc.grid.spacing())
-    eps = 1e-2
-    T64 = sc.T.astype(np.float64)
-    fd, gp = [], []
-    for k, j, i in vox:
-        center = np.array(sc.grid.origin) + (np.array([i, j, k]) + 0.5) * hgrid
-        pix = _pixels_near(sc, center, 3.0 * hgrid + 1e-3)
-        vals = []
-        for sgn in (1.0, -1.0):
-            T = T64.copy()
-            T[k, j, i] += sgn * eps
-            I = orc.render(sc.replace(T=T), pix=pix)["I"]
-            vals.append(float((w.reshape(-1)[pix] * I).sum()))
-        fd.append((vals[0] - vals[1]) / (2 * eps))
-        gp.append(g_gpu[k, j, i])
-    fd, gp = np.array(fd), np.array(gp)
-    scale = np.abs(fd).max()
-    assert scale > 0
-    bad = np.abs(gp - fd) > 1e-3 * np.abs(fd) + 1e-3 * scale
-    assert bad.sum() == 0, (np.flatnonzero(bad), gp[bad], fd[bad])
+    fd_check(orc, sc, gpu_grad(bos, sc, w), w, 64, rng, _pixels_near)
 
 
 @pytest.mark.parametrize("spp", [1, 3])

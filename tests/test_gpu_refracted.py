@@ -148,31 +148,12 @@ def _pixels_near_either_ray(scene, center, margin):
 @pytest.mark.slow
 def test_refracted_adjoint_full_size_against_oracle_finite_differences(bos, orc):
     # the benchmarked refracted launch: dL/dT at 16 seeded plume voxels against central
-    # differences of the oracle (h = 0.01 K) over the pixels the voxel can reach through the
-    # camera ray or the projector ray
+    # differences of the oracle over the pixels the voxel can reach through the camera ray or
+    # the projector ray (helpers.fd_check: A16's bar, kinks skipped)
+    from helpers import fd_check
+
     sc = refracted(S.room_adjoint(), boost=1.0)
     rng = np.random.default_rng(65)
     w = rng.standard_normal((sc.camera.height, sc.camera.width))
-    g_gpu = gpu_grad(bos, sc, w)
-    hot = np.argwhere(sc.T > 300.0)
-    vox = hot[rng.choice(len(hot), 16, replace=False)]
-    hgrid = np.array(sc.grid.spacing())
-    eps = 1e-2
-    T64 = sc.T.astype(np.float64)
-    fd, gp = [], []
-    for k, j, i in vox:
-        center = np.array(sc.grid.origin) + (np.array([i, j, k]) + 0.5) * hgrid
-        pix = _pixels_near_either_ray(sc, center, 3.0 * hgrid + 1e-3)
-        vals = []
-        for sgn in (1.0, -1.0):
-            T = T64.copy()
-            T[k, j, i] += sgn * eps
-            I = orc.render(sc.replace(T=T), pix=pix)["I"]
-            vals.append(float((w.reshape(-1)[pix] * I).sum()))
-        fd.append((vals[0] - vals[1]) / (2 * eps))
-        gp.append(g_gpu[k, j, i])
-    fd, gp = np.array(fd), np.array(gp)
-    scale = np.abs(fd).max()
-    assert scale > 0
-    bad = np.abs(gp - fd) > 1e-3 * np.abs(fd) + 1e-3 * scale
-    assert bad.sum() == 0, (np.flatnonzero(bad), gp[bad], fd[bad])
+    fd_check(orc, sc, gpu_grad(bos, sc, w), w, 16, rng, _pixels_near_either_ray)
+
