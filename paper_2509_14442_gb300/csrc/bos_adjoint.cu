@@ -627,7 +627,10 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
                     }
                     // scatter the three stages: one pass over the lane's cell row for the
                     // stages in stage 3's cell, then the others (a step that crosses a face)
-                    const bool same2 = key2 == key3, same1 = key1 == key3;
+#ifndef BOS_ADJ_ONE_PASS
+#define BOS_ADJ_ONE_PASS 1
+#endif
+                    const bool same2 = BOS_ADJ_ONE_PASS && key2 == key3, same1 = BOS_ADJ_ONE_PASS && key1 == key3;
                     accumulate3(rows, a_, key3, cf3, Q3, same2, cf2, Q2, same1, cf1, Q1, ca, acc, nx, nxy);
                     accumulate(rows, a_ && !same2, key2, cf2, Q2, ca, acc, nx, nxy);
                     accumulate(rows, a_ && !same1, key1, cf1, Q1, ca, acc, nx, nxy);
