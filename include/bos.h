@@ -334,17 +334,21 @@ uint64_t bos_device_bytes(bos_ctx* ctx);
 
 /* ------------------------------------------------------------------ request server
  *
- * Continuous batching of renders on one GPU.  A request is one frame: a temperature
- * field on the device plus geometry; it is a forward render, or with target_dev set a
- * forward + adjoint render (L_BOS against target_dev, then dL/dT).  Requests queue in
- * arrival order; the server admits the head when one of its slots is free and the
- * request's exact device footprint (bos_request_footprint) fits in the unused part of
- * the server's arena, one allocation of mem_limit_bytes made at creation.  Each admitted
- * request runs on its slot's own stream, so the work of all admitted requests overlaps
- * on the device; requests arriving meanwhile are admitted as slots and memory free up.
- * All device buffers named in a request are caller-owned and must stay valid until the
- * request is done.  The server never blocks without a bound: bos_wait and
- * bos_server_destroy take timeouts and return BOS_ERR_TIMEOUT. */
+ * Continuous batching of renders on one GPU.  A request is one frame: a temperature field
+ * on the device plus geometry; it is a forward render, or with target_dev set a forward +
+ * adjoint render (L_BOS against target_dev, then dL/dT).  Requests queue in arrival order;
+ * the server admits the head when fewer than `slots` requests are in flight and the
+ * request's exact device footprint (bos_request_footprint) fits in the unused part of the
+ * server's arena, one allocation of mem_limit_bytes made at creation.  Admitted requests
+ * share batched launches: each launch pulls warp tiles of every admitted request in the
+ * same phase (render, or adjoint) from one device work list, oldest request first, with a
+ * few milliseconds of work per launch, so a request that arrives while others run joins
+ * the next launch and the work of all admitted requests overlaps on the device.  Requests
+ * with FP32_COMP or BF16_COMP stores, Sharma RKN or quasi-linear tracing, light mode 0 or 1
+ * and ckpt_every <= 64 are batched; others run their own launches in the same order.  All
+ * device buffers named in a request are caller-owned and must stay valid until the request
+ * is done.  The server never blocks without a bound: bos_wait and bos_server_destroy take
+ * timeouts and return BOS_ERR_TIMEOUT; no kernel waits on the host. */
 
 typedef struct bos_server bos_server;
 
@@ -379,7 +383,9 @@ typedef struct {
 bos_status_t bos_request_footprint(const bos_request* req, uint64_t* bytes);
 
 /* Create a server on `device` with an arena of mem_limit_bytes and `slots` concurrent
- * requests (1..64).  BOS_ERR_OOM if the arena cannot be allocated. */
+ * requests (1..64).  BOS_ERR_OOM if the arena cannot be allocated.  With an arena of at
+ * least 804 MiB, 201 MiB of it hold the batched Sharma adjoint's per-warp segment states;
+ * below that, forward + adjoint Sharma requests run their own launches. */
 bos_status_t bos_server_create(bos_server** out, int device, uint64_t mem_limit_bytes, int slots, int flags);
 
 /* Queue a request (descriptors are copied).  BOS_ERR_ADMISSION if its footprint exceeds
@@ -395,6 +401,11 @@ bos_status_t bos_ticket(bos_server* s, uint64_t ticket, bos_ticket_info* info);
 /* Arena size, peak arena use, queued and running requests. */
 bos_status_t bos_server_stats(bos_server* s, uint64_t* arena_bytes, uint64_t* peak_used_bytes, int* queued,
                               int* running);
+
+/* Batched launches so far: their number, the warp tiles they ran, the sum over launches of
+ * the requests each one served, and the most requests one launch served. */
+bos_status_t bos_server_batches(bos_server* s, uint64_t* launches, uint64_t* tiles, uint64_t* job_shares,
+                                int* max_jobs);
 
 /* Stop accepting requests, wait up to timeout_ns for queued and running ones, then free
  * everything.  BOS_ERR_TIMEOUT leaves the server running (call again). */

@@ -120,6 +120,7 @@ SIGNATURES = {
     "bos_wait": (_i, [_v, _u64, _u64]),
     "bos_ticket": (_i, [_v, _u64, _P(bos_ticket_info)]),
     "bos_server_stats": (_i, [_v, _P(_u64), _P(_u64), _P(_i), _P(_i)]),
+    "bos_server_batches": (_i, [_v, _P(_u64), _P(_u64), _P(_u64), _P(_i)]),
     "bos_server_destroy": (_i, [_v, _u64]),
 }
 
@@ -505,6 +506,13 @@ class Server:
         q, r = C.c_int(), C.c_int()
         check(lib().bos_server_stats(self.h, C.byref(a), C.byref(p), C.byref(q), C.byref(r)), "bos_server_stats")
         return dict(arena_bytes=a.value, peak_used_bytes=p.value, queued=q.value, running=r.value)
+
+    def batches(self) -> dict:
+        """Batched launches so far: launches, tiles, request shares, most requests per launch."""
+        a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        m = C.c_int()
+        check(lib().bos_server_batches(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(m)), "bos_server_batches")
+        return dict(launches=a.value, tiles=b.value, job_shares=c.value, max_jobs=m.value)
 
     def close(self, timeout_s: float = 600.0) -> None:
         if self.h:

@@ -329,6 +329,337 @@ __host__ __device__ constexpr size_t adj_warp_floats(int K) {
 // Floats per lane and step of the recomputed segment: (dr, dv, A, B) of Sharma's step.
 constexpr int kSegFloats = 12;
 
+// One warp tile of the Sharma adjoint: reverse every ray of the tile from its checkpoints
+// and scatter its sensitivities into the lane rows (flushed into acc as the cells change).
+template <class E, bool CONN>
+__device__ __forceinline__ void adjoint_tile(const SceneDev& S, const CkptDev& ck, const AdjDev& adj,
+                                             const CompField<E>& F, const TileShape& ts, int t, int lane,
+                                             float* rows, float* st_buf, float* acc, CellAcc& ca, double* xlum) {
+    const int nx = S.g.n[0], nxy = S.g.n[0] * S.g.n[1];
+    const int spp = S.cam.spp;
+    const int K = ck.every;
+    double* const xlb = xlum + 3;
+    double* const ybar = xlum + 6;
+    double* const drbw = xlum + 9;
+    double* const dvbw = xlum + 12;
+    double* const tpb = xlum + 15;
+    double* const nqp = xlum + 18;
+    const int sl = lane % ts.G;
+    const TilePix tp = tile_pixel(S, ts, t, lane);
+    const int px = tp.px, py = tp.py;
+    const bool valid = tp.valid;
+    for (int qs = 0; qs < ts.samples_per_lane; ++qs) {
+        const int s = ts.samples_per_lane == 1 ? sl : qs;
+        const long long slot = ((long long)t * 32 + lane) * ts.samples_per_lane + qs;
+        bool act = valid;
+        Ray R;
+        R.N = 0;
+        R.wall = false;
+        double Ib = 0.0;
+        if (act) {
+            R = ray_setup(S, px, py, s);
+            Ib = (double)adj.dLdI[(size_t)tp.out] / spp;
+        }
+        const bool act0 = act && R.wall && R.N >= 0 && Ib != 0.0;
+        // Refracted projector connection (light mode 2, one aiming round): the luminance is
+        // read at a_1 = 2 x_w - y(x_w), y the wall hit of the projector ray aimed at x_w.
+        // Pass 0 reverses that projector ray for the seed -dL/da_1 and turns its entry state
+        // into dL/d aim; pass 1 reverses the camera ray with dL/dx_w = 2 dL/da_1 + dL/d aim.
+        Ray Rp;
+        Rp.N = 0;
+        Rp.wall = false;
+        bool pact = false;
+        if constexpr (CONN) {
+            for (int a = 0; a < 3; ++a) xlum[a] = xlb[a] = ybar[a] = 0.0;
+            nqp[0] = 1.0;
+            if (act0) {
+                const float4 c0 = ck.conn[2 * slot], c1 = ck.conn[2 * slot + 1];
+                const float dxf[3] = {c0.x, c0.y, c0.z};
+                double xref[3], gL[3], q[3];
+                for (int a = 0; a < 3; ++a) {
+                    xref[a] = S.cam.pos[a] + R.tw * R.d[a];
+                    xlum[a] = xref[a] + ((double)dxf[a] - (double)(&c1.x)[a]);
+                }
+                const double Lb = Ib * (double)c0.w;
+                wall_luminance(S.L, S.w, xlum, gL);
+                for (int a = 0; a < 3; ++a) {
+                    ybar[a] = -Lb * gL[a];
+                    xlb[a] = 2.0 * Lb * gL[a];
+                    q[a] = (xref[a] - S.L.proj.pos[a]) + (double)dxf[a];
+                }
+                nqp[0] = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+                Rp = projector_setup(S, xref, dxf);
+                const bool seeded = ybar[0] != 0.0 || ybar[1] != 0.0 || ybar[2] != 0.0;
+                if (!Rp.wall) {                 // y = aim
+                    for (int a = 0; a < 3; ++a) xlb[a] += ybar[a];
+                } else if (Rp.N <= 0) {         // straight projector ray
+                    double ab[3];
+                    straight_aim_adjoint(S, Rp, nqp[0], ybar, ab);
+                    for (int a = 0; a < 3; ++a) xlb[a] += ab[a];
+                } else {
+                    pact = seeded;
+                }
+            }
+        }
+        for (int pass = CONN ? 0 : 1; pass < 2; ++pass) {
+        const bool proj = CONN && pass == 0;
+        const Ray& RR = proj ? Rp : R;
+        const double* rs = proj ? S.L.proj.pos : S.cam.pos;
+        const float4* cstate = proj ? ck.pstate : ck.state;
+        act = proj ? pact : (act0 && R.N > 0);
+        CompState st0;
+        CompConst k;
+        double eta_in = 1.0, rin[3] = {0, 0, 0};
+        if (act) comp_setup(S, F, rs, RR, st0, k, eta_in, rin);
+        const int N = act ? RR.N : 0;
+        const int nseg = (N + K - 1) / K;
+        const int nseg_max = __reduce_max_sync(0xffffffffu, (unsigned)nseg);
+        float rb[3] = {0, 0, 0}, vb[3] = {0, 0, 0}, dtb = 0.0f, lenb = 0.0f;
+        double etab = 0.0;
+        if constexpr (CONN)
+            for (int a = 0; a < 3; ++a) tpb[a] = 0.0;
+        const float dt = act ? k.dt : 0.0f;
+        BrickCache bc = {kNoKey, 0u};
+        for (int c = nseg_max - 1; c >= 0; --c) {
+            const int n0 = c * K;
+            const int n1 = min(n0 + K, N);
+            const bool seg = act && n0 < N;
+            // ---- recompute the segment from its checkpoint, keeping each step's state
+            if (seg) {
+                CompState st;
+                const float4 s0 = cstate[((size_t)c * 3 + 0) * ck.nrays + slot];
+                const float4 s1 = cstate[((size_t)c * 3 + 1) * ck.nrays + slot];
+                const float4 s2 = cstate[((size_t)c * 3 + 2) * ck.nrays + slot];
+                st.dr[0] = s0.x; st.dr[1] = s0.y; st.dr[2] = s0.z;
+                st.dv[0] = s1.x; st.dv[1] = s1.y; st.dv[2] = s1.z;
+                st.cv[0] = s2.x; st.cv[1] = s2.y; st.cv[2] = s2.z;
+                st.cr[0] = s0.w; st.cr[1] = s1.w; st.cr[2] = s2.w;
+                st.excess = 0.0f;
+                for (int a = 0; a < 3; ++a) st.U[a] = st0.U[a] + (long long)n0 * k.dU[a];
+                for (int n = n0; n < n1; ++n) {
+                    float* p = st_buf + (size_t)(n - n0) * kSegFloats * 32 + lane;
+                    p[0] = st.dr[0]; p[32] = st.dr[1]; p[64] = st.dr[2];
+                    p[96] = st.dv[0]; p[128] = st.dv[1]; p[160] = st.dv[2];
+                    float AB[6];
+                    comp_step<E, 0>(F, st, k, bc, AB);
+                    for (int q = 0; q < 6; ++q) p[192 + 32 * q] = AB[q];
+                }
+                if (c == nseg - 1) {
+                    // the lane's last segment: start from the adjoint of the wall epilogue
+                    double rN[3], vN[3], drb[3], dvb[3], lb = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        rN[a] = rin[a] + RR.ell * RR.d[a] + ((double)st.dr[a] - (double)st.cr[a]);
+                        vN[a] = eta_in * RR.d[a] + ((double)st.dv[a] - (double)st.cv[a]);
+                    }
+                    if (proj) {
+                        hit_adjoint(S, rN, vN, ybar, drb, dvb);
+                        for (int a = 0; a < 3; ++a) {
+                            drbw[a] = drb[a];
+                            dvbw[a] = dvb[a];
+                        }
+                    } else {
+                        double len_before = R.t_in + R.ell + (double)ck.excess[slot];
+                        wall_adjoint(S, rN, vN, len_before, Ib, drb, dvb, lb, CONN ? xlum : nullptr,
+                                     CONN ? xlb : nullptr);
+                    }
+                    for (int a = 0; a < 3; ++a) {
+                        rb[a] = (float)drb[a];
+                        vb[a] = (float)dvb[a];
+                    }
+                    lenb = (float)lb;
+                    etab += dvb[0] * RR.d[0] + dvb[1] * RR.d[1] + dvb[2] * RR.d[2];
+                }
+            }
+            __syncwarp();
+            const float rseg[3] = {rb[0], rb[1], rb[2]};   // rb before this segment's steps
+            // ---- reverse the segment's steps
+            const int n_hi = __reduce_max_sync(0xffffffffu, (unsigned)(seg ? n1 : 0));
+            float tps[3] = {0.0f, 0.0f, 0.0f};   // sum over the segment's stages of (t / dt_step) pb
+            for (int n = n_hi - 1; n >= n0; --n) {
+                const bool a_ = seg && n < n1;
+                // the step's state and stage terms from the recompute: all three stage
+                // points are known, so each stage is evaluated (value and gradient) when
+                // its adjoint is formed, in the order 3, 2, 1
+                float dr[3] = {0, 0, 0}, dvv[3] = {0, 0, 0}, A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+                if (a_) {
+                    const float* p = st_buf + (size_t)(n - n0) * kSegFloats * 32 + lane;
+                    dr[0] = p[0]; dr[1] = p[32]; dr[2] = p[64];
+                    dvv[0] = p[96]; dvv[1] = p[128]; dvv[2] = p[160];
+                    A[0] = p[192]; A[1] = p[224]; A[2] = p[256];
+                    B[0] = p[288]; B[1] = p[320]; B[2] = p[352];
+                }
+                long long U[3];
+                for (int a = 0; a < 3; ++a) U[a] = st0.U[a] + (long long)n * k.dU[a];
+                float u[3] = {0, 0, 0};
+                if (a_) {
+                    float inc[3], nn = 0.0f;
+                    for (int a = 0; a < 3; ++a) {
+                        inc[a] = k.dS[a] + dt * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
+                        nn += inc[a] * inc[a];
+                    }
+                    const float rn = rsqrtf(nn);
+                    for (int a = 0; a < 3; ++a) {
+                        u[a] = inc[a] * rn;             // unit step direction: d|r_{n+1} - r_n|
+                        rb[a] += lenb * u[a];
+                    }
+                }
+                // r' = r + dt (v + (A + 2B)/6),  v' = v + (A + 4B + C)/6
+                float Ab[3], Bb[3], Cb[3], rn_[3], vn_[3];
+                for (int a = 0; a < 3; ++a) {
+                    Ab[a] = (dt * (1.0f / 6.0f)) * rb[a] + vb[a] * (1.0f / 6.0f);
+                    Bb[a] = (dt * (1.0f / 3.0f)) * rb[a] + vb[a] * (4.0f / 6.0f);
+                    Cb[a] = vb[a] * (1.0f / 6.0f);
+                    rn_[a] = rb[a];
+                    vn_[a] = vb[a] + dt * rb[a];
+                    dtb += rb[a] * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
+                }
+                float Db[3], pb[3] = {0, 0, 0}, D[3] = {0, 0, 0}, q[3];
+                long long Us[3];
+                Stage s;
+                float4 Q3 = make_float4(0, 0, 0, 0), Q2 = Q3, Q1 = Q3;
+                uint32_t key3 = kNoKey, key2 = kNoKey, key1 = kNoKey;
+                float cf3[3] = {0, 0, 0}, cf2[3] = {0, 0, 0}, cf1[3] = {0, 0, 0};
+                // C = dt D(p3),  p3 = S(n+1) + dr + dt dv + dt/2 B
+                if (a_) {
+                    for (int a = 0; a < 3; ++a) {
+                        q[a] = dr[a] + dt * dvv[a] + (0.5f * dt) * B[a];
+                        Us[a] = U[a] + k.dU[a];
+                    }
+                    stage_eval(F, Us, q, bc, s);
+                    rhs_from(s.ig, D);
+                }
+                for (int a = 0; a < 3; ++a) {
+                    dtb += Cb[a] * D[a];
+                    Db[a] = dt * Cb[a];
+                }
+                if (a_) {
+                    rhs_adjoint(F, s.ig, Db, pb, Q3);
+                    key3 = s.key;
+                    for (int a = 0; a < 3; ++a) cf3[a] = s.cf[a];
+                }
+                if constexpr (CONN) {
+                    const float tn = (float)(n + 1 - n0);
+                    for (int a = 0; a < 3; ++a) tps[a] += tn * pb[a];
+                }
+                for (int a = 0; a < 3; ++a) {
+                    rn_[a] += pb[a];
+                    vn_[a] += dt * pb[a];
+                    Bb[a] += (0.5f * dt) * pb[a];
+                    dtb += pb[a] * (dvv[a] + 0.5f * B[a]);
+                }
+                // B = dt D(p2),  p2 = S(n+1/2) + dr + dt/2 dv + dt/8 A
+                if (a_) {
+                    for (int a = 0; a < 3; ++a) {
+                        q[a] = dr[a] + (0.5f * dt) * dvv[a] + (0.125f * dt) * A[a];
+                        Us[a] = U[a] + k.dUh[a];
+                    }
+                    stage_eval(F, Us, q, bc, s);
+                    rhs_from(s.ig, D);
+                }
+                for (int a = 0; a < 3; ++a) {
+                    dtb += Bb[a] * D[a];
+                    Db[a] = dt * Bb[a];
+                }
+                if (a_) {
+                    rhs_adjoint(F, s.ig, Db, pb, Q2);
+                    key2 = s.key;
+                    for (int a = 0; a < 3; ++a) cf2[a] = s.cf[a];
+                }
+                if constexpr (CONN) {
+                    const float tn = (float)(n - n0) + 0.5f;
+                    for (int a = 0; a < 3; ++a) tps[a] += tn * pb[a];
+                }
+                for (int a = 0; a < 3; ++a) {
+                    rn_[a] += pb[a];
+                    vn_[a] += (0.5f * dt) * pb[a];
+                    Ab[a] += (0.125f * dt) * pb[a];
+                    dtb += pb[a] * (0.5f * dvv[a] + 0.125f * A[a]);
+                }
+                // A = dt D(p1),  p1 = S(n) + dr
+                if (a_) {
+                    stage_eval(F, U, dr, bc, s);
+                    rhs_from(s.ig, D);
+                }
+                for (int a = 0; a < 3; ++a) {
+                    dtb += Ab[a] * D[a];
+                    Db[a] = dt * Ab[a];
+                }
+                if (a_) {
+                    rhs_adjoint(F, s.ig, Db, pb, Q1);
+                    key1 = s.key;
+                    for (int a = 0; a < 3; ++a) cf1[a] = s.cf[a];
+                }
+                if constexpr (CONN) {
+                    const float tn = (float)(n - n0);
+                    for (int a = 0; a < 3; ++a) tps[a] += tn * pb[a];
+                }
+                if (a_) {
+                    for (int a = 0; a < 3; ++a) {
+                        rb[a] = rn_[a] + pb[a] - lenb * u[a];
+                        vb[a] = vn_[a];
+                    }
+                }
+                // scatter the three stages: one pass over the lane's cell row for the
+                // stages in stage 3's cell, then the others (a step that crosses a face)
+#ifndef BOS_ADJ_ONE_PASS
+#define BOS_ADJ_ONE_PASS 1
+#endif
+                const bool same2 = BOS_ADJ_ONE_PASS && key2 == key3, same1 = BOS_ADJ_ONE_PASS && key1 == key3;
+                accumulate3(rows, a_, key3, cf3, Q3, same2, cf2, Q2, same1, cf1, Q1, ca, acc, nx, nxy);
+                accumulate(rows, a_ && !same2, key2, cf2, Q2, ca, acc, nx, nxy);
+                accumulate(rows, a_ && !same1, key1, cf1, Q1, ca, acc, nx, nxy);
+            }
+            if constexpr (CONN) {
+                if (proj && seg)
+                    for (int a = 0; a < 3; ++a) tpb[a] += (double)tps[a] + (double)n0 * (double)(rb[a] - rseg[a]);
+            }
+            __syncwarp();
+        }
+        // ---- entry: v0 = eta_in d and dt = ell / (N eta_in), eta_in = 1 + deta(r_in)
+        int ci[3] = {0, 0, 0};
+        float cf[3] = {0, 0, 0};
+        if (act) {
+            etab -= (double)dtb * (double)dt / eta_in;
+            const float zero[3] = {0, 0, 0};
+            comp_cell(F, st0.U, zero, ci, cf);
+        }
+        accumulate(rows, act, cell_key_of(F, ci), cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), ca, acc, nx, nxy);
+        if constexpr (CONN) {
+            if (proj && act) {
+                // the projector ray's entry state as a function of its aim: r_in = P + t_in d,
+                // v0 = eta_in d (base of v_N), straight step (ell/N) d, dt = ell / (N eta_in),
+                // eta_in = 1 + deta(r_in), d = q / |q|, t_in and t_end on slab faces or the wall
+                const double Nd = (double)RR.N, ds = RR.ell / Nd;
+                Stage se;
+                const float zero[3] = {0, 0, 0};
+                stage_eval(F, st0.U, zero, bc, se);
+                const double ge[3] = {(double)se.ig.d0.x * (double)F.inv_h[0], (double)se.ig.d1.x * (double)F.inv_h[1],
+                                      (double)se.ig.d2.x * (double)F.inv_h[2]};
+                double dSb[3], rbi[3], db[3];
+                for (int a = 0; a < 3; ++a) {
+                    dSb[a] = tpb[a] + Nd * drbw[a];
+                    rbi[a] = (double)rb[a] + etab * ge[a];
+                    db[a] = eta_in * dvbw[a] + ds * dSb[a] + RR.t_in * rbi[a];
+                }
+                const double ellb = (double)dtb / (Nd * eta_in) +
+                                    (RR.d[0] * dSb[0] + RR.d[1] * dSb[1] + RR.d[2] * dSb[2]) / Nd;
+                const double tinb = RR.d[0] * rbi[0] + RR.d[1] * rbi[1] + RR.d[2] * rbi[2] - ellb;
+                if (RR.in_axis >= 0) db[RR.in_axis] += tinb * (-RR.t_in / RR.d[RR.in_axis]);
+                if (RR.out_axis == 3) {
+                    const double den = RR.d[0] * S.w.normal[0] + RR.d[1] * S.w.normal[1] + RR.d[2] * S.w.normal[2];
+                    for (int a = 0; a < 3; ++a) db[a] += ellb * (-RR.tw * S.w.normal[a] / den);
+                } else {
+                    const int oa = RR.out_axis;
+                    db[oa] += ellb * (-(RR.t_in + RR.ell) / RR.d[oa]);
+                }
+                const double dd = db[0] * RR.d[0] + db[1] * RR.d[1] + db[2] * RR.d[2];
+                for (int a = 0; a < 3; ++a) xlb[a] += (db[a] - dd * RR.d[a]) / nqp[0];
+            }
+        }
+        }   // passes
+    }
+}
+
 template <class E, bool CONN_T>
 __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
     constexpr bool CONN = CONN_T;
@@ -340,12 +671,6 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
     // through the hot loop.
     __shared__ double conn_sh[CONN ? kAdjWarps * 32 * kConnDoubles : 1];
     double* const xlum = conn_sh + (CONN ? (warp * 32 + lane) * kConnDoubles : 0);
-    double* const xlb = xlum + 3;
-    double* const ybar = xlum + 6;
-    double* const drbw = xlum + 9;
-    double* const dvbw = xlum + 12;
-    double* const tpb = xlum + 15;
-    double* const nqp = xlum + 18;
     const int K = ck.every;
     float* rows = reinterpret_cast<float*>(smem4) + (size_t)warp * adj_warp_floats(K);      // [32][kRow]
     // [K][12][32] step states and stage terms (dr, dv, A, B) of the segment being reversed
@@ -353,9 +678,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
     float* st_buf = adj.seg + ((size_t)blockIdx.x * kAdjWarps + warp) * ((size_t)K * kSegFloats * 32);
     const CompField<E> F = {static_cast<const E*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
                             {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
-    const int nx = S.g.n[0], nxy = S.g.n[0] * S.g.n[1];
-    const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
-    const TileShape ts = tile_shape(W, H, spp);
+    const TileShape ts = tile_shape(S.cam.width, S.cam.height, S.cam.spp);
     const int ntiles = tile_count(S, ts);
     float* acc = reinterpret_cast<float*>(adj.acc);
     {
@@ -364,328 +687,14 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
     }
     __syncwarp();
     CellAcc ca = {kNoKey};
-
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= ntiles) break;
-        const int sl = lane % ts.G;
-        const TilePix tp = tile_pixel(S, ts, t, lane);
-        const int px = tp.px, py = tp.py;
-        const bool valid = tp.valid;
-        for (int qs = 0; qs < ts.samples_per_lane; ++qs) {
-            const int s = ts.samples_per_lane == 1 ? sl : qs;
-            const long long slot = ((long long)t * 32 + lane) * ts.samples_per_lane + qs;
-            bool act = valid;
-            Ray R;
-            R.N = 0;
-            R.wall = false;
-            double Ib = 0.0;
-            if (act) {
-                R = ray_setup(S, px, py, s);
-                Ib = (double)adj.dLdI[(size_t)tp.out] / spp;
-            }
-            const bool act0 = act && R.wall && R.N >= 0 && Ib != 0.0;
-            // Refracted projector connection (light mode 2, one aiming round): the luminance is
-            // read at a_1 = 2 x_w - y(x_w), y the wall hit of the projector ray aimed at x_w.
-            // Pass 0 reverses that projector ray for the seed -dL/da_1 and turns its entry state
-            // into dL/d aim; pass 1 reverses the camera ray with dL/dx_w = 2 dL/da_1 + dL/d aim.
-            Ray Rp;
-            Rp.N = 0;
-            Rp.wall = false;
-            bool pact = false;
-            if constexpr (CONN) {
-                for (int a = 0; a < 3; ++a) xlum[a] = xlb[a] = ybar[a] = 0.0;
-                nqp[0] = 1.0;
-                if (act0) {
-                    const float4 c0 = ck.conn[2 * slot], c1 = ck.conn[2 * slot + 1];
-                    const float dxf[3] = {c0.x, c0.y, c0.z};
-                    double xref[3], gL[3], q[3];
-                    for (int a = 0; a < 3; ++a) {
-                        xref[a] = S.cam.pos[a] + R.tw * R.d[a];
-                        xlum[a] = xref[a] + ((double)dxf[a] - (double)(&c1.x)[a]);
-                    }
-                    const double Lb = Ib * (double)c0.w;
-                    wall_luminance(S.L, S.w, xlum, gL);
-                    for (int a = 0; a < 3; ++a) {
-                        ybar[a] = -Lb * gL[a];
-                        xlb[a] = 2.0 * Lb * gL[a];
-                        q[a] = (xref[a] - S.L.proj.pos[a]) + (double)dxf[a];
-                    }
-                    nqp[0] = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
-                    Rp = projector_setup(S, xref, dxf);
-                    const bool seeded = ybar[0] != 0.0 || ybar[1] != 0.0 || ybar[2] != 0.0;
-                    if (!Rp.wall) {                 // y = aim
-                        for (int a = 0; a < 3; ++a) xlb[a] += ybar[a];
-                    } else if (Rp.N <= 0) {         // straight projector ray
-                        double ab[3];
-                        straight_aim_adjoint(S, Rp, nqp[0], ybar, ab);
-                        for (int a = 0; a < 3; ++a) xlb[a] += ab[a];
-                    } else {
-                        pact = seeded;
-                    }
-                }
-            }
-            for (int pass = CONN ? 0 : 1; pass < 2; ++pass) {
-            const bool proj = CONN && pass == 0;
-            const Ray& RR = proj ? Rp : R;
-            const double* rs = proj ? S.L.proj.pos : S.cam.pos;
-            const float4* cstate = proj ? ck.pstate : ck.state;
-            act = proj ? pact : (act0 && R.N > 0);
-            CompState st0;
-            CompConst k;
-            double eta_in = 1.0, rin[3] = {0, 0, 0};
-            if (act) comp_setup(S, F, rs, RR, st0, k, eta_in, rin);
-            const int N = act ? RR.N : 0;
-            const int nseg = (N + K - 1) / K;
-            const int nseg_max = __reduce_max_sync(0xffffffffu, (unsigned)nseg);
-            float rb[3] = {0, 0, 0}, vb[3] = {0, 0, 0}, dtb = 0.0f, lenb = 0.0f;
-            double etab = 0.0;
-            if constexpr (CONN)
-                for (int a = 0; a < 3; ++a) tpb[a] = 0.0;
-            const float dt = act ? k.dt : 0.0f;
-            BrickCache bc = {kNoKey, 0u};
-            for (int c = nseg_max - 1; c >= 0; --c) {
-                const int n0 = c * K;
-                const int n1 = min(n0 + K, N);
-                const bool seg = act && n0 < N;
-                // ---- recompute the segment from its checkpoint, keeping each step's state
-                if (seg) {
-                    CompState st;
-                    const float4 s0 = cstate[((size_t)c * 3 + 0) * ck.nrays + slot];
-                    const float4 s1 = cstate[((size_t)c * 3 + 1) * ck.nrays + slot];
-                    const float4 s2 = cstate[((size_t)c * 3 + 2) * ck.nrays + slot];
-                    st.dr[0] = s0.x; st.dr[1] = s0.y; st.dr[2] = s0.z;
-                    st.dv[0] = s1.x; st.dv[1] = s1.y; st.dv[2] = s1.z;
-                    st.cv[0] = s2.x; st.cv[1] = s2.y; st.cv[2] = s2.z;
-                    st.cr[0] = s0.w; st.cr[1] = s1.w; st.cr[2] = s2.w;
-                    st.excess = 0.0f;
-                    for (int a = 0; a < 3; ++a) st.U[a] = st0.U[a] + (long long)n0 * k.dU[a];
-                    for (int n = n0; n < n1; ++n) {
-                        float* p = st_buf + (size_t)(n - n0) * kSegFloats * 32 + lane;
-                        p[0] = st.dr[0]; p[32] = st.dr[1]; p[64] = st.dr[2];
-                        p[96] = st.dv[0]; p[128] = st.dv[1]; p[160] = st.dv[2];
-                        float AB[6];
-                        comp_step<E, 0>(F, st, k, bc, AB);
-                        for (int q = 0; q < 6; ++q) p[192 + 32 * q] = AB[q];
-                    }
-                    if (c == nseg - 1) {
-                        // the lane's last segment: start from the adjoint of the wall epilogue
-                        double rN[3], vN[3], drb[3], dvb[3], lb = 0.0;
-                        for (int a = 0; a < 3; ++a) {
-                            rN[a] = rin[a] + RR.ell * RR.d[a] + ((double)st.dr[a] - (double)st.cr[a]);
-                            vN[a] = eta_in * RR.d[a] + ((double)st.dv[a] - (double)st.cv[a]);
-                        }
-                        if (proj) {
-                            hit_adjoint(S, rN, vN, ybar, drb, dvb);
-                            for (int a = 0; a < 3; ++a) {
-                                drbw[a] = drb[a];
-                                dvbw[a] = dvb[a];
-                            }
-                        } else {
-                            double len_before = R.t_in + R.ell + (double)ck.excess[slot];
-                            wall_adjoint(S, rN, vN, len_before, Ib, drb, dvb, lb, CONN ? xlum : nullptr,
-                                         CONN ? xlb : nullptr);
-                        }
-                        for (int a = 0; a < 3; ++a) {
-                            rb[a] = (float)drb[a];
-                            vb[a] = (float)dvb[a];
-                        }
-                        lenb = (float)lb;
-                        etab += dvb[0] * RR.d[0] + dvb[1] * RR.d[1] + dvb[2] * RR.d[2];
-                    }
-                }
-                __syncwarp();
-                const float rseg[3] = {rb[0], rb[1], rb[2]};   // rb before this segment's steps
-                // ---- reverse the segment's steps
-                const int n_hi = __reduce_max_sync(0xffffffffu, (unsigned)(seg ? n1 : 0));
-                float tps[3] = {0.0f, 0.0f, 0.0f};   // sum over the segment's stages of (t / dt_step) pb
-                for (int n = n_hi - 1; n >= n0; --n) {
-                    const bool a_ = seg && n < n1;
-                    // the step's state and stage terms from the recompute: all three stage
-                    // points are known, so each stage is evaluated (value and gradient) when
-                    // its adjoint is formed, in the order 3, 2, 1
-                    float dr[3] = {0, 0, 0}, dvv[3] = {0, 0, 0}, A[3] = {0, 0, 0}, B[3] = {0, 0, 0};
-                    if (a_) {
-                        const float* p = st_buf + (size_t)(n - n0) * kSegFloats * 32 + lane;
-                        dr[0] = p[0]; dr[1] = p[32]; dr[2] = p[64];
-                        dvv[0] = p[96]; dvv[1] = p[128]; dvv[2] = p[160];
-                        A[0] = p[192]; A[1] = p[224]; A[2] = p[256];
-                        B[0] = p[288]; B[1] = p[320]; B[2] = p[352];
-                    }
-                    long long U[3];
-                    for (int a = 0; a < 3; ++a) U[a] = st0.U[a] + (long long)n * k.dU[a];
-                    float u[3] = {0, 0, 0};
-                    if (a_) {
-                        float inc[3], nn = 0.0f;
-                        for (int a = 0; a < 3; ++a) {
-                            inc[a] = k.dS[a] + dt * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
-                            nn += inc[a] * inc[a];
-                        }
-                        const float rn = rsqrtf(nn);
-                        for (int a = 0; a < 3; ++a) {
-                            u[a] = inc[a] * rn;             // unit step direction: d|r_{n+1} - r_n|
-                            rb[a] += lenb * u[a];
-                        }
-                    }
-                    // r' = r + dt (v + (A + 2B)/6),  v' = v + (A + 4B + C)/6
-                    float Ab[3], Bb[3], Cb[3], rn_[3], vn_[3];
-                    for (int a = 0; a < 3; ++a) {
-                        Ab[a] = (dt * (1.0f / 6.0f)) * rb[a] + vb[a] * (1.0f / 6.0f);
-                        Bb[a] = (dt * (1.0f / 3.0f)) * rb[a] + vb[a] * (4.0f / 6.0f);
-                        Cb[a] = vb[a] * (1.0f / 6.0f);
-                        rn_[a] = rb[a];
-                        vn_[a] = vb[a] + dt * rb[a];
-                        dtb += rb[a] * (dvv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
-                    }
-                    float Db[3], pb[3] = {0, 0, 0}, D[3] = {0, 0, 0}, q[3];
-                    long long Us[3];
-                    Stage s;
-                    float4 Q3 = make_float4(0, 0, 0, 0), Q2 = Q3, Q1 = Q3;
-                    uint32_t key3 = kNoKey, key2 = kNoKey, key1 = kNoKey;
-                    float cf3[3] = {0, 0, 0}, cf2[3] = {0, 0, 0}, cf1[3] = {0, 0, 0};
-                    // C = dt D(p3),  p3 = S(n+1) + dr + dt dv + dt/2 B
-                    if (a_) {
-                        for (int a = 0; a < 3; ++a) {
-                            q[a] = dr[a] + dt * dvv[a] + (0.5f * dt) * B[a];
-                            Us[a] = U[a] + k.dU[a];
-                        }
-                        stage_eval(F, Us, q, bc, s);
-                        rhs_from(s.ig, D);
-                    }
-                    for (int a = 0; a < 3; ++a) {
-                        dtb += Cb[a] * D[a];
-                        Db[a] = dt * Cb[a];
-                    }
-                    if (a_) {
-                        rhs_adjoint(F, s.ig, Db, pb, Q3);
-                        key3 = s.key;
-                        for (int a = 0; a < 3; ++a) cf3[a] = s.cf[a];
-                    }
-                    if constexpr (CONN) {
-                        const float tn = (float)(n + 1 - n0);
-                        for (int a = 0; a < 3; ++a) tps[a] += tn * pb[a];
-                    }
-                    for (int a = 0; a < 3; ++a) {
-                        rn_[a] += pb[a];
-                        vn_[a] += dt * pb[a];
-                        Bb[a] += (0.5f * dt) * pb[a];
-                        dtb += pb[a] * (dvv[a] + 0.5f * B[a]);
-                    }
-                    // B = dt D(p2),  p2 = S(n+1/2) + dr + dt/2 dv + dt/8 A
-                    if (a_) {
-                        for (int a = 0; a < 3; ++a) {
-                            q[a] = dr[a] + (0.5f * dt) * dvv[a] + (0.125f * dt) * A[a];
-                            Us[a] = U[a] + k.dUh[a];
-                        }
-                        stage_eval(F, Us, q, bc, s);
-                        rhs_from(s.ig, D);
-                    }
-                    for (int a = 0; a < 3; ++a) {
-                        dtb += Bb[a] * D[a];
-                        Db[a] = dt * Bb[a];
-                    }
-                    if (a_) {
-                        rhs_adjoint(F, s.ig, Db, pb, Q2);
-                        key2 = s.key;
-                        for (int a = 0; a < 3; ++a) cf2[a] = s.cf[a];
-                    }
-                    if constexpr (CONN) {
-                        const float tn = (float)(n - n0) + 0.5f;
-                        for (int a = 0; a < 3; ++a) tps[a] += tn * pb[a];
-                    }
-                    for (int a = 0; a < 3; ++a) {
-                        rn_[a] += pb[a];
-                        vn_[a] += (0.5f * dt) * pb[a];
-                        Ab[a] += (0.125f * dt) * pb[a];
-                        dtb += pb[a] * (0.5f * dvv[a] + 0.125f * A[a]);
-                    }
-                    // A = dt D(p1),  p1 = S(n) + dr
-                    if (a_) {
-                        stage_eval(F, U, dr, bc, s);
-                        rhs_from(s.ig, D);
-                    }
-                    for (int a = 0; a < 3; ++a) {
-                        dtb += Ab[a] * D[a];
-                        Db[a] = dt * Ab[a];
-                    }
-                    if (a_) {
-                        rhs_adjoint(F, s.ig, Db, pb, Q1);
-                        key1 = s.key;
-                        for (int a = 0; a < 3; ++a) cf1[a] = s.cf[a];
-                    }
-                    if constexpr (CONN) {
-                        const float tn = (float)(n - n0);
-                        for (int a = 0; a < 3; ++a) tps[a] += tn * pb[a];
-                    }
-                    if (a_) {
-                        for (int a = 0; a < 3; ++a) {
-                            rb[a] = rn_[a] + pb[a] - lenb * u[a];
-                            vb[a] = vn_[a];
-                        }
-                    }
-                    // scatter the three stages: one pass over the lane's cell row for the
-                    // stages in stage 3's cell, then the others (a step that crosses a face)
-#ifndef BOS_ADJ_ONE_PASS
-#define BOS_ADJ_ONE_PASS 1
-#endif
-                    const bool same2 = BOS_ADJ_ONE_PASS && key2 == key3, same1 = BOS_ADJ_ONE_PASS && key1 == key3;
-                    accumulate3(rows, a_, key3, cf3, Q3, same2, cf2, Q2, same1, cf1, Q1, ca, acc, nx, nxy);
-                    accumulate(rows, a_ && !same2, key2, cf2, Q2, ca, acc, nx, nxy);
-                    accumulate(rows, a_ && !same1, key1, cf1, Q1, ca, acc, nx, nxy);
-                }
-                if constexpr (CONN) {
-                    if (proj && seg)
-                        for (int a = 0; a < 3; ++a) tpb[a] += (double)tps[a] + (double)n0 * (double)(rb[a] - rseg[a]);
-                }
-                __syncwarp();
-            }
-            // ---- entry: v0 = eta_in d and dt = ell / (N eta_in), eta_in = 1 + deta(r_in)
-            int ci[3] = {0, 0, 0};
-            float cf[3] = {0, 0, 0};
-            if (act) {
-                etab -= (double)dtb * (double)dt / eta_in;
-                const float zero[3] = {0, 0, 0};
-                comp_cell(F, st0.U, zero, ci, cf);
-            }
-            accumulate(rows, act, cell_key_of(F, ci), cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), ca, acc, nx, nxy);
-            if constexpr (CONN) {
-                if (proj && act) {
-                    // the projector ray's entry state as a function of its aim: r_in = P + t_in d,
-                    // v0 = eta_in d (base of v_N), straight step (ell/N) d, dt = ell / (N eta_in),
-                    // eta_in = 1 + deta(r_in), d = q / |q|, t_in and t_end on slab faces or the wall
-                    const double Nd = (double)RR.N, ds = RR.ell / Nd;
-                    Stage se;
-                    const float zero[3] = {0, 0, 0};
-                    stage_eval(F, st0.U, zero, bc, se);
-                    const double ge[3] = {(double)se.ig.d0.x * (double)F.inv_h[0], (double)se.ig.d1.x * (double)F.inv_h[1],
-                                          (double)se.ig.d2.x * (double)F.inv_h[2]};
-                    double dSb[3], rbi[3], db[3];
-                    for (int a = 0; a < 3; ++a) {
-                        dSb[a] = tpb[a] + Nd * drbw[a];
-                        rbi[a] = (double)rb[a] + etab * ge[a];
-                        db[a] = eta_in * dvbw[a] + ds * dSb[a] + RR.t_in * rbi[a];
-                    }
-                    const double ellb = (double)dtb / (Nd * eta_in) +
-                                        (RR.d[0] * dSb[0] + RR.d[1] * dSb[1] + RR.d[2] * dSb[2]) / Nd;
-                    const double tinb = RR.d[0] * rbi[0] + RR.d[1] * rbi[1] + RR.d[2] * rbi[2] - ellb;
-                    if (RR.in_axis >= 0) db[RR.in_axis] += tinb * (-RR.t_in / RR.d[RR.in_axis]);
-                    if (RR.out_axis == 3) {
-                        const double den = RR.d[0] * S.w.normal[0] + RR.d[1] * S.w.normal[1] + RR.d[2] * S.w.normal[2];
-                        for (int a = 0; a < 3; ++a) db[a] += ellb * (-RR.tw * S.w.normal[a] / den);
-                    } else {
-                        const int oa = RR.out_axis;
-                        db[oa] += ellb * (-(RR.t_in + RR.ell) / RR.d[oa]);
-                    }
-                    const double dd = db[0] * RR.d[0] + db[1] * RR.d[1] + db[2] * RR.d[2];
-                    for (int a = 0; a < 3; ++a) xlb[a] += (db[a] - dd * RR.d[a]) / nqp[0];
-                }
-            }
-            }   // passes
-        }
+        adjoint_tile<E, CONN>(S, ck, adj, F, ts, t, lane, rows, st_buf, acc, ca, xlum);
     }
-    flush_rows(rows, ca.key != kNoKey, ca, acc, nx, nxy);
+    flush_rows(rows, ca.key != kNoKey, ca, acc, S.g.n[0], S.g.n[0] * S.g.n[1]);
 }
 
 // Adjoint of quasi-linear tracing (Sec. 2.2).  The stage points lie on the straight
@@ -720,6 +729,139 @@ __device__ __forceinline__ float4 line_corner_record(const float4 v, const float
     return make_float4(Db[0] * v.y + Db[1] * v.z + Db[2] * v.w, eta * Db[0], eta * Db[1], eta * Db[2]);
 }
 
+// One warp tile of the quasi-linear adjoint (one forward-order sweep per ray).
+template <class E>
+__device__ __forceinline__ void adjoint_quasi_tile(const SceneDev& S, const CkptDev& ck, const AdjDev& adj,
+                                                   const CompField<E>& F, const TileShape& ts, int t, int lane,
+                                                   float* rows, float* acc, CellAcc& ca) {
+    const int nx = S.g.n[0], nxy = S.g.n[0] * S.g.n[1];
+    const int spp = S.cam.spp;
+    const float zero[3] = {0.0f, 0.0f, 0.0f};
+    const int sl = lane % ts.G;
+    const TilePix tp = tile_pixel(S, ts, t, lane);
+    const int px = tp.px, py = tp.py;
+    const bool valid = tp.valid;
+    for (int qs = 0; qs < ts.samples_per_lane; ++qs) {
+        const int s = ts.samples_per_lane == 1 ? sl : qs;
+        const long long slot = ((long long)t * 32 + lane) * ts.samples_per_lane + qs;
+        bool act = valid;
+        Ray R;
+        R.N = 0;
+        R.wall = false;
+        double Ib = 0.0;
+        if (act) {
+            R = ray_setup(S, px, py, s);
+            Ib = (double)adj.dLdI[(size_t)tp.out] / spp;
+        }
+        act = act && R.wall && R.N > 0 && Ib != 0.0;
+        CompState st;
+        CompConst k;
+        double eta_in = 1.0, rin[3] = {0, 0, 0};
+        float rb[3] = {0, 0, 0}, vbN[3] = {0, 0, 0}, lenb = 0.0f, usum[3] = {0, 0, 0};
+        double etab = 0.0;
+        if (act) {
+            comp_setup(S, F, S.cam.pos, R, st, k, eta_in, rin);
+            const float4 s0 = ck.state[0 * ck.nrays + slot];
+            const float4 s1 = ck.state[1 * ck.nrays + slot];
+            const float4 s2 = ck.state[2 * ck.nrays + slot];
+            usum[0] = s1.w;
+            usum[1] = s2.x;
+            usum[2] = s2.y;
+            double rN[3], vN[3], drb[3], dvb[3], lb;
+            const float drN[3] = {s0.x, s0.y, s0.z}, dvN[3] = {s1.x, s1.y, s1.z};
+            for (int a = 0; a < 3; ++a) {
+                rN[a] = rin[a] + R.ell * R.d[a] + (double)drN[a];
+                vN[a] = eta_in * R.d[a] + (double)dvN[a];
+            }
+            wall_adjoint(S, rN, vN, R.t_in + R.ell + (double)s0.w, Ib, drb, dvb, lb);
+            for (int a = 0; a < 3; ++a) {
+                rb[a] = (float)drb[a];
+                vbN[a] = (float)dvb[a];
+            }
+            lenb = (float)lb;
+            etab = dvb[0] * R.d[0] + dvb[1] * R.d[1] + dvb[2] * R.d[2];
+        }
+        const int N = act ? R.N : 0;
+        const int n_max = __reduce_max_sync(0xffffffffu, (unsigned)N);
+        const float dt = act ? k.dt : 0.0f;
+        BrickCache bc = {kNoKey, 0u};
+        // the start sample of step 0
+        LineSample p0 = {};
+        float A[3] = {0, 0, 0}, dv[3] = {0, 0, 0}, prefix[3] = {0, 0, 0}, carry[3] = {0, 0, 0}, dtb = 0.0f;
+        if (act) {
+            line_sample(F, st.U, bc, p0);
+            float D[3];
+            rhs_of(p0.v, D);
+            for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
+        }
+        for (int n = 0; n < n_max; ++n) {
+            const bool a_ = act && n < N;
+            LineSample pm = {}, pe = {};
+            float B[3] = {0, 0, 0}, C[3] = {0, 0, 0}, u[3] = {0, 0, 0}, Dm[3] = {0, 0, 0}, De[3] = {0, 0, 0};
+            float Db0[3] = {0, 0, 0}, Dbm[3] = {0, 0, 0};
+            if (a_) {
+                long long U2[3], U3[3];
+                for (int a = 0; a < 3; ++a) {
+                    U2[a] = st.U[a] + (long long)n * k.dU[a] + k.dUh[a];
+                    U3[a] = st.U[a] + (long long)(n + 1) * k.dU[a];
+                }
+                line_sample(F, U2, bc, pm);
+                rhs_of(pm.v, Dm);
+                line_sample(F, U3, bc, pe);
+                rhs_of(pe.v, De);
+                float inc[3], nn = 0.0f;
+                for (int a = 0; a < 3; ++a) {
+                    B[a] = dt * Dm[a];
+                    C[a] = dt * De[a];
+                    inc[a] = dt * (dv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
+                    const float w = k.dS[a] + inc[a];
+                    u[a] = w;
+                    nn += w * w;
+                }
+                const float rn = rsqrtf(nn);
+                const float rem = (float)(N - n - 1);
+                for (int a = 0; a < 3; ++a) {
+                    u[a] *= rn;
+                    prefix[a] += u[a];
+                    const float rbp = rb[a] + lenb * u[a];                       // adjoint of r_{n+1}
+                    const float vb1 = vbN[a] + dt * rem * rb[a] + dt * lenb * (usum[a] - prefix[a]);
+                    const float Ab = (dt * (1.0f / 6.0f)) * rbp + vb1 * (1.0f / 6.0f);
+                    const float Bb = (dt * (1.0f / 3.0f)) * rbp + vb1 * (4.0f / 6.0f);
+                    const float Cb = vb1 * (1.0f / 6.0f);
+                    dtb += rbp * (dv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f)) + Ab * (A[a] / dt) + Bb * Dm[a] +
+                           Cb * De[a];
+                    Db0[a] = carry[a] + dt * Ab;      // start sample: this step's A and the previous C
+                    Dbm[a] = dt * Bb;
+                    carry[a] = dt * Cb;
+                    dv[a] += (A[a] + 4.0f * B[a] + C[a]) * (1.0f / 6.0f);
+                    A[a] = C[a];
+                }
+            }
+            float4 Q = make_float4(0, 0, 0, 0), Qm = make_float4(0, 0, 0, 0);
+            if (a_) {
+                Q = line_corner_record(p0.v, Db0);
+                Qm = line_corner_record(pm.v, Dbm);
+            }
+            // the step's two samples share a cell more often than not: one row update
+            const bool same = a_ && pm.key == p0.key;
+            accumulate_dual(rows, a_, p0.key, p0.cf, Q, same, pm.cf, Qm, ca, acc, nx, nxy);
+            accumulate(rows, a_ && !same, pm.key, pm.cf, Qm, ca, acc, nx, nxy);
+            if (a_) p0 = pe;
+        }
+        // the end sample of the last step, then eta_in = 1 + deta(r_in)
+        float4 Q = make_float4(0, 0, 0, 0);
+        if (act) Q = line_corner_record(p0.v, carry);
+        accumulate(rows, act, p0.key, p0.cf, Q, ca, acc, nx, nxy);
+        int ci[3] = {0, 0, 0};
+        float cf[3] = {0, 0, 0};
+        if (act) {
+            etab -= (double)dtb * (double)dt / eta_in;
+            comp_cell(F, st.U, zero, ci, cf);
+        }
+        accumulate(rows, act, cell_key_of(F, ci), cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), ca, acc, nx, nxy);
+    }
+}
+
 template <class E, int MINB>
 __global__ void __launch_bounds__(kAdjWarps * 32, MINB)
     adjoint_quasi_kernel(SceneDev S, CkptDev ck, AdjDev adj, WorkDev wk) {
@@ -733,144 +875,18 @@ __global__ void __launch_bounds__(kAdjWarps * 32, MINB)
     __syncwarp();
     const CompField<E> F = {static_cast<const E*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
                             {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
-    const int nx = S.g.n[0], nxy = S.g.n[0] * S.g.n[1];
-    const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
-    const TileShape ts = tile_shape(W, H, spp);
+    const TileShape ts = tile_shape(S.cam.width, S.cam.height, S.cam.spp);
     const int ntiles = tile_count(S, ts);
     float* acc = reinterpret_cast<float*>(adj.acc);
     CellAcc ca = {kNoKey};
-    const float zero[3] = {0.0f, 0.0f, 0.0f};
-
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= ntiles) break;
-        const int sl = lane % ts.G;
-        const TilePix tp = tile_pixel(S, ts, t, lane);
-        const int px = tp.px, py = tp.py;
-        const bool valid = tp.valid;
-        for (int qs = 0; qs < ts.samples_per_lane; ++qs) {
-            const int s = ts.samples_per_lane == 1 ? sl : qs;
-            const long long slot = ((long long)t * 32 + lane) * ts.samples_per_lane + qs;
-            bool act = valid;
-            Ray R;
-            R.N = 0;
-            R.wall = false;
-            double Ib = 0.0;
-            if (act) {
-                R = ray_setup(S, px, py, s);
-                Ib = (double)adj.dLdI[(size_t)tp.out] / spp;
-            }
-            act = act && R.wall && R.N > 0 && Ib != 0.0;
-            CompState st;
-            CompConst k;
-            double eta_in = 1.0, rin[3] = {0, 0, 0};
-            float rb[3] = {0, 0, 0}, vbN[3] = {0, 0, 0}, lenb = 0.0f, usum[3] = {0, 0, 0};
-            double etab = 0.0;
-            if (act) {
-                comp_setup(S, F, S.cam.pos, R, st, k, eta_in, rin);
-                const float4 s0 = ck.state[0 * ck.nrays + slot];
-                const float4 s1 = ck.state[1 * ck.nrays + slot];
-                const float4 s2 = ck.state[2 * ck.nrays + slot];
-                usum[0] = s1.w;
-                usum[1] = s2.x;
-                usum[2] = s2.y;
-                double rN[3], vN[3], drb[3], dvb[3], lb;
-                const float drN[3] = {s0.x, s0.y, s0.z}, dvN[3] = {s1.x, s1.y, s1.z};
-                for (int a = 0; a < 3; ++a) {
-                    rN[a] = rin[a] + R.ell * R.d[a] + (double)drN[a];
-                    vN[a] = eta_in * R.d[a] + (double)dvN[a];
-                }
-                wall_adjoint(S, rN, vN, R.t_in + R.ell + (double)s0.w, Ib, drb, dvb, lb);
-                for (int a = 0; a < 3; ++a) {
-                    rb[a] = (float)drb[a];
-                    vbN[a] = (float)dvb[a];
-                }
-                lenb = (float)lb;
-                etab = dvb[0] * R.d[0] + dvb[1] * R.d[1] + dvb[2] * R.d[2];
-            }
-            const int N = act ? R.N : 0;
-            const int n_max = __reduce_max_sync(0xffffffffu, (unsigned)N);
-            const float dt = act ? k.dt : 0.0f;
-            BrickCache bc = {kNoKey, 0u};
-            // the start sample of step 0
-            LineSample p0 = {};
-            float A[3] = {0, 0, 0}, dv[3] = {0, 0, 0}, prefix[3] = {0, 0, 0}, carry[3] = {0, 0, 0}, dtb = 0.0f;
-            if (act) {
-                line_sample(F, st.U, bc, p0);
-                float D[3];
-                rhs_of(p0.v, D);
-                for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
-            }
-            for (int n = 0; n < n_max; ++n) {
-                const bool a_ = act && n < N;
-                LineSample pm = {}, pe = {};
-                float B[3] = {0, 0, 0}, C[3] = {0, 0, 0}, u[3] = {0, 0, 0}, Dm[3] = {0, 0, 0}, De[3] = {0, 0, 0};
-                float Db0[3] = {0, 0, 0}, Dbm[3] = {0, 0, 0};
-                if (a_) {
-                    long long U2[3], U3[3];
-                    for (int a = 0; a < 3; ++a) {
-                        U2[a] = st.U[a] + (long long)n * k.dU[a] + k.dUh[a];
-                        U3[a] = st.U[a] + (long long)(n + 1) * k.dU[a];
-                    }
-                    line_sample(F, U2, bc, pm);
-                    rhs_of(pm.v, Dm);
-                    line_sample(F, U3, bc, pe);
-                    rhs_of(pe.v, De);
-                    float inc[3], nn = 0.0f;
-                    for (int a = 0; a < 3; ++a) {
-                        B[a] = dt * Dm[a];
-                        C[a] = dt * De[a];
-                        inc[a] = dt * (dv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f));
-                        const float w = k.dS[a] + inc[a];
-                        u[a] = w;
-                        nn += w * w;
-                    }
-                    const float rn = rsqrtf(nn);
-                    const float rem = (float)(N - n - 1);
-                    for (int a = 0; a < 3; ++a) {
-                        u[a] *= rn;
-                        prefix[a] += u[a];
-                        const float rbp = rb[a] + lenb * u[a];                       // adjoint of r_{n+1}
-                        const float vb1 = vbN[a] + dt * rem * rb[a] + dt * lenb * (usum[a] - prefix[a]);
-                        const float Ab = (dt * (1.0f / 6.0f)) * rbp + vb1 * (1.0f / 6.0f);
-                        const float Bb = (dt * (1.0f / 3.0f)) * rbp + vb1 * (4.0f / 6.0f);
-                        const float Cb = vb1 * (1.0f / 6.0f);
-                        dtb += rbp * (dv[a] + (A[a] + 2.0f * B[a]) * (1.0f / 6.0f)) + Ab * (A[a] / dt) + Bb * Dm[a] +
-                               Cb * De[a];
-                        Db0[a] = carry[a] + dt * Ab;      // start sample: this step's A and the previous C
-                        Dbm[a] = dt * Bb;
-                        carry[a] = dt * Cb;
-                        dv[a] += (A[a] + 4.0f * B[a] + C[a]) * (1.0f / 6.0f);
-                        A[a] = C[a];
-                    }
-                }
-                float4 Q = make_float4(0, 0, 0, 0), Qm = make_float4(0, 0, 0, 0);
-                if (a_) {
-                    Q = line_corner_record(p0.v, Db0);
-                    Qm = line_corner_record(pm.v, Dbm);
-                }
-                // the step's two samples share a cell more often than not: one row update
-                const bool same = a_ && pm.key == p0.key;
-                accumulate_dual(rows, a_, p0.key, p0.cf, Q, same, pm.cf, Qm, ca, acc, nx, nxy);
-                accumulate(rows, a_ && !same, pm.key, pm.cf, Qm, ca, acc, nx, nxy);
-                if (a_) p0 = pe;
-            }
-            // the end sample of the last step, then eta_in = 1 + deta(r_in)
-            float4 Q = make_float4(0, 0, 0, 0);
-            if (act) Q = line_corner_record(p0.v, carry);
-            accumulate(rows, act, p0.key, p0.cf, Q, ca, acc, nx, nxy);
-            int ci[3] = {0, 0, 0};
-            float cf[3] = {0, 0, 0};
-            if (act) {
-                etab -= (double)dtb * (double)dt / eta_in;
-                comp_cell(F, st.U, zero, ci, cf);
-            }
-            accumulate(rows, act, cell_key_of(F, ci), cf, make_float4((float)etab, 0.0f, 0.0f, 0.0f), ca, acc, nx, nxy);
-        }
+        adjoint_quasi_tile<E>(S, ck, adj, F, ts, t, lane, rows, acc, ca);
     }
-    flush_rows(rows, ca.key != kNoKey, ca, acc, nx, nxy);
+    flush_rows(rows, ca.key != kNoKey, ca, acc, S.g.n[0], S.g.n[0] * S.g.n[1]);
 }
 
 // ---- float64 adjoint (FP64 store and tracer, Sharma RKN) -------------------------------------
@@ -1153,6 +1169,84 @@ __global__ void gradient_kernel(GridDev g, const A* __restrict__ acc, const floa
             dLdT[c] = (float)tot * (-(float)g.K / (Tc * Tc));
         }
     }
+}
+
+// Batched adjoints (the request server): one launch covers warp tiles of several jobs,
+// indexed as in render_batch_kernel.  The lane rows belong to one job's accumulators at a
+// time, so they are flushed whenever a warp moves on to another job's tile.  The Sharma
+// form's segment slices come from seg_base with room for k_max steps.
+template <class E, bool QUASI>
+__global__ void __launch_bounds__(kAdjWarps * 32, QUASI ? BOS_ADJ_QUASI_MIN_BLOCKS : BOS_ADJ_MIN_BLOCKS)
+    adjoint_batch_kernel(const BatchJob* __restrict__ jobs, int njobs, int total, int* counter, float* seg_base,
+                         int k_max) {
+    extern __shared__ float4 smem4[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* rows = reinterpret_cast<float*>(smem4) + (size_t)warp * 32 * kRow;
+    float* st_buf = seg_base + ((size_t)blockIdx.x * kAdjWarps + warp) * ((size_t)k_max * kSegFloats * 32);
+    {
+        float4* row = reinterpret_cast<float4*>(rows + lane * kRow);
+        for (int c = 0; c < 8; ++c) row[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    __syncwarp();
+    CellAcc ca = {kNoKey};
+    int cur = -1;                      // job whose accumulators the rows belong to
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(counter, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= total) break;
+        const int j = batch_job_of(jobs, njobs, g);
+        if (j != cur && cur >= 0) {
+            const BatchJob& P = jobs[cur];
+            flush_rows(rows, ca.key != kNoKey, ca, reinterpret_cast<float*>(P.adj.acc), P.S.g.n[0],
+                       P.S.g.n[0] * P.S.g.n[1]);
+        }
+        cur = j;
+        const BatchJob& J = jobs[j];
+        const CompField<E> F = {static_cast<const E*>(J.S.g.store), {J.S.g.n[0], J.S.g.n[1], J.S.g.n[2]},
+                                {J.S.g.inv_hf[0], J.S.g.inv_hf[1], J.S.g.inv_hf[2]}};
+        const TileShape ts = tile_shape(J.S.cam.width, J.S.cam.height, J.S.cam.spp);
+        float* acc = reinterpret_cast<float*>(J.adj.acc);
+        if constexpr (QUASI)
+            adjoint_quasi_tile<E>(J.S, J.ck, J.adj, F, ts, J.tile0 + (g - J.first), lane, rows, acc, ca);
+        else
+            adjoint_tile<E, false>(J.S, J.ck, J.adj, F, ts, J.tile0 + (g - J.first), lane, rows, st_buf, acc, ca,
+                                   nullptr);
+    }
+    if (cur >= 0) {
+        const BatchJob& P = jobs[cur];
+        flush_rows(rows, ca.key != kNoKey, ca, reinterpret_cast<float*>(P.adj.acc), P.S.g.n[0], P.S.g.n[0] * P.S.g.n[1]);
+    }
+}
+
+template <class E, bool QUASI>
+static cudaError_t launch_adjoint_batch_c(const BatchJob* jobs, int njobs, int total, int* counter, float* seg_base,
+                                          int k_max, int num_sms, cudaStream_t st) {
+    const size_t smem = (size_t)kAdjWarps * 32 * kRow * sizeof(float);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_batch_kernel<E, QUASI>,
+                                                                  kAdjWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int blocks = num_sms * per_sm < kAdjMaxBlocks ? num_sms * per_sm : kAdjMaxBlocks;
+    adjoint_batch_kernel<E, QUASI><<<blocks, kAdjWarps * 32, smem, st>>>(jobs, njobs, total, counter, seg_base, k_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_batch(int mode, int integ, const BatchJob* jobs, int njobs, int total, int* counter,
+                                 float* seg_base, int k_max, int num_sms, cudaStream_t st) {
+    if (k_max > 64 || (integ != 0 && integ != 2)) return cudaErrorNotSupported;
+    if (mode == 1) return integ == 2 ? launch_adjoint_batch_c<F4P, true>(jobs, njobs, total, counter, seg_base, k_max, num_sms, st)
+                                     : launch_adjoint_batch_c<F4P, false>(jobs, njobs, total, counter, seg_base, k_max, num_sms, st);
+    if (mode == 2) return integ == 2 ? launch_adjoint_batch_c<B4P, true>(jobs, njobs, total, counter, seg_base, k_max, num_sms, st)
+                                     : launch_adjoint_batch_c<B4P, false>(jobs, njobs, total, counter, seg_base, k_max, num_sms, st);
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_gradient(const GridDev& g, const float4* acc, const float* T, float* dLdT, int num_sms,
+                            cudaStream_t st) {
+    gradient_kernel<float4><<<num_sms * 8, 256, 0, st>>>(g, acc, T, dLdT);
+    return cudaGetLastError();
 }
 
 template <class E, bool CONN>

@@ -486,19 +486,17 @@ bos_status_t bos_set_geometry(bos_ctx* c, const bos_camera_desc* cam, const bos_
     return BOS_OK;
 }
 
-static bos_status_t render_impl(bos_ctx* c, int mode, float* I, float* disp, double* hit, int save, void* stream,
-                                const int32_t* pix = nullptr, long long npix = 0) {
-    if (!c || !I) return fail(BOS_ERR_INVALID_ARG, "bos_render: NULL context or I");
+// Checks, checkpoint buffers and counters of a render (everything but the launch).
+static bos_status_t render_prepare(bos_ctx* c, int mode, int save, cudaStream_t st, const int32_t* pix, long long npix,
+                                   SceneDev& S, CkptDev& ck) {
     if (!c->has_grid || !c->has_geom) return fail(BOS_ERR_NOT_READY, "bos_render: set_grid and set_geometry first");
     if (c->light.mode == 2 && (mode == 3 || mode == 4))
         return fail(BOS_ERR_UNIMPLEMENTED, "bos_render: the refracted projector connection needs FP32_COMP or BF16_COMP");
-    DeviceGuard dg(c->device);
-    cudaStream_t st = (cudaStream_t)stream;
     c->integ.max_steps = step_bound(c);
-    SceneDev S = scene_of(c);
+    S = scene_of(c);
     S.pix = pix;
     S.npix = npix;
-    CkptDev ck{};
+    ck = CkptDev{};
     ck.every = c->integ.ckpt_every;
     {
         TileShape ts = tile_shape(c->cam.width, c->cam.height, c->cam.spp);
@@ -539,9 +537,21 @@ static bos_status_t render_impl(bos_ctx* c, int mode, float* I, float* disp, dou
     cudaError_t e = cudaMemsetAsync(c->small, 0, 4, st);               // tile counter
     if (e == cudaSuccess && mode != 0) e = cudaMemsetAsync(c->steps, 0, 8, st);   // the reference traces nothing
     if (e != cudaSuccess) return cuda_fail(e, "bos_render: memset");
+    return BOS_OK;
+}
+
+static bos_status_t render_impl(bos_ctx* c, int mode, float* I, float* disp, double* hit, int save, void* stream,
+                                const int32_t* pix = nullptr, long long npix = 0) {
+    if (!c || !I) return fail(BOS_ERR_INVALID_ARG, "bos_render: NULL context or I");
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    SceneDev S;
+    CkptDev ck;
+    bos_status_t s = render_prepare(c, mode, save, st, pix, npix, S, ck);
+    if (s != BOS_OK) return s;
     WorkDev w{c->tile_counter, c->steps, c->err};
     RenderOut o{I, disp, hit};
-    e = launch_render(mode, S, o, w, ck, c->num_sms, st);
+    cudaError_t e = launch_render(mode, S, o, w, ck, c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(e, "bos_render: launch");
     c->saved = save != 0;
     c->saved_ck = ck;
@@ -690,3 +700,60 @@ bos_status_t bos_status(bos_ctx* c) {
 }
 
 }  // extern "C"
+
+namespace bos {
+
+// ---- hooks of the request server's batched launches
+
+bool ctx_batchable(const bos_ctx* c) {
+    const int mode = mode_of(c->grid.prec);
+    return (mode == 1 || mode == 2) && (c->integ.integrator == 0 || c->integ.integrator == 2) && c->light.mode != 2 &&
+           c->integ.ckpt_every <= 64;
+}
+
+bos_status_t ctx_batch_render(bos_ctx* c, float* I, float* disp, int save, cudaStream_t st, BatchJob* J, int* ntiles,
+                              double* steps_per_tile) {
+    DeviceGuard dg(c->device);
+    const int mode = mode_of(c->grid.prec);
+    SceneDev S;
+    CkptDev ck;
+    bos_status_t s = render_prepare(c, mode, save, st, nullptr, 0, S, ck);
+    if (s != BOS_OK) return s;
+    *J = BatchJob{};
+    J->S = S;
+    J->out = RenderOut{I, disp, nullptr};
+    J->wk = WorkDev{c->tile_counter, c->steps, c->err};
+    J->ck = ck;
+    const TileShape ts = tile_shape(c->cam.width, c->cam.height, c->cam.spp);
+    *ntiles = tile_count(S, ts);
+    *steps_per_tile = 32.0 * ts.samples_per_lane * (double)c->integ.max_steps;
+    c->saved = save != 0;
+    c->saved_ck = ck;
+    c->saved_mode = mode;
+    c->saved_pix = nullptr;
+    c->saved_npix = 0;
+    return BOS_OK;
+}
+
+bos_status_t ctx_batch_backward(bos_ctx* c, const float* dLdI, cudaStream_t st, BatchJob* J) {
+    if (!c->saved) return fail(BOS_ERR_NOT_READY, "bos_backward: needs a bos_render with save_for_backward=1");
+    DeviceGuard dg(c->device);
+    const size_t cells = (size_t)c->g.n[0] * c->g.n[1] * c->g.n[2];
+    bos_status_t s = dev_alloc(c, (void**)&c->acc, &c->acc_bytes, cells * sizeof(float4), "bos_backward: accumulators");
+    if (s != BOS_OK) return s;
+    cudaError_t e = cudaMemsetAsync(c->acc, 0, cells * sizeof(float4), st);
+    if (e != cudaSuccess) return cuda_fail(e, "bos_backward: memset");
+    J->adj = AdjDev{c->acc, dLdI, c->err, nullptr};
+    J->ck = c->saved_ck;
+    return BOS_OK;
+}
+
+bos_status_t ctx_gradient(bos_ctx* c, float* dLdT, cudaStream_t st) {
+    DeviceGuard dg(c->device);
+    cudaError_t e = launch_gradient(c->g, c->acc, c->T, dLdT, c->num_sms, st);
+    return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_backward: gradient");
+}
+
+int ctx_num_sms(const bos_ctx* c) { return c->num_sms; }
+
+}  // namespace bos

@@ -423,13 +423,79 @@ __device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, 
 #ifndef BOS_FWD_QUASI_MIN_BLOCKS
 #define BOS_FWD_QUASI_MIN_BLOCKS 3        // the same for quasi-linear tracing (more registers, more overlap)
 #endif
+// One warp tile of a render: the rays of its (up to) 32 lanes, averaged per pixel, written
+// to the outputs; adds the traced ray-steps to my_steps.
+template <int MODE, int INTEG, bool CONN>
+__device__ __forceinline__ void render_tile(const SceneDev& S, const RenderOut& out, const WorkDev& wk,
+                                            const CkptDev& ck, const TileShape& ts, int t, int lane,
+                                            unsigned long long& my_steps) {
+    const int spp = S.cam.spp;
+    const int sl = lane % ts.G;
+    const TilePix tp = tile_pixel(S, ts, t, lane);
+    if (tp.bad) flag_error(wk.err, DEV_BAD_PIXEL);
+    const int px = tp.px, py = tp.py;
+    const bool valid = tp.valid;
+    Sums acc = {0, 0, 0, 0, 0};
+    if (valid) {
+        for (int q = 0; q < ts.samples_per_lane; ++q) {
+            const int s = ts.samples_per_lane == 1 ? sl : q;
+            const long long ray = ((long long)t * 32 + lane) * ts.samples_per_lane + q;   // checkpoint slot
+            Ray R = ray_setup(S, px, py, s);
+            if (!R.wall) continue;
+            if (R.N < 0) {
+                flag_error(wk.err, DEV_STEP_BUDGET);
+                continue;
+            }
+            RayResult r;
+            if (MODE == 0 || (R.N == 0 && !CONN)) {
+                r = straight_epilogue(S, R, out.hit != nullptr);
+                if (R.N == 0 && ck.state != nullptr) {
+                    if (MODE == 4) reinterpret_cast<double*>(ck.excess)[ray] = 0.0;
+                    else ck.excess[ray] = 0.0f;
+                }
+            } else {
+                r = trace_ray<MODE, INTEG, CONN>(S, R, ck, ray, out.hit != nullptr, my_steps);
+            }
+            acc.I += r.I;
+            acc.du += r.disp[0];
+            acc.dv += r.disp[1];
+            acc.hu += r.hit[0];
+            acc.hv += r.hit[1];
+        }
+    }
+    for (int m = 1; m < ts.G; m <<= 1) {
+        acc.I += __shfl_xor_sync(0xffffffffu, acc.I, m);
+        acc.du += __shfl_xor_sync(0xffffffffu, acc.du, m);
+        acc.dv += __shfl_xor_sync(0xffffffffu, acc.dv, m);
+        acc.hu += __shfl_xor_sync(0xffffffffu, acc.hu, m);
+        acc.hv += __shfl_xor_sync(0xffffffffu, acc.hv, m);
+    }
+    if (valid && sl == 0) {
+        const size_t p = (size_t)tp.out;
+        const double inv = 1.0 / spp;
+        out.I[p] = (float)(acc.I * inv);
+        if (out.disp) {
+            out.disp[2 * p] = (float)(acc.du * inv);
+            out.disp[2 * p + 1] = (float)(acc.dv * inv);
+        }
+        if (out.hit) {
+            out.hit[2 * p] = acc.hu * inv;
+            out.hit[2 * p + 1] = acc.hv * inv;
+        }
+    }
+}
+
+__device__ __forceinline__ void add_steps(unsigned long long* steps, unsigned long long my_steps, int lane) {
+    for (int m = 16; m >= 1; m >>= 1) my_steps += __shfl_xor_sync(0xffffffffu, my_steps, m);
+    if (lane == 0 && my_steps) atomicAdd(steps, my_steps);
+}
+
 // FEW: the form for launches with few warp tiles (a pixel minibatch), without a register
 // cap: the GPU is not full either way, and each ray finishes sooner without spills.
 template <int MODE, int INTEG, bool CONN, bool FEW = false>
 __global__ void __launch_bounds__(128, FEW ? 1 : INTEG == 2 ? BOS_FWD_QUASI_MIN_BLOCKS : BOS_FWD_MIN_BLOCKS)
     render_kernel(SceneDev S, RenderOut out, WorkDev wk, CkptDev ck) {
-    const int W = S.cam.width, H = S.cam.height, spp = S.cam.spp;
-    const TileShape ts = tile_shape(W, H, spp);
+    const TileShape ts = tile_shape(S.cam.width, S.cam.height, S.cam.spp);
     const int ntiles = tile_count(S, ts);
     const int lane = threadIdx.x & 31;
     unsigned long long my_steps = 0;
@@ -438,62 +504,31 @@ __global__ void __launch_bounds__(128, FEW ? 1 : INTEG == 2 ? BOS_FWD_QUASI_MIN_
         if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= ntiles) break;
-        const int sl = lane % ts.G;
-        const TilePix tp = tile_pixel(S, ts, t, lane);
-        if (tp.bad) flag_error(wk.err, DEV_BAD_PIXEL);
-        const int px = tp.px, py = tp.py;
-        const bool valid = tp.valid;
-        Sums acc = {0, 0, 0, 0, 0};
-        if (valid) {
-            for (int q = 0; q < ts.samples_per_lane; ++q) {
-                const int s = ts.samples_per_lane == 1 ? sl : q;
-                const long long ray = ((long long)t * 32 + lane) * ts.samples_per_lane + q;   // checkpoint slot
-                Ray R = ray_setup(S, px, py, s);
-                if (!R.wall) continue;
-                if (R.N < 0) {
-                    flag_error(wk.err, DEV_STEP_BUDGET);
-                    continue;
-                }
-                RayResult r;
-                if (MODE == 0 || (R.N == 0 && !CONN)) {
-                    r = straight_epilogue(S, R, out.hit != nullptr);
-                    if (R.N == 0 && ck.state != nullptr) {
-                        if (MODE == 4) reinterpret_cast<double*>(ck.excess)[ray] = 0.0;
-                        else ck.excess[ray] = 0.0f;
-                    }
-                } else {
-                    r = trace_ray<MODE, INTEG, CONN>(S, R, ck, ray, out.hit != nullptr, my_steps);
-                }
-                acc.I += r.I;
-                acc.du += r.disp[0];
-                acc.dv += r.disp[1];
-                acc.hu += r.hit[0];
-                acc.hv += r.hit[1];
-            }
-        }
-        for (int m = 1; m < ts.G; m <<= 1) {
-            acc.I += __shfl_xor_sync(0xffffffffu, acc.I, m);
-            acc.du += __shfl_xor_sync(0xffffffffu, acc.du, m);
-            acc.dv += __shfl_xor_sync(0xffffffffu, acc.dv, m);
-            acc.hu += __shfl_xor_sync(0xffffffffu, acc.hu, m);
-            acc.hv += __shfl_xor_sync(0xffffffffu, acc.hv, m);
-        }
-        if (valid && sl == 0) {
-            const size_t p = (size_t)tp.out;
-            const double inv = 1.0 / spp;
-            out.I[p] = (float)(acc.I * inv);
-            if (out.disp) {
-                out.disp[2 * p] = (float)(acc.du * inv);
-                out.disp[2 * p + 1] = (float)(acc.dv * inv);
-            }
-            if (out.hit) {
-                out.hit[2 * p] = acc.hu * inv;
-                out.hit[2 * p + 1] = acc.hv * inv;
-            }
-        }
+        render_tile<MODE, INTEG, CONN>(S, out, wk, ck, ts, t, lane, my_steps);
     }
-    for (int m = 16; m >= 1; m >>= 1) my_steps += __shfl_xor_sync(0xffffffffu, my_steps, m);
-    if (lane == 0 && my_steps) atomicAdd(wk.steps, my_steps);
+    add_steps(wk.steps, my_steps, lane);
+}
+
+// Batched render: one launch covers warp tiles of several requests' renders (the request
+// server's continuous batching).  Work item g belongs to job j with jobs[j].first <= g <
+// jobs[j + 1].first and is that job's tile jobs[j].tile0 + (g - jobs[j].first).  Warps
+// pull items in order, so the jobs' tiles are interleaved as they are listed.
+template <int MODE, int INTEG>
+__global__ void __launch_bounds__(128, INTEG == 2 ? BOS_FWD_QUASI_MIN_BLOCKS : BOS_FWD_MIN_BLOCKS)
+    render_batch_kernel(const BatchJob* __restrict__ jobs, int njobs, int total, int* counter) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(counter, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= total) break;
+        const int j = batch_job_of(jobs, njobs, g);
+        const BatchJob& J = jobs[j];
+        const TileShape ts = tile_shape(J.S.cam.width, J.S.cam.height, J.S.cam.spp);
+        unsigned long long my_steps = 0;
+        render_tile<MODE, INTEG, false>(J.S, J.out, J.wk, J.ck, ts, J.tile0 + (g - J.first), lane, my_steps);
+        add_steps(J.wk.steps, my_steps, lane);
+    }
 }
 
 // ===================================================================== small kernels
@@ -625,6 +660,26 @@ cudaError_t launch_render(int mode, const SceneDev& S, const RenderOut& o, const
         default: return cudaErrorInvalidValue;
     }
 #undef BOS_CASE
+}
+
+template <int MODE, int INTEG>
+static cudaError_t launch_render_batch_c(const BatchJob* jobs, int njobs, int total, int* counter, int num_sms,
+                                         cudaStream_t st) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_batch_kernel<MODE, INTEG>, 128, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    render_batch_kernel<MODE, INTEG><<<num_sms * per_sm, 128, 0, st>>>(jobs, njobs, total, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_batch(int mode, int integ, const BatchJob* jobs, int njobs, int total, int* counter,
+                                int num_sms, cudaStream_t st) {
+    if (mode == 1) return integ == 2 ? launch_render_batch_c<1, 2>(jobs, njobs, total, counter, num_sms, st)
+                                     : launch_render_batch_c<1, 0>(jobs, njobs, total, counter, num_sms, st);
+    if (mode == 2) return integ == 2 ? launch_render_batch_c<2, 2>(jobs, njobs, total, counter, num_sms, st)
+                                     : launch_render_batch_c<2, 0>(jobs, njobs, total, counter, num_sms, st);
+    return cudaErrorNotSupported;
 }
 
 cudaError_t launch_ray_steps(const SceneDev& S, int32_t* nsteps, int num_sms, cudaStream_t st) {

@@ -61,6 +61,29 @@ inline size_t adjoint_segment_bytes(int K) {
     return (size_t)kAdjMaxBlocks * kAdjWarpsPerBlock * (size_t)K * 12 * 32 * sizeof(float);
 }
 
+// One request's share of a batched launch (the request server): its scene, buffers and the
+// range of its warp tiles in the launch.  Work item g of the launch is tile
+// tile0 + (g - first) of the job j with first(j) <= g < first(j + 1).
+struct BatchJob {
+    SceneDev S;
+    RenderOut out;
+    WorkDev wk;
+    CkptDev ck;
+    AdjDev adj;
+    int tile0;
+    int first;
+};
+
+__host__ __device__ __forceinline__ int batch_job_of(const BatchJob* jobs, int njobs, int g) {
+    int lo = 0, hi = njobs - 1;            // the last job whose first item is <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].first <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Message returned by bos_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
@@ -70,6 +93,16 @@ RayConst ray_const_of(const SceneDev& S);
 cudaError_t launch_build_store(const GridDev& g, const float* T, void* store, cudaStream_t st);
 cudaError_t launch_render(int mode, const SceneDev& S, const RenderOut& o, const WorkDev& w, const CkptDev& ck,
                           int num_sms, cudaStream_t st);
+// Batched launches over several jobs' warp tiles (modes 1, 2 = FP32_COMP, BF16_COMP;
+// integrator 0 = Sharma RKN, 2 = quasi-linear; light modes 0 and 1).  `counter` is zeroed
+// by the caller; seg_base holds kAdjMaxBlocks x kAdjWarpsPerBlock segment slices of K_max
+// steps for the Sharma adjoint.
+cudaError_t launch_render_batch(int mode, int integ, const BatchJob* jobs, int njobs, int total, int* counter,
+                                int num_sms, cudaStream_t st);
+cudaError_t launch_adjoint_batch(int mode, int integ, const BatchJob* jobs, int njobs, int total, int* counter,
+                                 float* seg_base, int k_max, int num_sms, cudaStream_t st);
+cudaError_t launch_gradient(const GridDev& g, const float4* acc, const float* T, float* dLdT, int num_sms,
+                            cudaStream_t st);
 cudaError_t launch_ray_steps(const SceneDev& S, int32_t* nsteps, int num_sms, cudaStream_t st);
 cudaError_t launch_export_nodes(const GridDev& g, void* out, int num_sms, cudaStream_t st);
 cudaError_t launch_loss_l2(const float* I, const float* target, long long n, double* loss, float* dLdI, int num_sms,

@@ -1,14 +1,26 @@
 // Request server: continuous batching of forward and forward+adjoint renders on one GPU.
 //
 // Requests arrive at any time (bos_submit, from any thread) and queue FIFO.  A scheduler
-// thread admits the queue head as soon as (a) one of the server's slots is free and
-// (b) the request's exact device footprint fits in the free space of the server's arena,
-// a single device allocation of mem_limit_bytes made once at creation (first-fit with
-// coalescing; nothing is allocated or freed per request).  An admitted request runs on its
-// slot's own non-blocking stream and context (field build, render, loss, backward), so the
-// kernels of all admitted requests overlap on the device, and requests that arrive while
-// others run are admitted as soon as slots and memory free up.  A host function enqueued
-// behind the request's last kernel marks its completion; every wait is bounded.
+// thread admits the queue head as soon as (a) fewer than `slots` requests are in flight
+// and (b) the request's exact device footprint fits in the free space of the server's
+// arena, a single device allocation of mem_limit_bytes made once at creation (first-fit
+// with coalescing; nothing is allocated or freed per request).
+//
+// Admitted requests are executed by batched launches on one server stream.  The field
+// build of a request is enqueued at admission; after it, the request's warp tiles join a
+// shared pool, and each batched launch (render_batch_kernel, adjoint_batch_kernel) pulls
+// warp tiles of every admitted request in its phase from one device work list: the
+// requests share the GPU at warp-tile granularity, oldest first, with a bounded amount of
+// work per launch, so a request that arrives while others run joins the next launch.  A
+// request moves from its render tiles (I_flow and, for forward + adjoint, checkpoints) to
+// L_BOS and its adjoint tiles, then the gradient epilogue; an event behind its last kernel
+// marks completion.  Launches are cut at batch boundaries rather than kept resident: the
+// gathers read the field stores through the non-coherent L1 path, which may assume the
+// data does not change while a kernel runs, and stores are rebuilt in recycled arena
+// memory as requests come and go.  Requests of other kinds (float64 or plain float32
+// stores, RK4, the refracted projector connection) run their own launches on the same
+// stream, in the same admission order.  No kernel waits on the host or on another kernel:
+// the only waits are host-side and bounded (bos_wait, bos_server_destroy).
 //
 // The fake executor (BOS_SERVER_FAKE_EXECUTOR) runs the same admission, slot and memory
 // logic without any CUDA call: an admitted request "runs" for a time proportional to
@@ -17,6 +29,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -88,6 +101,9 @@ class Arena {
     size_t size_ = 0, used_ = 0;
 };
 
+// Phases of an admitted request on the GPU.
+enum Phase { PH_RENDER = 0, PH_ADJOINT = 1, PH_FINISH = 2 };
+
 struct Req {
     bos_request r;
     uint64_t footprint = 0;
@@ -96,11 +112,21 @@ struct Req {
     int slot = -1;
     bool done = false;
     size_t off = 0;
+    // GPU engine
+    uint64_t order = 0;             // admission order
+    bool batched = false;
+    int phase = PH_FINISH;
+    int mode = 0, integ = 0;
+    bos::BatchJob J{};
+    int tiles[2] = {0, 0}, next[2] = {0, 0};
+    double cost = 1.0;              // ray-step bound of one warp tile
+    float* dLdI = nullptr;
+    cudaEvent_t ev = nullptr;       // behind the request's last kernel
 };
 
 struct Slot {
-    cudaStream_t stream = nullptr;
     bos_ctx* ctx = nullptr;
+    cudaEvent_t ev = nullptr;       // completion of the slot's request
     bool busy = false;
     uint64_t ticket = 0;
     std::atomic<bool> finished{false};
@@ -108,6 +134,25 @@ struct Slot {
     uint64_t fake_due = 0;
     struct bos_server* owner = nullptr;
 };
+
+// One batched launch in flight: its job list (pinned host copy and device copy), work
+// counter and completion event.
+struct Batch {
+    bos::BatchJob* host = nullptr;
+    bos::BatchJob* dev = nullptr;
+    int* counter = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+};
+
+constexpr int kMaxBatchJobs = 64;       // jobs per batched launch (= the slot limit)
+constexpr int kBatches = 4;             // job-list buffers
+constexpr int kInFlight = 2;            // batched launches enqueued ahead of the GPU
+// work per batched launch, in ray-step bounds: a few milliseconds of the GPU, so that a new
+// request waits at most about that long to join
+constexpr double kRenderBudget = 2.5e8;
+constexpr double kAdjointBudget = 1.0e8;
+constexpr int kSegK = 64;               // segment slices of the batched Sharma adjoint hold up to 64 steps
 
 size_t scratch_bytes(const bos_request& r) {   // dL/dI between the loss and the backward
     return r.target_dev ? bos::align_up((size_t)r.cam.width * r.cam.height * sizeof(float)) : 0;
@@ -130,22 +175,26 @@ struct bos_server {
     bool stop = false;
     std::thread sched;
     size_t peak_used = 0;
+    // GPU engine
+    cudaStream_t stream = nullptr;
+    Batch batches[kBatches];
+    float* seg = nullptr;              // segment slices of the batched Sharma adjoint (in the arena)
+    int num_sms = 1;
+    uint64_t admitted = 0;
+    std::vector<uint64_t> active;      // tickets of admitted, unfinished requests in admission order
+    uint64_t n_batches = 0, n_batch_tiles = 0, n_batch_jobs = 0;
+    int max_batch_jobs = 0;
 
     bool fake() const { return flags & BOS_SERVER_FAKE_EXECUTOR; }
     void run();
     void launch(Req& q, Slot& s);
     void finish(Slot& s);
+    bool launch_batch();
+    void after_phase(Req& q);
+    void fail_request(Req& q, bos_status_t e);
 };
 
 namespace {
-
-void CUDART_CB on_done(void* arg) {
-    // Runs on a driver thread: no CUDA calls here, only flags and a wake-up.
-    Slot* s = static_cast<Slot*>(arg);
-    s->t_finished.store(now_ns());
-    s->finished.store(true);
-    s->owner->cv.notify_all();
-}
 
 bos_status_t validate_request(const bos_request* r) {
     if (!r || !r->T_dev || !r->pattern_dev || !r->I_dev) return BOS_ERR_INVALID_ARG;
@@ -158,6 +207,16 @@ bos_status_t validate_request(const bos_request* r) {
 
 }  // namespace
 
+// A request whose launch failed: let the work already enqueued drain before its memory is
+// reused, then mark it finished.
+void bos_server::fail_request(Req& q, bos_status_t e) {
+    q.status = e;
+    q.phase = PH_FINISH;
+    q.batched = false;
+    cudaStreamSynchronize(stream);
+    cudaEventRecord(q.ev, stream);
+}
+
 void bos_server::launch(Req& q, Slot& s) {
     if (fake()) {
         // simulated run time: 1 ms + 1 ms per 64 MiB of footprint
@@ -166,25 +225,146 @@ void bos_server::launch(Req& q, Slot& s) {
     }
     const bos_request& r = q.r;
     char* region = base + q.off;
-    size_t scratch = scratch_bytes(r);
-    bos::ctx_bind_arena(s.ctx, region + scratch, q.footprint - scratch, s.stream);
-    float* dLdI = (float*)region;
-    void* st = (void*)s.stream;
+    const size_t scratch = scratch_bytes(r);
+    bos::ctx_bind_arena(s.ctx, region + scratch, q.footprint - scratch, stream);
+    q.dLdI = (float*)region;
+    q.order = admitted++;
+    q.ev = s.ev;
+    void* st = (void*)stream;
     bos_status_t e = bos_set_grid(s.ctx, &r.grid, r.T_dev, st);
     if (e == BOS_OK) e = bos_set_geometry(s.ctx, &r.cam, &r.wall, &r.light, r.pattern_dev, &r.integ);
-    if (e == BOS_OK) e = bos_render(s.ctx, r.I_dev, r.disp_dev, nullptr, r.target_dev ? 1 : 0, st);
-    if (e == BOS_OK && r.target_dev) {
-        e = bos_loss_l2(r.I_dev, r.target_dev, (int64_t)r.cam.width * r.cam.height, r.loss_dev, dLdI, st);
-        if (e == BOS_OK) e = bos_backward(s.ctx, dLdI, r.dLdT_dev, st);
+    if (e == BOS_OK && bos::ctx_batchable(s.ctx) && (!r.target_dev || r.integ.integrator == 2 || seg != nullptr)) {
+        // its warp tiles join the batched launches
+        int ntiles = 0;
+        e = bos::ctx_batch_render(s.ctx, r.I_dev, r.disp_dev, r.target_dev ? 1 : 0, stream, &q.J, &ntiles, &q.cost);
+        if (e == BOS_OK) {
+            q.batched = true;
+            q.phase = PH_RENDER;
+            q.mode = r.grid.prec == BOS_PREC_BF16_COMP ? 2 : 1;
+            q.integ = r.integ.integrator;
+            q.tiles[0] = q.tiles[1] = ntiles;
+            q.next[0] = q.next[1] = 0;
+            return;
+        }
+    } else if (e == BOS_OK) {
+        // its own launches, in admission order on the same stream
+        e = bos_render(s.ctx, r.I_dev, r.disp_dev, nullptr, r.target_dev ? 1 : 0, st);
+        if (e == BOS_OK && r.target_dev) {
+            e = bos_loss_l2(r.I_dev, r.target_dev, (int64_t)r.cam.width * r.cam.height, r.loss_dev, q.dLdI, st);
+            if (e == BOS_OK) e = bos_backward(s.ctx, q.dLdI, r.dLdT_dev, st);
+        }
+        if (e == BOS_OK && cudaEventRecord(q.ev, stream) != cudaSuccess) e = BOS_ERR_CUDA;
+        if (e == BOS_OK) {
+            q.phase = PH_FINISH;
+            return;
+        }
     }
-    if (e == BOS_OK && cudaLaunchHostFunc(s.stream, on_done, &s) != cudaSuccess) e = BOS_ERR_CUDA;
+    fail_request(q, e);
+}
+
+// The request's tiles of its current phase are all enqueued: what follows them.
+void bos_server::after_phase(Req& q) {
+    Slot& s = *slots[q.slot];
+    const bos_request& r = q.r;
+    bos_status_t e = BOS_OK;
+    if (q.phase == PH_RENDER && r.target_dev) {
+        e = bos_loss_l2(r.I_dev, r.target_dev, (int64_t)r.cam.width * r.cam.height, r.loss_dev, q.dLdI, (void*)stream);
+        if (e == BOS_OK) e = bos::ctx_batch_backward(s.ctx, q.dLdI, stream, &q.J);
+        if (e == BOS_OK) {
+            q.phase = PH_ADJOINT;
+            return;
+        }
+    } else if (q.phase == PH_ADJOINT) {
+        e = bos::ctx_gradient(s.ctx, r.dLdT_dev, stream);
+    }
+    if (e == BOS_OK && cudaEventRecord(q.ev, stream) != cudaSuccess) e = BOS_ERR_CUDA;
     if (e != BOS_OK) {
-        q.status = e;
-        // let the work already enqueued drain before the memory is reused
-        cudaStreamSynchronize(s.stream);
-        s.t_finished.store(now_ns());
-        s.finished.store(true);
+        fail_request(q, e);
+        return;
     }
+    q.phase = PH_FINISH;
+}
+
+// Enqueue one batched launch: the phase and kernel variant of the oldest request with tiles
+// to run, and tiles of every request of that kind, oldest first, shared out of the
+// launch's work budget (every request gets at least one warp tile).
+bool bos_server::launch_batch() {
+    Batch* b = nullptr;
+    int inflight = 0;
+    for (auto& x : batches) {
+        if (x.busy) ++inflight;
+        else if (!b) b = &x;
+    }
+    if (!b || inflight >= kInFlight) return false;
+    Req* head = nullptr;
+    for (uint64_t tk : active) {
+        Req& q = reqs[tk];
+        if (q.batched && q.phase < PH_FINISH && q.next[q.phase] < q.tiles[q.phase]) {
+            head = &q;
+            break;
+        }
+    }
+    if (!head) return false;
+    const int phase = head->phase, mode = head->mode, integ = head->integ;
+    std::vector<Req*> sel;
+    double demand = 0.0;
+    for (uint64_t tk : active) {
+        Req& q = reqs[tk];
+        if (q.batched && q.phase == phase && q.mode == mode && q.integ == integ && q.next[phase] < q.tiles[phase] &&
+            (int)sel.size() < kMaxBatchJobs) {
+            sel.push_back(&q);
+            demand += q.cost * (q.tiles[phase] - q.next[phase]);
+        }
+    }
+    const double budget = phase == PH_RENDER ? kRenderBudget : kAdjointBudget;
+    const double share = budget / (double)sel.size();
+    std::vector<int> take(sel.size());
+    double used = 0.0;
+    for (size_t i = 0; i < sel.size(); ++i) {
+        Req& q = *sel[i];
+        const int rem = q.tiles[phase] - q.next[phase];
+        int n = (int)std::min<double>(rem, std::max(1.0, share / q.cost));
+        take[i] = n;
+        used += n * q.cost;
+    }
+    for (size_t i = 0; i < sel.size() && used < budget; ++i) {   // the rest of the budget, oldest first
+        Req& q = *sel[i];
+        const int rem = q.tiles[phase] - q.next[phase] - take[i];
+        const int n = (int)std::min<double>(rem, (budget - used) / q.cost);
+        if (n > 0) {
+            take[i] += n;
+            used += n * q.cost;
+        }
+    }
+    int total = 0, k_max = 1;
+    for (size_t i = 0; i < sel.size(); ++i) {
+        Req& q = *sel[i];
+        bos::BatchJob& J = b->host[i];
+        J = q.J;
+        J.tile0 = q.next[phase];
+        J.first = total;
+        total += take[i];
+        q.next[phase] += take[i];
+        k_max = std::max(k_max, q.J.ck.every);
+    }
+    cudaError_t e = cudaMemcpyAsync(b->dev, b->host, sel.size() * sizeof(bos::BatchJob), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->counter, 0, sizeof(int), stream);
+    if (e == cudaSuccess)
+        e = phase == PH_RENDER ? bos::launch_render_batch(mode, integ, b->dev, (int)sel.size(), total, b->counter,
+                                                          num_sms, stream)
+                               : bos::launch_adjoint_batch(mode, integ, b->dev, (int)sel.size(), total, b->counter, seg,
+                                                           integ == 2 ? 1 : kSegK, num_sms, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev, stream);
+    b->busy = true;
+    ++n_batches;
+    n_batch_tiles += (uint64_t)total;
+    n_batch_jobs += sel.size();
+    max_batch_jobs = std::max(max_batch_jobs, (int)sel.size());
+    for (Req* q : sel) {
+        if (e != cudaSuccess) fail_request(*q, BOS_ERR_CUDA);
+        else if (q->next[phase] == q->tiles[phase]) after_phase(*q);
+    }
+    return e == cudaSuccess;
 }
 
 void bos_server::finish(Slot& s) {
@@ -198,6 +378,7 @@ void bos_server::finish(Slot& s) {
     q.done = true;
     s.busy = false;
     s.finished.store(false);
+    active.erase(std::remove(active.begin(), active.end(), s.ticket), active.end());
 }
 
 void bos_server::run() {
@@ -206,11 +387,21 @@ void bos_server::run() {
     for (;;) {
         bool any_busy = false;
         const uint64_t t = now_ns();
+        if (!fake())
+            for (auto& x : batches)
+                if (x.busy && cudaEventQuery(x.ev) == cudaSuccess) x.busy = false;
         for (auto& sp : slots) {
             Slot& s = *sp;
             if (s.busy && fake() && !s.finished.load() && t >= s.fake_due) {
                 s.t_finished.store(t);
                 s.finished.store(true);
+            }
+            if (s.busy && !fake() && !s.finished.load()) {
+                Req& q = reqs[s.ticket];
+                if (q.phase == PH_FINISH && cudaEventQuery(q.ev) == cudaSuccess) {
+                    s.t_finished.store(now_ns());
+                    s.finished.store(true);
+                }
             }
             if (s.busy && s.finished.load()) finish(s);
             any_busy = any_busy || s.busy;
@@ -237,11 +428,15 @@ void bos_server::run() {
             free_slot->ticket = tk;
             any_busy = true;
             if (arena.used() > peak_used) peak_used = arena.used();
+            active.push_back(tk);
             launch(q, *free_slot);
         }
+        if (!fake())
+            while (launch_batch()) {
+            }
         cv.notify_all();
         if (stop && pending.empty() && !any_busy) break;
-        cv.wait_for(lk, std::chrono::microseconds(fake() ? 200 : 500));
+        cv.wait_for(lk, std::chrono::microseconds(fake() ? 200 : 100));
     }
 }
 
@@ -253,47 +448,84 @@ bos_status_t bos_request_footprint(const bos_request* r, uint64_t* bytes) {
     return BOS_OK;
 }
 
+namespace {
+
+// Release every CUDA resource of a server (after its stream has drained).
+void release_gpu(bos_server* s) {
+    for (auto& o : s->slots) {
+        if (o->ctx) {
+            bos::ctx_bind_arena(o->ctx, nullptr, 0, s->stream);
+            bos_destroy(o->ctx);
+        }
+        if (o->ev) cudaEventDestroy(o->ev);
+    }
+    for (auto& b : s->batches) {
+        if (b.ev) cudaEventDestroy(b.ev);
+        if (b.host) cudaFreeHost(b.host);
+        if (b.dev) cudaFree(b.dev);
+        if (b.counter) cudaFree(b.counter);
+    }
+    if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->base) cudaFree(s->base);
+}
+
+}  // namespace
+
 bos_status_t bos_server_create(bos_server** out, int device, uint64_t mem_limit_bytes, int nslots, int flags) {
-    if (!out || nslots < 1 || nslots > 64 || mem_limit_bytes < (1u << 20)) return BOS_ERR_INVALID_ARG;
+    if (!out || nslots < 1 || nslots > kMaxBatchJobs || mem_limit_bytes < (1u << 20)) return BOS_ERR_INVALID_ARG;
     *out = nullptr;
     std::unique_ptr<bos_server> s(new bos_server());
     s->device = device;
     s->flags = flags;
     s->limit = mem_limit_bytes;
     s->arena.reset(mem_limit_bytes);
+    for (int i = 0; i < nslots; ++i) {
+        std::unique_ptr<Slot> sl(new Slot());
+        sl->owner = s.get();
+        s->slots.push_back(std::move(sl));
+    }
     if (!s->fake()) {
         int prev = 0;
         cudaGetDevice(&prev);
         if (cudaSetDevice(device) != cudaSuccess) return BOS_ERR_INVALID_ARG;
+        bos_status_t st = BOS_OK;
         if (cudaMalloc((void**)&s->base, mem_limit_bytes) != cudaSuccess) {
             cudaGetLastError();
+            s->base = nullptr;
+            st = BOS_ERR_OOM;
+        }
+        if (st == BOS_OK && cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) st = BOS_ERR_CUDA;
+        if (st == BOS_OK) cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, device);
+        for (auto& b : s->batches) {
+            if (st != BOS_OK) break;
+            if (cudaHostAlloc((void**)&b.host, kMaxBatchJobs * sizeof(bos::BatchJob), cudaHostAllocDefault) != cudaSuccess ||
+                cudaMalloc((void**)&b.dev, kMaxBatchJobs * sizeof(bos::BatchJob)) != cudaSuccess ||
+                cudaMalloc((void**)&b.counter, sizeof(int)) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess)
+                st = BOS_ERR_CUDA;
+        }
+        for (auto& o : s->slots) {
+            if (st != BOS_OK) break;
+            if (cudaEventCreateWithFlags(&o->ev, cudaEventDisableTiming) != cudaSuccess) st = BOS_ERR_CUDA;
+            if (st == BOS_OK) st = bos_create(&o->ctx, device, 0);
+            if (st == BOS_OK) bos::ctx_bind_arena(o->ctx, nullptr, 0, s->stream);
+        }
+        // segment slices of the batched Sharma adjoint, carved once from the arena when it is
+        // large enough (otherwise forward + adjoint requests of that kind run their own launches)
+        const size_t seg_bytes = bos::adjoint_segment_bytes(kSegK);
+        size_t off = 0;
+        if (st == BOS_OK && mem_limit_bytes >= 4 * seg_bytes && s->arena.alloc(seg_bytes, &off)) {
+            s->seg = (float*)(s->base + off);
+            s->peak_used = s->arena.used();
+        }
+        if (st == BOS_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) st = BOS_ERR_CUDA;
+        if (st != BOS_OK) {
+            cudaGetLastError();
+            release_gpu(s.get());
             cudaSetDevice(prev);
-            return BOS_ERR_OOM;
+            return st;
         }
         cudaSetDevice(prev);
-    }
-    for (int i = 0; i < nslots; ++i) {
-        std::unique_ptr<Slot> sl(new Slot());
-        sl->owner = s.get();
-        if (!s->fake()) {
-            int prev = 0;
-            cudaGetDevice(&prev);
-            cudaSetDevice(device);
-            cudaError_t e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking);
-            cudaSetDevice(prev);
-            bos_status_t st = e == cudaSuccess ? bos_create(&sl->ctx, device, 0) : BOS_ERR_CUDA;
-            if (st != BOS_OK) {
-                for (auto& o : s->slots) {
-                    if (o->ctx) bos_destroy(o->ctx);
-                    if (o->stream) cudaStreamDestroy(o->stream);
-                }
-                if (sl->stream) cudaStreamDestroy(sl->stream);
-                cudaFree(s->base);
-                return st;
-            }
-            bos::ctx_bind_arena(sl->ctx, nullptr, 0, sl->stream);
-        }
-        s->slots.push_back(std::move(sl));
     }
     bos_server* raw = s.release();
     raw->sched = std::thread([raw] { raw->run(); });
@@ -363,6 +595,17 @@ bos_status_t bos_server_stats(bos_server* s, uint64_t* arena_bytes, uint64_t* pe
     return BOS_OK;
 }
 
+bos_status_t bos_server_batches(bos_server* s, uint64_t* launches, uint64_t* tiles, uint64_t* job_shares,
+                                int* max_jobs) {
+    if (!s) return BOS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (launches) *launches = s->n_batches;
+    if (tiles) *tiles = s->n_batch_tiles;
+    if (job_shares) *job_shares = s->n_batch_jobs;
+    if (max_jobs) *max_jobs = s->max_batch_jobs;
+    return BOS_OK;
+}
+
 bos_status_t bos_server_destroy(bos_server* s, uint64_t timeout_ns) {
     if (!s) return BOS_OK;
     {
@@ -388,15 +631,12 @@ bos_status_t bos_server_destroy(bos_server* s, uint64_t timeout_ns) {
     if (!drained) return BOS_ERR_TIMEOUT;   // the server stays alive; the caller may retry
     s->sched.join();
     if (!s->fake()) {
-        for (auto& sp : s->slots) {
-            if (sp->stream) cudaStreamSynchronize(sp->stream);
-            if (sp->ctx) {
-                bos::ctx_bind_arena(sp->ctx, nullptr, 0, sp->stream);
-                bos_destroy(sp->ctx);
-            }
-            if (sp->stream) cudaStreamDestroy(sp->stream);
-        }
-        if (s->base) cudaFree(s->base);
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(s->device);
+        cudaStreamSynchronize(s->stream);
+        release_gpu(s);
+        cudaSetDevice(prev);
     }
     delete s;
     return BOS_OK;

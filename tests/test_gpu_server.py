@@ -43,7 +43,7 @@ def make(bos, i, spec):
 def alone(bos, d):
     sc = d["scene"]
     ctx = bos.Context(0)
-    ctx.set_grid(sc.grid, d["T"], bos.BOS_PREC_FP32_COMP)
+    ctx.set_grid(sc.grid, d["T"], d.get("prec", bos.BOS_PREC_FP32_COMP))
     ctx.set_geometry(sc.camera, sc.wall, sc.light, sc.integ, pattern=d["pattern"])
     adj = "target" in d
     I, D, _ = ctx.render(disp=True, save_for_backward=adj)
@@ -61,7 +61,7 @@ def alone(bos, d):
 def submit(bos, srv, d):
     sc = d["scene"]
     p = lambda k: d[k].data_ptr() if k in d else None
-    req = bos.make_request(sc.grid, bos.BOS_PREC_FP32_COMP, d["T"].data_ptr(), sc.camera, sc.wall, sc.light,
+    req = bos.make_request(sc.grid, d.get("prec", bos.BOS_PREC_FP32_COMP), d["T"].data_ptr(), sc.camera, sc.wall, sc.light,
                            d["pattern"].data_ptr(), sc.integ, p("I"), p("disp"), p("target"), p("loss"), p("dLdT"))
     return srv.submit(req, keep=d)
 
@@ -75,9 +75,12 @@ def test_results_alone_equal_results_in_the_mix(bos):
         assert srv.wait(t, 120.0) == bos.BOS_OK
     torch.cuda.synchronize()
     infos = [srv.info(t) for t in tickets]
+    batches = srv.batches()
     srv.close()
-    # several requests were on the device at once
+    # several requests were on the device at once, and batched launches served warp tiles of
+    # several of them
     assert max(sum(1 for j in infos if j["admit_ns"] <= i["admit_ns"] < j["done_ns"]) for i in infos) > 1
+    assert batches["launches"] > 0 and batches["max_jobs"] > 1, batches
     for d, r in zip(reqs, ref):
         assert torch.equal(d["I"], r["I"])            # the forward is deterministic
         assert torch.equal(d["disp"], r["disp"])
@@ -114,6 +117,33 @@ def test_refracted_requests_alone_equal_results_in_the_mix(bos):
     for t in tickets:
         assert srv.wait(t, 120.0) == bos.BOS_OK
     torch.cuda.synchronize()
+    srv.close()
+    for d, r in zip(reqs, ref):
+        assert torch.equal(d["I"], r["I"])
+        assert torch.equal(d["disp"], r["disp"])
+        if "dLdT" in d:
+            assert torch.linalg.norm(d["dLdT"] - r["dLdT"]) <= 1e-5 * torch.linalg.norm(r["dLdT"])
+
+
+def test_quasi_linear_and_bf16_requests_are_batched_and_equal_alone(bos):
+    """Requests of the other batched kinds (quasi-linear tracing, the BF16 store) in one mix:
+    each result is the same as alone."""
+    reqs = []
+    for i, s in enumerate(SPECS[:6]):
+        d = make(bos, 200 + i, s)
+        sc = d["scene"]
+        if i % 2 == 0:
+            d["scene"] = sc.replace(integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=2))
+        if i % 3 == 0:
+            d["prec"] = bos.BOS_PREC_BF16_COMP
+        reqs.append(d)
+    ref = [alone(bos, d) for d in reqs]
+    srv = bos.Server(0, 2 << 30, 6)
+    tickets = [submit(bos, srv, d) for d in reqs]
+    for t in tickets:
+        assert srv.wait(t, 120.0) == bos.BOS_OK
+    torch.cuda.synchronize()
+    assert srv.batches()["launches"] > 0
     srv.close()
     for d, r in zip(reqs, ref):
         assert torch.equal(d["I"], r["I"])
