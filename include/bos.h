@@ -320,6 +320,20 @@ bos_status_t bos_render_noalloc(const bos_grid_desc* grid, const float* T_dev, c
  * Allocates nothing (one 4-byte device-to-host copy). */
 bos_status_t bos_noalloc_status(void);
 
+/* The checked build (library built with BOS_CHECKED=1, libbos_checked.so), a stand-in for a
+ * memory checker: every gather from the field store, every node-accumulator atomic and
+ * every checkpoint access is checked against the extent of its buffer; an index outside it
+ * is recorded in the context's error word (bos_status then returns BOS_ERR_DEVICE_CHECK)
+ * and replaced by index 0, so the access stays inside the buffer.  No counterpart in the
+ * paper.  bos_checked_build returns 1 in that build and 0 otherwise. */
+int bos_checked_build(void);
+
+/* Checked build only, for testing the checks: lower the field-store bound the checks use to
+ * `elems` elements (never above the real extent), so that gathers beyond it are reported
+ * while every access still lands inside the real store.  BOS_ERR_UNIMPLEMENTED in the
+ * ordinary build; BOS_ERR_NOT_READY before bos_set_grid; bos_set_grid restores the bound. */
+bos_status_t bos_debug_store_bound(bos_ctx* ctx, uint32_t elems);
+
 /* Sticky device-side status of the context (call after synchronising). */
 bos_status_t bos_status(bos_ctx* ctx);
 

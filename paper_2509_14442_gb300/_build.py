@@ -14,6 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libbos.so")
+# the checked build (BOS_CHECKED=1): bounds checks on every indexed device buffer
+LIB_CHECKED = os.path.join(HERE, "libbos_checked.so")
 SOURCES = ["bos_forward.cu", "bos_adjoint.cu", "bos_api.cu", "bos_server.cu", "bos_noalloc.cu", "bos_optim.cu",
            "bos_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -28,21 +30,23 @@ def nvcc() -> str:
     return cand
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "bos.h")]
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
-    if not force and not _stale():
-        return LIB
-    build_dir = os.path.join(HERE, "_build")
+def build(force: bool = False, verbose: bool = False, extra: list | None = None, checked: bool = False) -> str:
+    """Build libbos.so (or, checked=True, libbos_checked.so with BOS_CHECKED=1)."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not _stale(lib):
+        return lib
+    build_dir = os.path.join(HERE, "_build_checked" if checked else "_build")
     os.makedirs(build_dir, exist_ok=True)
     nv = nvcc()
-    extra = list(extra or [])
+    extra = list(extra or []) + (["-DBOS_CHECKED=1"] if checked else [])
 
     def compile_one(src: str) -> str:
         obj = os.path.join(build_dir, src.replace(".cu", ".o"))
@@ -56,13 +60,13 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
 
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nv, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -110,6 +110,8 @@ SIGNATURES = {
     "bos_render_noalloc": (_i, [_P(bos_grid_desc), _v, _P(bos_camera_desc), _P(bos_wall_desc), _P(bos_light_desc),
                                 _v, _P(bos_integrator_desc), _v, _v, _v]),
     "bos_noalloc_status": (_i, []),
+    "bos_checked_build": (_i, []),
+    "bos_debug_store_bound": (_i, [_v, C.c_uint32]),
     "bos_status": (_i, [_v]),
     "bos_error_string": (C.c_char_p, [_i]),
     "bos_last_error": (C.c_char_p, []),
@@ -127,15 +129,21 @@ SIGNATURES = {
 _lib = None
 
 
+def checked() -> bool:
+    """True when this process uses the checked build (environment BOS_CHECKED=1)."""
+    return os.environ.get("BOS_CHECKED", "0") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked() else _build.LIB
 
 
 def lib(build: bool = True):
-    """Load libbos.so (building it first if it is missing or stale)."""
+    """Load libbos.so, or libbos_checked.so with BOS_CHECKED=1 in the environment (building
+    it first if it is missing or stale)."""
     global _lib
     if _lib is None:
-        path = _build.build() if build else _build.LIB
+        path = _build.build(checked=checked()) if build else lib_path()
         if not os.path.exists(path):
             raise RuntimeError(f"BOS CUDA library not found at {path}; run __graft_entry__.build()")
         L = C.CDLL(path)

@@ -90,7 +90,7 @@ __device__ __forceinline__ void stage_eval(const CompField<E>& F, const long lon
     int ci[3];
     comp_cell(F, U, q, ci, s.cf);
     s.key = cell_key_of(F, ci);
-    uint32_t o = cached_offset(bc, ci[0], ci[1], ci[2]);
+    const uint32_t o = comp_offset(F, bc, ci);
     s.ig = trilinear_grad2(F.store, o, s.cf[0], s.cf[1], s.cf[2]);
 }
 
@@ -113,7 +113,9 @@ __device__ __forceinline__ void rhs_adjoint(const CompField<E>& F, const InterpG
 // cell, the warp flushes: lanes whose rows belong to the same cell are summed column by
 // column (lane l owns corner l/4, channel l%4) and each sum is one atomic.
 struct CellAcc {
-    uint32_t key;   // node index of the accumulated cell's base corner, kNoKey if empty
+    uint32_t key;      // node index of the accumulated cell's base corner, kNoKey if empty
+    uint32_t ncells;   // nodes of the accumulators (the checked build's bound)
+    int* err;
 };
 
 __device__ __forceinline__ void flush_rows(float* rows, bool flag, CellAcc& ca, float* acc, int nx, int nxy) {
@@ -147,7 +149,7 @@ __device__ __forceinline__ void flush_rows(float* rows, bool flag, CellAcc& ca, 
                 sum += v[0];
             }
         }
-        if (sum != 0.0f) atomicAdd(acc + ((size_t)(lk + off) << 2) + (lane & 3), sum);
+        if (sum != 0.0f) atomicAdd(acc + ((size_t)bounded(lk + off, ca.ncells, ca.err) << 2) + (lane & 3), sum);
     }
     __syncwarp();
     if (flag) {
@@ -427,9 +429,10 @@ __device__ __forceinline__ void adjoint_tile(const SceneDev& S, const CkptDev& c
             // ---- recompute the segment from its checkpoint, keeping each step's state
             if (seg) {
                 CompState st;
-                const float4 s0 = cstate[((size_t)c * 3 + 0) * ck.nrays + slot];
-                const float4 s1 = cstate[((size_t)c * 3 + 1) * ck.nrays + slot];
-                const float4 s2 = cstate[((size_t)c * 3 + 2) * ck.nrays + slot];
+                const size_t cc = bounded((size_t)c, (size_t)ck.max_ckpt, ck.err);
+                const float4 s0 = cstate[(cc * 3 + 0) * ck.nrays + slot];
+                const float4 s1 = cstate[(cc * 3 + 1) * ck.nrays + slot];
+                const float4 s2 = cstate[(cc * 3 + 2) * ck.nrays + slot];
                 st.dr[0] = s0.x; st.dr[1] = s0.y; st.dr[2] = s0.z;
                 st.dv[0] = s1.x; st.dv[1] = s1.y; st.dv[2] = s1.z;
                 st.cv[0] = s2.x; st.cv[1] = s2.y; st.cv[2] = s2.z;
@@ -676,8 +679,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
     // [K][12][32] step states and stage terms (dr, dv, A, B) of the segment being reversed
     // (this warp's slice)
     float* st_buf = adj.seg + ((size_t)blockIdx.x * kAdjWarps + warp) * ((size_t)K * kSegFloats * 32);
-    const CompField<E> F = {static_cast<const E*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
-                            {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
+    const CompField<E> F = comp_field<E>(S.g);
     const TileShape ts = tile_shape(S.cam.width, S.cam.height, S.cam.spp);
     const int ntiles = tile_count(S, ts);
     float* acc = reinterpret_cast<float*>(adj.acc);
@@ -686,7 +688,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, BOS_ADJ_MIN_BLOCKS) adjoint_ke
         for (int c = 0; c < 8; ++c) row[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     __syncwarp();
-    CellAcc ca = {kNoKey};
+    CellAcc ca = {kNoKey, (uint32_t)S.g.n[0] * S.g.n[1] * S.g.n[2], S.g.err};
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
@@ -720,7 +722,7 @@ __device__ __forceinline__ void line_sample(const CompField<E>& F, const long lo
     int ci[3];
     comp_cell(F, U, zero, ci, p.cf);
     p.key = cell_key_of(F, ci);
-    p.v = trilinear2(F.store, cached_offset(bc, ci[0], ci[1], ci[2]), p.cf[0], p.cf[1], p.cf[2]);
+    p.v = trilinear2(F.store, comp_offset(F, bc, ci), p.cf[0], p.cf[1], p.cf[2]);
 }
 
 // Corner record of D = (1 + deta) grad at a line sample for the adjoint Db of D.
@@ -873,12 +875,11 @@ __global__ void __launch_bounds__(kAdjWarps * 32, MINB)
         for (int c = 0; c < 8; ++c) row[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     __syncwarp();
-    const CompField<E> F = {static_cast<const E*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
-                            {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
+    const CompField<E> F = comp_field<E>(S.g);
     const TileShape ts = tile_shape(S.cam.width, S.cam.height, S.cam.spp);
     const int ntiles = tile_count(S, ts);
     float* acc = reinterpret_cast<float*>(adj.acc);
-    CellAcc ca = {kNoKey};
+    CellAcc ca = {kNoKey, (uint32_t)S.g.n[0] * S.g.n[1] * S.g.n[2], S.g.err};
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(wk.tile_counter, 1);
@@ -938,8 +939,9 @@ __device__ __forceinline__ void dstage_eval(const GridDev& g, const double x[3],
         const double u = (x[a] - g.origin[a]) / g.h[a] - 0.5;
         split_coord(u, g.n[a], s.i[a], s.f[a]);
     }
-    s.g = trilinear_grad_d(static_cast<const D4*>(g.store), brick_offset(s.i[0], s.i[1], s.i[2]), s.f[0], s.f[1],
-                           s.f[2]);
+    uint32_t o = bounded(brick_offset(s.i[0], s.i[1], s.i[2]) + 91u, g.store_elems, g.err);
+    o = o ? o - 91u : 0u;
+    s.g = trilinear_grad_d(static_cast<const D4*>(g.store), o, s.f[0], s.f[1], s.f[2]);
 }
 
 __device__ __forceinline__ void drhs(const DStage& s, double D[3]) {
@@ -966,7 +968,8 @@ __device__ __forceinline__ void drhs_adjoint_scatter(const GridDev& g, const DSt
         const double w = ((c & 1) ? s.f[0] : 1.0 - s.f[0]) * ((c & 2) ? s.f[1] : 1.0 - s.f[1]) *
                          ((c & 4) ? s.f[2] : 1.0 - s.f[2]);
         const size_t node = base + (size_t)(c & 1) + (size_t)((c >> 1) & 1) * nx + (size_t)(c >> 2) * nxy;
-        for (int ch = 0; ch < 4; ++ch) atomicAdd(acc + node * 4 + ch, w * Q[ch]);
+        const size_t nd = bounded(node, (size_t)g.n[0] * g.n[1] * g.n[2], g.err);
+        for (int ch = 0; ch < 4; ++ch) atomicAdd(acc + nd * 4 + ch, w * Q[ch]);
     }
 }
 
@@ -1020,9 +1023,10 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_fp64_kernel(SceneDev S
                 if (seg) {
                     // ---- recompute the segment from its checkpoint (full_step's operations)
                     double r[3], v[3];
+                    const size_t cc = bounded((size_t)c, (size_t)ck.max_ckpt, ck.err);
                     for (int q = 0; q < 3; ++q) {
-                        r[q] = ckd[((size_t)c * 6 + q) * ck.nrays + slot];
-                        v[q] = ckd[((size_t)c * 6 + 3 + q) * ck.nrays + slot];
+                        r[q] = ckd[(cc * 6 + q) * ck.nrays + slot];
+                        v[q] = ckd[(cc * 6 + 3 + q) * ck.nrays + slot];
                     }
                     for (int n = n0; n < n1; ++n) {
                         double* p = buf + (size_t)(n - n0) * 6 * 32 + lane;
@@ -1130,7 +1134,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_fp64_kernel(SceneDev S
                     const double w = ((c & 1) ? se.f[0] : 1.0 - se.f[0]) * ((c & 2) ? se.f[1] : 1.0 - se.f[1]) *
                                      ((c & 4) ? se.f[2] : 1.0 - se.f[2]);
                     const size_t node = base + (size_t)(c & 1) + (size_t)((c >> 1) & 1) * nx + (size_t)(c >> 2) * nxy;
-                    atomicAdd(acc + node * 4, w * etab);
+                    atomicAdd(acc + bounded(node, (size_t)g.n[0] * g.n[1] * g.n[2], g.err) * 4, w * etab);
                 }
             }
         }
@@ -1188,7 +1192,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, QUASI ? BOS_ADJ_QUASI_MIN_BLOC
         for (int c = 0; c < 8; ++c) row[c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     __syncwarp();
-    CellAcc ca = {kNoKey};
+    CellAcc ca = {kNoKey, 0u, nullptr};
     int cur = -1;                      // job whose accumulators the rows belong to
     for (;;) {
         int g = 0;
@@ -1203,8 +1207,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32, QUASI ? BOS_ADJ_QUASI_MIN_BLOC
         }
         cur = j;
         const BatchJob& J = jobs[j];
-        const CompField<E> F = {static_cast<const E*>(J.S.g.store), {J.S.g.n[0], J.S.g.n[1], J.S.g.n[2]},
-                                {J.S.g.inv_hf[0], J.S.g.inv_hf[1], J.S.g.inv_hf[2]}};
+        ca.ncells = (uint32_t)J.S.g.n[0] * J.S.g.n[1] * J.S.g.n[2];
+        ca.err = J.S.g.err;
+        const CompField<E> F = comp_field<E>(J.S.g);
         const TileShape ts = tile_shape(J.S.cam.width, J.S.cam.height, J.S.cam.spp);
         float* acc = reinterpret_cast<float*>(J.adj.acc);
         if constexpr (QUASI)

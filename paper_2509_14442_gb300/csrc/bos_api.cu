@@ -446,6 +446,8 @@ bos_status_t bos_set_grid(bos_ctx* c, const bos_grid_desc* d, const float* T_dev
     g.prec = d->prec;
     size_t slots = (size_t)morton3(g.nb[0] - 1, g.nb[1] - 1, g.nb[2] - 1) + 1;
     size_t want = slots * kBrickCells * elem_bytes(d->prec);
+    g.store_elems = (uint32_t)(slots * kBrickCells);
+    g.err = c->err;
     bos_status_t s = dev_alloc(c, &c->store, &c->store_bytes, want, "bos_set_grid: brick store");
     if (s != BOS_OK) return s;
     g.store = c->store;
@@ -498,6 +500,7 @@ static bos_status_t render_prepare(bos_ctx* c, int mode, int save, cudaStream_t 
     S.npix = npix;
     ck = CkptDev{};
     ck.every = c->integ.ckpt_every;
+    ck.err = c->err;
     {
         TileShape ts = tile_shape(c->cam.width, c->cam.height, c->cam.spp);
         long long tiles = pix ? (npix + (32 / ts.G) - 1) / (32 / ts.G) : (long long)ts.tiles_x * ts.tiles_y;
@@ -684,6 +687,20 @@ bos_status_t bos_probe_read_l1(const void* buf, uint64_t bytes, int repeats, flo
     return e == cudaSuccess ? BOS_OK : cuda_fail(e, "bos_probe_read_l1");
 }
 
+bos_status_t bos_debug_store_bound(bos_ctx* c, uint32_t elems) {
+#if BOS_CHECKED
+    if (!c || !c->has_grid) return fail(BOS_ERR_NOT_READY, "bos_debug_store_bound: set_grid first");
+    if (elems < c->g.store_elems) c->g.store_elems = elems;
+    return BOS_OK;
+#else
+    (void)c;
+    (void)elems;
+    return fail(BOS_ERR_UNIMPLEMENTED, "bos_debug_store_bound: bounds checks exist only in the checked build");
+#endif
+}
+
+int bos_checked_build(void) { return BOS_CHECKED; }
+
 bos_status_t bos_status(bos_ctx* c) {
     if (!c) return fail(BOS_ERR_INVALID_ARG, "bos_status: NULL context");
     DeviceGuard dg(c->device);
@@ -695,6 +712,7 @@ bos_status_t bos_status(bos_ctx* c) {
         case DEV_STEP_BUDGET: return fail(BOS_ERR_DEVICE_CHECK, "a ray needed more steps than the step bound");
         case DEV_CKPT_OVERFLOW: return fail(BOS_ERR_DEVICE_CHECK, "a ray needed more checkpoints than allocated");
         case DEV_BAD_PIXEL: return fail(BOS_ERR_DEVICE_CHECK, "a pixel index of the list is outside the image");
+        case DEV_BOUNDS: return fail(BOS_ERR_DEVICE_CHECK, "an index fell outside its buffer (checked build)");
         default: return fail(BOS_ERR_DEVICE_CHECK, "device error %d", err);
     }
 }

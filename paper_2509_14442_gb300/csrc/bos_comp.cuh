@@ -22,7 +22,28 @@ struct CompField {
     const E* store;
     int n[3];
     float inv_h[3];
+    uint32_t nelem;   // store elements (the checked build's bound)
+    int* err;
 };
+
+template <class E>
+__device__ __forceinline__ CompField<E> comp_field(const GridDev& g) {
+    return CompField<E>{static_cast<const E*>(g.store), {g.n[0], g.n[1], g.n[2]}, {g.inv_hf[0], g.inv_hf[1], g.inv_hf[2]},
+                        g.store_elems, g.err};
+}
+
+// Store offset of the base corner of a cell: the x-paired elements of its 8 corners span
+// o .. o + 90 (the checked build bounds that range).
+template <class E>
+__device__ __forceinline__ uint32_t comp_offset(const CompField<E>& F, BrickCache& bc, const int ci[3]) {
+    const uint32_t o = cached_offset(bc, ci[0], ci[1], ci[2]);
+#if BOS_CHECKED
+    const uint32_t b = bounded(o + 90u, F.nelem, F.err);
+    return b ? b - 90u : 0u;
+#else
+    return o;
+#endif
+}
 
 // Cell and fraction of fixed-point straight position U plus deviation q (metres).  The
 // 32-bit fraction word becomes a float through its top 23 bits (U carries a +2^-24 bias
@@ -61,7 +82,7 @@ template <class E>
 __device__ __forceinline__ float4 comp_eval(const CompField<E>& F, const long long U[3], const float q[3],
                                             BrickCache& bc, int ci[3], float cf[3]) {
     comp_cell(F, U, q, ci, cf);
-    uint32_t o = cached_offset(bc, ci[0], ci[1], ci[2]);
+    const uint32_t o = comp_offset(F, bc, ci);
     return trilinear2(F.store, o, cf[0], cf[1], cf[2]);
 }
 

@@ -9,7 +9,40 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#ifndef BOS_CHECKED
+#define BOS_CHECKED 0   // 1: the checked build (bounds checks on every indexed device buffer)
+#endif
+
 namespace bos {
+
+// Device-side error word: first error code wins.
+enum DeviceError : int { DEV_OK = 0, DEV_STEP_BUDGET = 1, DEV_CKPT_OVERFLOW = 2, DEV_BAD_PIXEL = 3, DEV_BOUNDS = 4 };
+
+__device__ __forceinline__ void flag_error(int* err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+// Index i into a buffer of n elements.  The checked build records an index outside the
+// buffer in the error word and returns 0 instead, so the access stays inside the buffer;
+// the ordinary build returns i as it is.
+__device__ __forceinline__ uint32_t bounded(uint32_t i, uint32_t n, int* err) {
+#if BOS_CHECKED
+    if (i >= n) {
+        flag_error(err, DEV_BOUNDS);
+        return 0;
+    }
+#endif
+    return i;
+}
+__device__ __forceinline__ size_t bounded(size_t i, size_t n, int* err) {
+#if BOS_CHECKED
+    if (i >= n) {
+        flag_error(err, DEV_BOUNDS);
+        return 0;
+    }
+#endif
+    return i;
+}
 
 // ------------------------------------------------------------------ descriptors
 
@@ -25,6 +58,8 @@ struct GridDev {
     float hf[3];
     int prec;
     const void* store; // bricks: slot * 729 + (lz * 9 + ly) * 9 + lx
+    uint32_t store_elems;   // elements of the store (the checked build's bound)
+    int* err;               // the context's error word (the checked build's reports)
 };
 
 struct CamDev {
@@ -321,7 +356,8 @@ __device__ __forceinline__ void field_at(const GridDev& g, const double x[3], do
         double u = (x[a] - g.origin[a]) / g.h[a] - 0.5;
         split_coord(u, g.n[a], i[a], f[a]);
     }
-    uint32_t o = brick_offset(i[0], i[1], i[2]);
+    uint32_t o = bounded(brick_offset(i[0], i[1], i[2]) + 91u, g.store_elems, g.err);
+    o = o ? o - 91u : 0u;
     D4 v = trilinear_d(static_cast<const D4*>(g.store), o, f[0], f[1], f[2]);
     eta = 1.0 + v.x;
     grad[0] = v.y;
@@ -616,11 +652,5 @@ __device__ __forceinline__ TilePix tile_pixel(const SceneDev& S, const TileShape
     return r;
 }
 
-// Device-side error word: first error code wins.
-enum DeviceError : int { DEV_OK = 0, DEV_STEP_BUDGET = 1, DEV_CKPT_OVERFLOW = 2, DEV_BAD_PIXEL = 3 };
-
-__device__ __forceinline__ void flag_error(int* err, int code) {
-    if (err) atomicCAS(err, 0, code);
-}
 
 }  // namespace bos

@@ -207,7 +207,7 @@ __device__ __forceinline__ void comp_run(const SceneDev& S, const CompField<E>& 
         for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
         for (int n = 0; n < R.N; ++n) {
             if (state != nullptr && n % K == 0) {
-                size_t c = (size_t)(n / K);
+                const size_t c = bounded((size_t)(n / K), (size_t)ck.max_ckpt, ck.err);
                 state[(c * 3 + 0) * ck.nrays + ray] = make_float4(st.dr[0], st.dr[1], st.dr[2], st.cr[0]);
                 state[(c * 3 + 1) * ck.nrays + ray] = make_float4(st.dv[0], st.dv[1], st.dv[2], st.cr[1]);
                 state[(c * 3 + 2) * ck.nrays + ray] = make_float4(st.cv[0], st.cv[1], st.cv[2], st.cr[2]);
@@ -258,7 +258,7 @@ __device__ __forceinline__ void comp_run(const SceneDev& S, const CompField<E>& 
     } else {
         for (int n = 0; n < R.N; ++n) {
             if (state != nullptr && n % K == 0) {
-                size_t c = (size_t)(n / K);
+                const size_t c = bounded((size_t)(n / K), (size_t)ck.max_ckpt, ck.err);
                 state[(c * 3 + 0) * ck.nrays + ray] = make_float4(st.dr[0], st.dr[1], st.dr[2], st.cr[0]);
                 state[(c * 3 + 1) * ck.nrays + ray] = make_float4(st.dv[0], st.dv[1], st.dv[2], st.cr[1]);
                 state[(c * 3 + 2) * ck.nrays + ray] = make_float4(st.cv[0], st.cv[1], st.cv[2], st.cr[2]);
@@ -355,7 +355,7 @@ __device__ RayResult trace_full(const SceneDev& S, const FullField<T>& F, const 
     const T rl[3] = {r[0], r[1], r[2]}, v0[3] = {v[0], v[1], v[2]};
     for (int n = 0; n < R.N; ++n) {
         if (save != nullptr && n % ck.every == 0) {
-            const size_t c = (size_t)(n / ck.every);
+            const size_t c = bounded((size_t)(n / ck.every), (size_t)ck.max_ckpt, ck.err);
             for (int q = 0; q < 3; ++q) {
                 save[(c * 6 + q) * ck.nrays + ray] = (double)r[q];
                 save[(c * 6 + 3 + q) * ck.nrays + ray] = (double)v[q];
@@ -399,12 +399,10 @@ __device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, 
     if constexpr (MODE == 0) {
         return straight_epilogue(S, R, want_hit);
     } else if constexpr (MODE == 1) {
-        CompField<F4P> F = {static_cast<const F4P*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
-                               {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
+        const CompField<F4P> F = comp_field<F4P>(S.g);
         return trace_comp<F4P, INTEG, CONN>(S, F, R, ck, ray, want_hit, steps);
     } else if constexpr (MODE == 2) {
-        CompField<B4P> F = {static_cast<const B4P*>(S.g.store), {S.g.n[0], S.g.n[1], S.g.n[2]},
-                              {S.g.inv_hf[0], S.g.inv_hf[1], S.g.inv_hf[2]}};
+        const CompField<B4P> F = comp_field<B4P>(S.g);
         return trace_comp<B4P, INTEG, CONN>(S, F, R, ck, ray, want_hit, steps);
     } else if constexpr (MODE == 3) {
         FullField<float> F = {S.g};

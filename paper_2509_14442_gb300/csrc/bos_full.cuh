@@ -37,7 +37,9 @@ struct FullField<float> {
             float u = (x[a] - (float)g.origin[a]) * g.inv_hf[a] - 0.5f;
             split_coord(u, g.n[a], i[a], f[a]);
         }
-        return trilinear(static_cast<const F4P*>(g.store), brick_offset(i[0], i[1], i[2]), f[0], f[1], f[2]);
+        uint32_t o = bounded(brick_offset(i[0], i[1], i[2]) + 90u, g.store_elems, g.err);
+        o = o ? o - 90u : 0u;
+        return trilinear(static_cast<const F4P*>(g.store), o, f[0], f[1], f[2]);
     }
     __device__ __forceinline__ void rhs(const float x[3], float D[3]) const { rhs_of(at(x), D); }
     __device__ __forceinline__ float eta(const float x[3]) const { return 1.0f + at(x).x; }

@@ -41,6 +41,7 @@ struct CkptDev {
     // refracted projector connection (light mode 2), kept when state != nullptr:
     float4* pstate;                 // checkpoints of each slot's projector ray (same layout as state)
     float4* conn;                   // 2 per slot: (x_w - x_ref, cos/len), (x_w - a_1, 0)
+    int* err;                       // the context's error word (the checked build's reports)
 };
 
 // Grid adjoint accumulators: per node (d L/d deta, d L/d grad eta) in float32.

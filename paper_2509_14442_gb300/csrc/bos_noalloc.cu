@@ -117,6 +117,7 @@ extern "C" bos_status_t bos_render_noalloc(const bos_grid_desc* grid, const floa
     const size_t elem = grid->prec == BOS_PREC_BF16_COMP ? 16 : 32;   // store element (x pairs, or FP64 records)
     const size_t slots = (size_t)morton3(g.nb[0] - 1, g.nb[1] - 1, g.nb[2] - 1) + 1;
     const size_t store_bytes = slots * kBrickCells * elem;
+    g.store_elems = (uint32_t)(slots * kBrickCells);
     if (store_bytes > kScratchBytes - kCounterBytes)
         return refuse(BOS_ERR_INVALID_ARG,
                       "the field store of this grid needs %zu bytes; the fixed scratch holds at most %zu bytes",
@@ -174,6 +175,7 @@ extern "C" bos_status_t bos_render_noalloc(const bos_grid_desc* grid, const floa
                      : grid->prec == BOS_PREC_FP32     ? 3
                                                        : 4;
     WorkDev w{(int*)scratch, (unsigned long long*)(scratch + 64), (int*)(scratch + kErrOffset)};
+    S.g.err = w.err;
     CkptDev ck{};
     ck.every = integ->ckpt_every;
     RenderOut o{I_dev, disp_dev, nullptr};
@@ -201,6 +203,7 @@ extern "C" bos_status_t bos_noalloc_status(void) {
         case DEV_OK: return BOS_OK;
         case DEV_STEP_BUDGET: return refuse(BOS_ERR_DEVICE_CHECK, "a ray needed more steps than the step bound");
         case DEV_BAD_PIXEL: return refuse(BOS_ERR_DEVICE_CHECK, "a pixel index is outside the image");
+        case DEV_BOUNDS: return refuse(BOS_ERR_DEVICE_CHECK, "an index fell outside its buffer (checked build)");
         default: return refuse(BOS_ERR_DEVICE_CHECK, "device error %d", err);
     }
 }

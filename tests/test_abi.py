@@ -122,3 +122,20 @@ def test_tile_count_is_capped_below_int_max():
     a[2].width, a[2].height, a[2].spp = 1 << 19, 1 << 19, 1      # 2^33 tiles of 8 x 4 pixels
     assert _call_noalloc(bos, a) == bos.BOS_ERR_INVALID_ARG
     assert b"warp tiles" in bos.lib().bos_last_error()
+
+
+def test_checked_build_exports_every_symbol_and_says_so():
+    """The checked build (BOS_CHECKED=1) is the same ABI with bounds checks compiled in."""
+    import ctypes
+
+    from paper_2509_14442_gb300 import _build, bos
+
+    path = _build.build(checked=True)
+    Lc = ctypes.CDLL(path)
+    for name in declared_symbols():
+        assert hasattr(Lc, name), name
+    Lc.bos_checked_build.restype = ctypes.c_int
+    assert Lc.bos_checked_build() == 1
+    assert bos.lib().bos_checked_build() == (1 if bos.checked() else 0)
+    if not bos.checked():
+        assert bos.lib().bos_debug_store_bound(None, 0) == bos.BOS_ERR_UNIMPLEMENTED
