@@ -6,20 +6,20 @@
 // arena, a single device allocation of mem_limit_bytes made once at creation (first-fit
 // with coalescing; nothing is allocated or freed per request).
 //
-// Admitted requests are executed by batched launches on one server stream.  The field
-// build of a request is enqueued at admission; after it, the request's warp tiles join a
-// shared pool, and each batched launch (render_batch_kernel, adjoint_batch_kernel) pulls
-// warp tiles of every admitted request in its phase from one device work list: the
-// requests share the GPU at warp-tile granularity, oldest first, with a bounded amount of
-// work per launch, so a request that arrives while others run joins the next launch.  A
-// request moves from its render tiles (I_flow and, for forward + adjoint, checkpoints) to
-// L_BOS and its adjoint tiles, then the gradient epilogue; an event behind its last kernel
-// marks completion.  Launches are cut at batch boundaries rather than kept resident: the
+// Admitted requests are executed by batched launches.  The field build of a request is
+// enqueued at admission; after it, the request's warp tiles join a shared pool, and each
+// batched launch (render_batch_kernel, adjoint_batch_kernel) pulls warp tiles of admitted
+// requests in its phase from one device work list, oldest request first, up to a bounded
+// amount of work per launch, so a request that arrives while others run joins the next
+// launch.  Render launches (with the builds and L_BOS) run on one stream and adjoint
+// launches (with the gradient epilogues) on another, so the two overlap on the device and
+// fill each other's tails; a request's hand-over from its render phase to its adjoint is
+// an event.  An event behind its last kernel marks completion.  Launches are cut at batch boundaries rather than kept resident: the
 // gathers read the field stores through the non-coherent L1 path, which may assume the
 // data does not change while a kernel runs, and stores are rebuilt in recycled arena
 // memory as requests come and go.  Requests of other kinds (float64 or plain float32
-// stores, RK4, the refracted projector connection) run their own launches on the same
-// stream, in the same admission order.  No kernel waits on the host or on another kernel:
+// stores, RK4, the refracted projector connection) run their own launches on the render
+// stream, in admission order.  No kernel waits on the host or on another kernel:
 // the only waits are host-side and bounded (bos_wait, bos_server_destroy).
 //
 // The fake executor (BOS_SERVER_FAKE_EXECUTOR) runs the same admission, slot and memory
@@ -122,11 +122,14 @@ struct Req {
     double cost = 1.0;              // ray-step bound of one warp tile
     float* dLdI = nullptr;
     cudaEvent_t ev = nullptr;       // behind the request's last kernel
+    cudaEvent_t ev_hand = nullptr;  // behind its render phase and L_BOS (forward + adjoint)
+    bool handed = false;            // its first adjoint launch waits on ev_hand
 };
 
 struct Slot {
     bos_ctx* ctx = nullptr;
     cudaEvent_t ev = nullptr;       // completion of the slot's request
+    cudaEvent_t ev_hand = nullptr;  // its render phase (and L_BOS) done: the adjoint may start
     bool busy = false;
     uint64_t ticket = 0;
     std::atomic<bool> finished{false};
@@ -143,15 +146,17 @@ struct Batch {
     int* counter = nullptr;
     cudaEvent_t ev = nullptr;
     bool busy = false;
+    int phase = 0;
 };
 
 constexpr int kMaxBatchJobs = 64;       // jobs per batched launch (= the slot limit)
-constexpr int kBatches = 4;             // job-list buffers
-constexpr int kInFlight = 2;            // batched launches enqueued ahead of the GPU
-// work per batched launch, in ray-step bounds: a few milliseconds of the GPU, so that a new
-// request waits at most about that long to join
-constexpr double kRenderBudget = 2.5e8;
-constexpr double kAdjointBudget = 1.0e8;
+constexpr int kBatches = 8;             // job-list buffers
+constexpr int kInFlight = 2;            // batched launches per phase enqueued ahead of the GPU
+// Work per batched launch, in ray-step bounds (a ray's step budget, ~1.6x its actual steps):
+// ~10 ms of the GPU, long enough that the tail of a launch (its last warps finishing) is a
+// small part of it, short enough that a new request joins soon.
+constexpr double kRenderBudget = 1.0e9;
+constexpr double kAdjointBudget = 2.5e8;
 constexpr int kSegK = 64;               // segment slices of the batched Sharma adjoint hold up to 64 steps
 
 size_t scratch_bytes(const bos_request& r) {   // dL/dI between the loss and the backward
@@ -175,8 +180,9 @@ struct bos_server {
     bool stop = false;
     std::thread sched;
     size_t peak_used = 0;
-    // GPU engine
-    cudaStream_t stream = nullptr;
+    // GPU engine: stream 0 carries field builds, render launches and L_BOS; stream 1 the
+    // adjoint launches and gradient epilogues, so that the two kinds of launch overlap
+    cudaStream_t stream = nullptr, stream_adj = nullptr;
     Batch batches[kBatches];
     float* seg = nullptr;              // segment slices of the batched Sharma adjoint (in the arena)
     int num_sms = 1;
@@ -189,7 +195,7 @@ struct bos_server {
     void run();
     void launch(Req& q, Slot& s);
     void finish(Slot& s);
-    bool launch_batch();
+    bool launch_batch(int phase);
     void after_phase(Req& q);
     void fail_request(Req& q, bos_status_t e);
 };
@@ -214,6 +220,7 @@ void bos_server::fail_request(Req& q, bos_status_t e) {
     q.phase = PH_FINISH;
     q.batched = false;
     cudaStreamSynchronize(stream);
+    cudaStreamSynchronize(stream_adj);
     cudaEventRecord(q.ev, stream);
 }
 
@@ -230,6 +237,8 @@ void bos_server::launch(Req& q, Slot& s) {
     q.dLdI = (float*)region;
     q.order = admitted++;
     q.ev = s.ev;
+    q.ev_hand = s.ev_hand;
+    q.handed = false;
     void* st = (void*)stream;
     bos_status_t e = bos_set_grid(s.ctx, &r.grid, r.T_dev, st);
     if (e == BOS_OK) e = bos_set_geometry(s.ctx, &r.cam, &r.wall, &r.light, r.pattern_dev, &r.integ);
@@ -270,14 +279,18 @@ void bos_server::after_phase(Req& q) {
     if (q.phase == PH_RENDER && r.target_dev) {
         e = bos_loss_l2(r.I_dev, r.target_dev, (int64_t)r.cam.width * r.cam.height, r.loss_dev, q.dLdI, (void*)stream);
         if (e == BOS_OK) e = bos::ctx_batch_backward(s.ctx, q.dLdI, stream, &q.J);
+        if (e == BOS_OK && cudaEventRecord(q.ev_hand, stream) != cudaSuccess) e = BOS_ERR_CUDA;
         if (e == BOS_OK) {
             q.phase = PH_ADJOINT;
+            q.handed = true;
             return;
         }
     } else if (q.phase == PH_ADJOINT) {
-        e = bos::ctx_gradient(s.ctx, r.dLdT_dev, stream);
+        e = bos::ctx_gradient(s.ctx, r.dLdT_dev, stream_adj);
+        if (e == BOS_OK && cudaEventRecord(q.ev, stream_adj) != cudaSuccess) e = BOS_ERR_CUDA;
+    } else if (cudaEventRecord(q.ev, stream) != cudaSuccess) {
+        e = BOS_ERR_CUDA;
     }
-    if (e == BOS_OK && cudaEventRecord(q.ev, stream) != cudaSuccess) e = BOS_ERR_CUDA;
     if (e != BOS_OK) {
         fail_request(q, e);
         return;
@@ -285,60 +298,52 @@ void bos_server::after_phase(Req& q) {
     q.phase = PH_FINISH;
 }
 
-// Enqueue one batched launch: the phase and kernel variant of the oldest request with tiles
-// to run, and tiles of every request of that kind, oldest first, shared out of the
-// launch's work budget (every request gets at least one warp tile).
-bool bos_server::launch_batch() {
+// Enqueue one batched launch of `phase` (render on stream 0, adjoint on stream 1): the
+// kernel variant of the oldest request with tiles of that phase to run, and tiles of the
+// requests of that kind, oldest first, up to the launch's work budget (every request in the
+// launch gets at least one warp tile).
+bool bos_server::launch_batch(int phase) {
     Batch* b = nullptr;
     int inflight = 0;
     for (auto& x : batches) {
-        if (x.busy) ++inflight;
-        else if (!b) b = &x;
+        if (x.busy && x.phase == phase) ++inflight;
+        else if (!x.busy && !b) b = &x;
     }
     if (!b || inflight >= kInFlight) return false;
     Req* head = nullptr;
     for (uint64_t tk : active) {
         Req& q = reqs[tk];
-        if (q.batched && q.phase < PH_FINISH && q.next[q.phase] < q.tiles[q.phase]) {
+        if (q.batched && q.phase == phase && q.next[phase] < q.tiles[phase]) {
             head = &q;
             break;
         }
     }
     if (!head) return false;
-    const int phase = head->phase, mode = head->mode, integ = head->integ;
-    std::vector<Req*> sel;
-    double demand = 0.0;
-    for (uint64_t tk : active) {
-        Req& q = reqs[tk];
-        if (q.batched && q.phase == phase && q.mode == mode && q.integ == integ && q.next[phase] < q.tiles[phase] &&
-            (int)sel.size() < kMaxBatchJobs) {
-            sel.push_back(&q);
-            demand += q.cost * (q.tiles[phase] - q.next[phase]);
-        }
-    }
+    const int mode = head->mode, integ = head->integ;
+    cudaStream_t st = phase == PH_RENDER ? stream : stream_adj;
     const double budget = phase == PH_RENDER ? kRenderBudget : kAdjointBudget;
-    const double share = budget / (double)sel.size();
-    std::vector<int> take(sel.size());
+    std::vector<Req*> sel;
+    std::vector<int> take;
     double used = 0.0;
-    for (size_t i = 0; i < sel.size(); ++i) {
-        Req& q = *sel[i];
+    for (uint64_t tk : active) {
+        if (used >= budget || (int)sel.size() >= kMaxBatchJobs) break;
+        Req& q = reqs[tk];
+        if (!(q.batched && q.phase == phase && q.mode == mode && q.integ == integ && q.next[phase] < q.tiles[phase]))
+            continue;
         const int rem = q.tiles[phase] - q.next[phase];
-        int n = (int)std::min<double>(rem, std::max(1.0, share / q.cost));
-        take[i] = n;
+        const int n = (int)std::min<double>(rem, std::max(1.0, (budget - used) / q.cost));
+        sel.push_back(&q);
+        take.push_back(n);
         used += n * q.cost;
     }
-    for (size_t i = 0; i < sel.size() && used < budget; ++i) {   // the rest of the budget, oldest first
-        Req& q = *sel[i];
-        const int rem = q.tiles[phase] - q.next[phase] - take[i];
-        const int n = (int)std::min<double>(rem, (budget - used) / q.cost);
-        if (n > 0) {
-            take[i] += n;
-            used += n * q.cost;
-        }
-    }
     int total = 0, k_max = 1;
+    cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < sel.size(); ++i) {
         Req& q = *sel[i];
+        if (phase == PH_ADJOINT && q.handed) {   // its render phase and L_BOS ran on stream 0
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, q.ev_hand, 0);
+            q.handed = false;
+        }
         bos::BatchJob& J = b->host[i];
         J = q.J;
         J.tile0 = q.next[phase];
@@ -347,15 +352,17 @@ bool bos_server::launch_batch() {
         q.next[phase] += take[i];
         k_max = std::max(k_max, q.J.ck.every);
     }
-    cudaError_t e = cudaMemcpyAsync(b->dev, b->host, sel.size() * sizeof(bos::BatchJob), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->counter, 0, sizeof(int), stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->dev, b->host, sel.size() * sizeof(bos::BatchJob), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->counter, 0, sizeof(int), st);
     if (e == cudaSuccess)
         e = phase == PH_RENDER ? bos::launch_render_batch(mode, integ, b->dev, (int)sel.size(), total, b->counter,
-                                                          num_sms, stream)
+                                                          num_sms, st)
                                : bos::launch_adjoint_batch(mode, integ, b->dev, (int)sel.size(), total, b->counter, seg,
-                                                           integ == 2 ? 1 : kSegK, num_sms, stream);
-    if (e == cudaSuccess) e = cudaEventRecord(b->ev, stream);
+                                                           integ == 2 ? 1 : kSegK, num_sms, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev, st);
     b->busy = true;
+    b->phase = phase;
     ++n_batches;
     n_batch_tiles += (uint64_t)total;
     n_batch_jobs += sel.size();
@@ -432,8 +439,9 @@ void bos_server::run() {
             launch(q, *free_slot);
         }
         if (!fake())
-            while (launch_batch()) {
-            }
+            for (int ph = PH_RENDER; ph <= PH_ADJOINT; ++ph)
+                while (launch_batch(ph)) {
+                }
         cv.notify_all();
         if (stop && pending.empty() && !any_busy) break;
         cv.wait_for(lk, std::chrono::microseconds(fake() ? 200 : 100));
@@ -458,6 +466,7 @@ void release_gpu(bos_server* s) {
             bos_destroy(o->ctx);
         }
         if (o->ev) cudaEventDestroy(o->ev);
+        if (o->ev_hand) cudaEventDestroy(o->ev_hand);
     }
     for (auto& b : s->batches) {
         if (b.ev) cudaEventDestroy(b.ev);
@@ -466,6 +475,7 @@ void release_gpu(bos_server* s) {
         if (b.counter) cudaFree(b.counter);
     }
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->stream_adj) cudaStreamDestroy(s->stream_adj);
     if (s->base) cudaFree(s->base);
 }
 
@@ -494,7 +504,9 @@ bos_status_t bos_server_create(bos_server** out, int device, uint64_t mem_limit_
             s->base = nullptr;
             st = BOS_ERR_OOM;
         }
-        if (st == BOS_OK && cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) st = BOS_ERR_CUDA;
+        if (st == BOS_OK && (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+                             cudaStreamCreateWithFlags(&s->stream_adj, cudaStreamNonBlocking) != cudaSuccess))
+            st = BOS_ERR_CUDA;
         if (st == BOS_OK) cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, device);
         for (auto& b : s->batches) {
             if (st != BOS_OK) break;
@@ -506,7 +518,9 @@ bos_status_t bos_server_create(bos_server** out, int device, uint64_t mem_limit_
         }
         for (auto& o : s->slots) {
             if (st != BOS_OK) break;
-            if (cudaEventCreateWithFlags(&o->ev, cudaEventDisableTiming) != cudaSuccess) st = BOS_ERR_CUDA;
+            if (cudaEventCreateWithFlags(&o->ev, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&o->ev_hand, cudaEventDisableTiming) != cudaSuccess)
+                st = BOS_ERR_CUDA;
             if (st == BOS_OK) st = bos_create(&o->ctx, device, 0);
             if (st == BOS_OK) bos::ctx_bind_arena(o->ctx, nullptr, 0, s->stream);
         }
@@ -635,6 +649,7 @@ bos_status_t bos_server_destroy(bos_server* s, uint64_t timeout_ns) {
         cudaGetDevice(&prev);
         cudaSetDevice(s->device);
         cudaStreamSynchronize(s->stream);
+        cudaStreamSynchronize(s->stream_adj);
         release_gpu(s);
         cudaSetDevice(prev);
     }
