@@ -11,10 +11,10 @@
 // batched launch (render_batch_kernel, adjoint_batch_kernel) pulls warp tiles of admitted
 // requests in its phase from one device work list, oldest request first, up to a bounded
 // amount of work per launch, so a request that arrives while others run joins the next
-// launch.  Render launches (with the builds and L_BOS) run on one stream and adjoint
-// launches (with the gradient epilogues) on another, so the two overlap on the device and
-// fill each other's tails; a request's hand-over from its render phase to its adjoint is
-// an event.  An event behind its last kernel marks completion.  Launches are cut at batch boundaries rather than kept resident: the
+// launch.  Render launches (with L_BOS) run on one stream, adjoint launches (with the
+// gradient epilogues) on another and field builds on a third, so they overlap on the
+// device and fill each other's tails; a request's hand-overs from its build to its render
+// launches and from its render phase to its adjoint are events.  An event behind its last kernel marks completion.  Launches are cut at batch boundaries rather than kept resident: the
 // gathers read the field stores through the non-coherent L1 path, which may assume the
 // data does not change while a kernel runs, and stores are rebuilt in recycled arena
 // memory as requests come and go.  Requests of other kinds (float64 or plain float32
@@ -124,12 +124,15 @@ struct Req {
     cudaEvent_t ev = nullptr;       // behind the request's last kernel
     cudaEvent_t ev_hand = nullptr;  // behind its render phase and L_BOS (forward + adjoint)
     bool handed = false;            // its first adjoint launch waits on ev_hand
+    cudaEvent_t ev_build = nullptr; // behind its field build (on the build stream)
+    bool built = false;             // its first render launch waits on ev_build
 };
 
 struct Slot {
     bos_ctx* ctx = nullptr;
     cudaEvent_t ev = nullptr;       // completion of the slot's request
     cudaEvent_t ev_hand = nullptr;  // its render phase (and L_BOS) done: the adjoint may start
+    cudaEvent_t ev_build = nullptr; // its field build done: its render tiles may start
     bool busy = false;
     uint64_t ticket = 0;
     std::atomic<bool> finished{false};
@@ -183,6 +186,7 @@ struct bos_server {
     // GPU engine: stream 0 carries field builds, render launches and L_BOS; stream 1 the
     // adjoint launches and gradient epilogues, so that the two kinds of launch overlap
     cudaStream_t stream = nullptr, stream_adj = nullptr;
+    cudaStream_t stream_build = nullptr;   // field builds of batched requests, overlapping the launches
     Batch batches[kBatches];
     float* seg = nullptr;              // segment slices of the batched Sharma adjoint (in the arena)
     int num_sms = 1;
@@ -221,6 +225,7 @@ void bos_server::fail_request(Req& q, bos_status_t e) {
     q.batched = false;
     cudaStreamSynchronize(stream);
     cudaStreamSynchronize(stream_adj);
+    cudaStreamSynchronize(stream_build);
     cudaEventRecord(q.ev, stream);
 }
 
@@ -238,12 +243,22 @@ void bos_server::launch(Req& q, Slot& s) {
     q.order = admitted++;
     q.ev = s.ev;
     q.ev_hand = s.ev_hand;
-    q.handed = false;
+    q.ev_build = s.ev_build;
+    q.handed = q.built = false;
     void* st = (void*)stream;
-    bos_status_t e = bos_set_grid(s.ctx, &r.grid, r.T_dev, st);
+    // requests of the batched kinds (the ones bos::ctx_batchable accepts)
+    const bool batch = (r.grid.prec == BOS_PREC_FP32_COMP || r.grid.prec == BOS_PREC_BF16_COMP) &&
+                       (r.integ.integrator == 0 || r.integ.integrator == 2) && r.light.mode != 2 &&
+                       r.integ.ckpt_every <= 64 && (!r.target_dev || r.integ.integrator == 2 || seg != nullptr);
+    // the field build: on the build stream for a batched request (its first render launch
+    // waits for it), else in line with its own launches
+    bos_status_t e = bos_set_grid(s.ctx, &r.grid, r.T_dev, batch ? (void*)stream_build : st);
+    if (e == BOS_OK && batch && cudaEventRecord(q.ev_build, stream_build) != cudaSuccess) e = BOS_ERR_CUDA;
     if (e == BOS_OK) e = bos_set_geometry(s.ctx, &r.cam, &r.wall, &r.light, r.pattern_dev, &r.integ);
-    if (e == BOS_OK && bos::ctx_batchable(s.ctx) && (!r.target_dev || r.integ.integrator == 2 || seg != nullptr)) {
+    if (e == BOS_OK && batch && !bos::ctx_batchable(s.ctx)) e = BOS_ERR_CUDA;   // the two tests agree by construction
+    if (e == BOS_OK && batch) {
         // its warp tiles join the batched launches
+        q.built = true;
         int ntiles = 0;
         e = bos::ctx_batch_render(s.ctx, r.I_dev, r.disp_dev, r.target_dev ? 1 : 0, stream, &q.J, &ntiles, &q.cost);
         if (e == BOS_OK) {
@@ -343,6 +358,10 @@ bool bos_server::launch_batch(int phase) {
         if (phase == PH_ADJOINT && q.handed) {   // its render phase and L_BOS ran on stream 0
             if (e == cudaSuccess) e = cudaStreamWaitEvent(st, q.ev_hand, 0);
             q.handed = false;
+        }
+        if (phase == PH_RENDER && q.built) {     // its field build ran on the build stream
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, q.ev_build, 0);
+            q.built = false;
         }
         bos::BatchJob& J = b->host[i];
         J = q.J;
@@ -467,6 +486,7 @@ void release_gpu(bos_server* s) {
         }
         if (o->ev) cudaEventDestroy(o->ev);
         if (o->ev_hand) cudaEventDestroy(o->ev_hand);
+        if (o->ev_build) cudaEventDestroy(o->ev_build);
     }
     for (auto& b : s->batches) {
         if (b.ev) cudaEventDestroy(b.ev);
@@ -476,6 +496,7 @@ void release_gpu(bos_server* s) {
     }
     if (s->stream) cudaStreamDestroy(s->stream);
     if (s->stream_adj) cudaStreamDestroy(s->stream_adj);
+    if (s->stream_build) cudaStreamDestroy(s->stream_build);
     if (s->base) cudaFree(s->base);
 }
 
@@ -505,7 +526,8 @@ bos_status_t bos_server_create(bos_server** out, int device, uint64_t mem_limit_
             st = BOS_ERR_OOM;
         }
         if (st == BOS_OK && (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
-                             cudaStreamCreateWithFlags(&s->stream_adj, cudaStreamNonBlocking) != cudaSuccess))
+                             cudaStreamCreateWithFlags(&s->stream_adj, cudaStreamNonBlocking) != cudaSuccess ||
+                             cudaStreamCreateWithFlags(&s->stream_build, cudaStreamNonBlocking) != cudaSuccess))
             st = BOS_ERR_CUDA;
         if (st == BOS_OK) cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, device);
         for (auto& b : s->batches) {
@@ -519,7 +541,8 @@ bos_status_t bos_server_create(bos_server** out, int device, uint64_t mem_limit_
         for (auto& o : s->slots) {
             if (st != BOS_OK) break;
             if (cudaEventCreateWithFlags(&o->ev, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&o->ev_hand, cudaEventDisableTiming) != cudaSuccess)
+                cudaEventCreateWithFlags(&o->ev_hand, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&o->ev_build, cudaEventDisableTiming) != cudaSuccess)
                 st = BOS_ERR_CUDA;
             if (st == BOS_OK) st = bos_create(&o->ctx, device, 0);
             if (st == BOS_OK) bos::ctx_bind_arena(o->ctx, nullptr, 0, s->stream);
@@ -650,6 +673,7 @@ bos_status_t bos_server_destroy(bos_server* s, uint64_t timeout_ns) {
         cudaSetDevice(s->device);
         cudaStreamSynchronize(s->stream);
         cudaStreamSynchronize(s->stream_adj);
+        cudaStreamSynchronize(s->stream_build);
         release_gpu(s);
         cudaSetDevice(prev);
     }
