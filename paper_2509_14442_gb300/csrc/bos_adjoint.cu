@@ -118,27 +118,9 @@ struct CellAcc {
     int* err;
 };
 
-#ifndef BOS_FLUSH_OUTLINE
-#define BOS_FLUSH_OUTLINE 0
-#endif
-#if BOS_FLUSH_OUTLINE
-#define BOS_FLUSH_INLINE __noinline__
-#else
-#define BOS_FLUSH_INLINE __forceinline__
-#endif
-
-// The warp's flush of the rows of the lanes in `pend` (ballot of the lanes whose row must go).
-__device__ BOS_FLUSH_INLINE void flush_pending(float* rows, unsigned pend, bool flag, CellAcc& ca, float* acc, int nx,
-                                               int nxy);
-
 __device__ __forceinline__ void flush_rows(float* rows, bool flag, CellAcc& ca, float* acc, int nx, int nxy) {
-    const unsigned pend = __ballot_sync(0xffffffffu, flag);
+    unsigned pend = __ballot_sync(0xffffffffu, flag);
     if (!pend) return;
-    flush_pending(rows, pend, flag, ca, acc, nx, nxy);
-}
-
-__device__ BOS_FLUSH_INLINE void flush_pending(float* rows, unsigned pend, bool flag, CellAcc& ca, float* acc, int nx,
-                                               int nxy) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
     const int corner = lane >> 2;
