@@ -120,14 +120,16 @@ FP64_NOMINAL_FLOPS = 1.25e12
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the timed kernels,
 # captured by ncu on the small case of the same kernels (room_adj_small: the 256^2x192 field,
-# a 512^2 camera; one kernel, one launch) and reported for the timed launch scaled by the
-# ratio of the two launches' algorithmic HBM bytes (`algorithmic_hbm`: checkpoints by
-# ray count and step count, field store, accumulators, images).  Reported only while the
-# kernel sources still hash to the captured ones.
+# a 512^2 camera; one kernel, one launch).  The timed launch's figure is that capture with
+# its per-ray algorithmic bytes (checkpoints, path records, image) replaced by those of the
+# timed launch (`algorithmic_hbm`): the per-grid part (the field store, the accumulators)
+# is the same at both sizes.  Reported only while the kernel sources still hash to the
+# captured ones.
 TRAFFIC_SOURCES = ("bos_forward.cu", "bos_adjoint.cu", "bos_comp.cuh", "bos_device.cuh", "bos_full.cuh")
-TRAFFIC_CAPTURE = {"workload": "room_adj_small", "sha256": None,
-                   "render_kernel": None, "adjoint_kernel": None,
-                   "algorithmic": {"render_kernel": None, "adjoint_kernel": None}}
+TRAFFIC_CAPTURE = {"workload": "room_adj_small", "sha256": "a6c2ee3f5572d651d01933476ab0ddc80c33743882ce6a29c9f006c41a24d912",
+                   "render_kernel": 409570048 + 429263872, "adjoint_kernel": 953942016 + 249702912,
+                   # per-ray algorithmic bytes of the captured launches (512^2 rays, 8,650,752 checkpoints)
+                   "rays": {"render_kernel": 417333248, "adjoint_kernel": 417333248}}
 
 
 def kernel_sources_sha256() -> str:
@@ -142,22 +144,25 @@ def kernel_sources_sha256() -> str:
 
 def algorithmic_hbm(scene, ckpt_slots: int, store_bytes: int) -> dict:
     """Algorithmic DRAM bytes of one launch of the render (with checkpoints) and of the
-    adjoint: `ckpt_slots` = sum over rays of ceil(N/K) checkpoints of 48 B, plus 4 B of
-    path-length excess per ray; the field store read once; the adjoint's float4 node
-    accumulators (read and written by the atomics, 32 B per cell) and 4 B of dL/dI per
-    pixel; the render's 4 B image per pixel."""
-    ck = ckpt_slots * 48 + scene.rays * 4
-    return {"render_kernel": ck + store_bytes + scene.pixels * 4,
-            "adjoint_kernel": ck + store_bytes + scene.grid.cells * 32 + scene.pixels * 4}
+    adjoint, split into the part that grows with the rays ("rays": ckpt_slots = sum over
+    rays of ceil(N/K) checkpoints of 48 B, 4 B of path-length record per ray, the render's
+    4 B image or the adjoint's 4 B of dL/dI per pixel) and the part fixed by the grid
+    ("grid": the field store read once; for the adjoint also its float4 node accumulators,
+    read and written by the atomics, 32 B per cell).  "total" = their sum."""
+    rays = ckpt_slots * 48 + scene.rays * 4 + scene.pixels * 4
+    grid = {"render_kernel": store_bytes, "adjoint_kernel": store_bytes + scene.grid.cells * 32}
+    return {k: {"rays": rays, "grid": g, "total": rays + g} for k, g in grid.items()}
 
 
 def kernel_traffic(name: str, alg: dict):
     c = TRAFFIC_CAPTURE
-    if c["sha256"] is None or c.get(name) is None or kernel_sources_sha256() != c["sha256"]:
+    if c["sha256"] is None or c.get(name) is None or c["rays"].get(name) is None or \
+            kernel_sources_sha256() != c["sha256"]:
         return None
-    return {"bytes": c[name] * alg[name] / c["algorithmic"][name], "captured_bytes": c[name],
-            "captured_on": c["workload"], "scale": alg[name] / c["algorithmic"][name],
-            "scaling": "captured DRAM bytes x (algorithmic HBM bytes of this launch / of the captured launch)"}
+    return {"bytes": c[name] - c["rays"][name] + alg[name]["rays"], "captured_bytes": c[name],
+            "captured_on": c["workload"],
+            "scaling": "captured DRAM bytes - per-ray algorithmic bytes of the captured launch "
+                       "+ per-ray algorithmic bytes of this launch (the per-grid part is the same grid)"}
 
 
 def parse():
@@ -627,7 +632,7 @@ def kernel_entries(res, prec: str, P: dict) -> dict:
                 "frac": tflops / alu_peak if tflops is not None else None,
                 "bytes_per_ray_step": bytes_per_step, "achieved_gbs": gbs, "l2_frac": gbs / P["l2"],
                 "l1_bytes_per_ray_step": l1_bytes_per_step, "l1_achieved_gbs": l1_gbs, "l1_frac": l1_gbs / P["l1"],
-                "algorithmic_hbm_bytes": alg[name] if alg else None,
+                "algorithmic_hbm_bytes": alg[name]["total"] if alg else None,
                 "traffic": kernel_traffic(name, alg) if alg else None}
 
     k = {"render_kernel": entry(statistics.mean(res["render_ms"]), FLOPS_PER_STEP.get(integ), fwd_b, fwd_l1,

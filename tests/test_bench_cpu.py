@@ -30,27 +30,33 @@ def test_reference_arm_is_silent_on_other_ranks():
 
 
 def test_traffic_is_reported_only_for_the_captured_sources():
-    """The DRAM traffic of a timed launch is the small-case capture scaled by the ratio of
-    algorithmic HBM bytes, and only while the kernel sources hash to the captured ones."""
+    """The DRAM traffic of a timed launch is the small-case capture with its per-ray
+    algorithmic bytes replaced by the timed launch's, and only while the kernel sources
+    hash to the captured ones."""
     import bench
 
     from paper_2509_14442_gb300 import scenes
 
     sc = scenes.room((16, 16, 12), 64, 32, 1, 7, field=False)
     alg = bench.algorithmic_hbm(sc, ckpt_slots=1000, store_bytes=4096)
-    assert alg["render_kernel"] == 1000 * 48 + sc.rays * 4 + 4096 + sc.pixels * 4
-    assert alg["adjoint_kernel"] == 1000 * 48 + sc.rays * 4 + 4096 + sc.grid.cells * 32 + sc.pixels * 4
-    saved = dict(bench.TRAFFIC_CAPTURE)
+    rays = 1000 * 48 + sc.rays * 4 + sc.pixels * 4
+    assert alg["render_kernel"] == {"rays": rays, "grid": 4096, "total": rays + 4096}
+    assert alg["adjoint_kernel"]["grid"] == 4096 + sc.grid.cells * 32
+    # the committed capture: the small case's per-ray bytes follow from its own counts
+    small = scenes.room((256, 256, 192), 512, 512, 1, 7, field=False)
+    cap = bench.TRAFFIC_CAPTURE
+    assert cap["rays"]["adjoint_kernel"] == 8650752 * 48 + small.rays * 4 + small.pixels * 4
+    saved = {k: (dict(v) if isinstance(v, dict) else v) for k, v in cap.items()}
     try:
-        bench.TRAFFIC_CAPTURE.update(sha256=bench.kernel_sources_sha256(), adjoint_kernel=3.0e6,
-                                     algorithmic={"render_kernel": 1.0, "adjoint_kernel": 1.5e6})
+        cap.update(sha256=bench.kernel_sources_sha256(), adjoint_kernel=3.0e6,
+                   rays={"render_kernel": 1.0, "adjoint_kernel": 1.0e6})
         t = bench.kernel_traffic("adjoint_kernel", alg)
-        assert abs(t["bytes"] - 3.0e6 * alg["adjoint_kernel"] / 1.5e6) < 1e-6 * t["bytes"]
-        bench.TRAFFIC_CAPTURE["sha256"] = "0" * 64                        # sources changed since the capture
+        assert t["bytes"] == 3.0e6 - 1.0e6 + rays
+        cap["sha256"] = "0" * 64                                          # sources changed since the capture
         assert bench.kernel_traffic("adjoint_kernel", alg) is None
     finally:
-        bench.TRAFFIC_CAPTURE.clear()
-        bench.TRAFFIC_CAPTURE.update(saved)
+        cap.clear()
+        cap.update(saved)
 
 
 def test_reference_arm_reports_the_gpu_arms_config_and_its_measured_time(monkeypatch, capsys):
