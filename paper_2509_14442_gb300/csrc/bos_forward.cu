@@ -438,7 +438,7 @@ __device__ __forceinline__ void render_tile(const SceneDev& S, const RenderOut& 
         for (int q = 0; q < ts.samples_per_lane; ++q) {
             const int s = ts.samples_per_lane == 1 ? sl : q;
             const long long ray = ((long long)t * 32 + lane) * ts.samples_per_lane + q;   // checkpoint slot
-            Ray R = ray_setup(S, px, py, s);
+            Ray R = ray_setup<MODE != 0>(S, px, py, s);
             if (!R.wall) continue;
             if (R.N < 0) {
                 flag_error(wk.err, DEV_STEP_BUDGET);
@@ -447,7 +447,7 @@ __device__ __forceinline__ void render_tile(const SceneDev& S, const RenderOut& 
             RayResult r;
             if (MODE == 0 || (R.N == 0 && !CONN)) {
                 r = straight_epilogue(S, R, out.hit != nullptr);
-                if (R.N == 0 && ck.state != nullptr) {
+                if (MODE != 0 && R.N == 0 && ck.state != nullptr) {
                     if (MODE == 4) reinterpret_cast<double*>(ck.excess)[ray] = 0.0;
                     else ck.excess[ray] = 0.0f;
                 }

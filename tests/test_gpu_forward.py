@@ -139,6 +139,31 @@ def test_single_pixel_and_rays_missing_the_box(bos, orc):
     _check(gpu_render(wide, bos.BOS_PREC_FP32_COMP), o)
 
 
+def test_wide_view_with_tied_slab_faces(bos, orc):
+    """A 65 x 65 image centred on the cube's x-z centre line with a wide view: on both image
+    diagonals |d_x| = |d_z| exactly, so a ray leaves through an x face and a z face at the
+    same distance (a tie the slab test breaks in axis order); the centre row and column have
+    d_z = 0 or d_x = 0; border rays miss the cube.  Step counts are bit-exact and images
+    within the usual tolerances, so the slab test's ordering shortcut decides like the
+    plain evaluation."""
+    base = S.blob_cube(n=24, width=65, height=65, steps=32)
+    sc = with_camera(base, fx=40.0, fy=40.0, cx=32.5, cy=32.5).replace(
+        integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=0, ckpt_every=16))
+    o = orc.render(sc, nsteps=True)
+    n_orc = o["nsteps"].reshape(65, 65)
+    diag = np.array([n_orc[i, i] for i in range(65)])
+    assert (diag > 0).sum() >= 20 and (n_orc == 0).any()
+    ctx = bos.Context(0)
+    ctx.set_scene(sc, bos.BOS_PREC_FP32_COMP)
+    n = ctx.ray_steps().cpu().numpy()
+    ctx.close()
+    assert np.array_equal(n, o["nsteps"].reshape(-1))
+    _check(gpu_render(sc, bos.BOS_PREC_FP32_COMP), o)
+    o_ref = orc.render(sc, straight=True)
+    g_ref = gpu_render(sc, bos.BOS_PREC_FP32_COMP, reference=True)
+    assert float(np.abs(g_ref["I"] - o_ref["I"]).max()) <= 1e-5
+
+
 # ------------------------------------------------------------------ full sizes, sampled pixels
 
 @pytest.mark.slow

@@ -150,3 +150,26 @@ def test_quasi_linear_and_bf16_requests_are_batched_and_equal_alone(bos):
         assert torch.equal(d["disp"], r["disp"])
         if "dLdT" in d:
             assert torch.linalg.norm(d["dLdT"] - r["dLdT"]) <= 1e-5 * torch.linalg.norm(r["dLdT"])
+
+
+def test_server_adjoint_request_matches_oracle(bos, orc):
+    """A forward + adjoint request served through the batched launches: its loss and dL/dT
+    against the oracle's render and discrete adjoint for the same target (relative L2 of
+    the gradient as in the adjoint parity tests)."""
+    d = make(bos, 7, ((40, 40, 30), (72, 56), 1, True))
+    # a target far above the image (I <= ~0.03): the seed -2 (target - I) is then not
+    # affected by the ~1e-6 intensity rounding of either side
+    d["target"].fill_(0.2)
+    sc = d["scene"]
+    srv = bos.Server(0, 2 << 30, 2)
+    t = submit(bos, srv, d)
+    assert srv.wait(t, 60.0) == bos.BOS_OK
+    assert srv.batches()["launches"] >= 2               # a render and an adjoint launch
+    srv.close()
+    o = orc.render(sc)
+    target = d["target"].cpu().numpy().astype(np.float64)
+    loss_orc = float(((target - o["I"]) ** 2).sum())
+    assert abs(d["loss"].item() - loss_orc) <= 1e-4 * loss_orc
+    g_orc = orc.grad(sc, -2.0 * (target - o["I"]))
+    g = d["dLdT"].cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - g_orc) <= 1e-4 * np.linalg.norm(g_orc)
