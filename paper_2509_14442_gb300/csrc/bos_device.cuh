@@ -416,13 +416,9 @@ struct Ray {
 };
 
 // Slab test and step count of the straight ray rs + t d (unit d) whose direction is
-// already in R.d: wall-plane distance, traced segment [t_in, min(t_out, t_w)] and N.
-// lo_m / hi_m are the box faces minus rs and qn = (wall origin - rs) . normal.  The result
-// is that of the plain IEEE double evaluation: each face distance (face - rs) / d_a is
-// compared in order with strict inequalities (ties keep the earlier candidate), and the
-// entry and exit distances are correctly rounded divisions.  Only the two winning faces are
-// divided in float64: the winners are picked from float32 estimates, and where any other
-// candidate lies within the estimates' error of a winner, all six are divided exactly.
+// already in R.d: wall-plane distance, traced segment [t_in, min(t_out, t_w)] and N, bit-exact
+// with a plain IEEE double evaluation of the same formulas.  lo_m / hi_m are the box faces
+// minus rs and qn = (wall origin - rs) . normal.
 __device__ __forceinline__ void ray_segment(const SceneDev& S, const double rs[3], const double lo_m[3],
                                             const double hi_m[3], double qn, Ray& R) {
     R.N = 0;
@@ -435,74 +431,29 @@ __device__ __forceinline__ void ray_segment(const SceneDev& S, const double rs[3
     R.wall = den > 0.0;
     if (!R.wall) return;
     R.tw = ddiv(qn, den);
+    double t_in = 0.0, t_out = __longlong_as_double(0x7ff0000000000000LL);
+    int ia = -1, oa = -1;
     bool inside = true;
-    // float32 estimates of the entry / exit distance of each slab (the exact ones satisfy
-    // t0 <= t1: lo_m <= hi_m, and a negative d_a swaps them).  With every operand and
-    // quotient in [2^-60, 2^60] in magnitude, the conversions and the division are normal
-    // float roundings: each estimate is within 3.01 * 2^-24 (relative) of the exact quotient and
-    // has its sign.  Operands outside that range, zeros and NaNs take the exact path.
-    float e0[3], e1[3];
-    bool use[3];
-    bool close = false;
-    auto in_range = [](double x) { return fabs(x) >= 0x1p-60 && fabs(x) <= 0x1p60; };
     for (int a = 0; a < 3; ++a) {
-        use[a] = R.d[a] != 0.0;
-        if (!use[a]) {
+        if (R.d[a] == 0.0) {
             if (rs[a] < S.g.origin[a] || rs[a] > dadd(S.g.origin[a], S.g.extent[a])) inside = false;
-            e0[a] = e1[a] = 0.0f;
             continue;
         }
-        if (!in_range(R.d[a]) || !in_range(lo_m[a]) || !in_range(hi_m[a])) close = true;
-        const float df = (float)R.d[a];
-        const float l = __fdiv_rn((float)lo_m[a], df), h = __fdiv_rn((float)hi_m[a], df);
-        e0[a] = R.d[a] > 0.0 ? l : h;
-        e1[a] = R.d[a] > 0.0 ? h : l;
-        if (!in_range(e0[a]) || !in_range(e1[a])) close = true;
-    }
-    // winners of the ordered max / min on the estimates; `close` when a decision is within
-    // the estimates' error: two estimates whose exact values are in the other order differ
-    // by at most 3.01 * 2^-24 * (|x| + |y|) < 2^-20 * max(|x|, |y|); comparisons against the
-    // starting 0 are decided by the sign, which the estimates keep
-    int ia = -1, oa = -1;
-    float bi = 0.0f, bo = __int_as_float(0x7f800000);
-    auto near = [](float x, float y) { return fabsf(x - y) <= 0x1p-20f * fmaxf(fabsf(x), fabsf(y)); };
-    for (int a = 0; a < 3; ++a) {
-        if (!use[a]) continue;
-        if (e0[a] > bi) {
-            bi = e0[a];
+        double t0 = ddiv(lo_m[a], R.d[a]);
+        double t1 = ddiv(hi_m[a], R.d[a]);
+        if (t0 > t1) {
+            double t = t0;
+            t0 = t1;
+            t1 = t;
+        }
+        if (t0 > t_in) {
+            t_in = t0;
             ia = a;
         }
-        if (e1[a] < bo) {
-            bo = e1[a];
+        if (t1 < t_out) {
+            t_out = t1;
             oa = a;
         }
-    }
-    for (int a = 0; a < 3 && !close; ++a)     // a loser near a winner decided by its estimate
-        if (use[a] && ((a != ia && near(e0[a], bi)) || (a != oa && near(e1[a], bo)))) close = true;
-    double t_in = 0.0, t_out = __longlong_as_double(0x7ff0000000000000LL);
-    if (close) {
-        ia = oa = -1;
-        for (int a = 0; a < 3; ++a) {
-            if (!use[a]) continue;
-            double t0 = ddiv(lo_m[a], R.d[a]);
-            double t1 = ddiv(hi_m[a], R.d[a]);
-            if (t0 > t1) {
-                double t = t0;
-                t0 = t1;
-                t1 = t;
-            }
-            if (t0 > t_in) {
-                t_in = t0;
-                ia = a;
-            }
-            if (t1 < t_out) {
-                t_out = t1;
-                oa = a;
-            }
-        }
-    } else {
-        if (ia >= 0) t_in = ddiv(R.d[ia] > 0.0 ? lo_m[ia] : hi_m[ia], R.d[ia]);
-        if (oa >= 0) t_out = ddiv(R.d[oa] > 0.0 ? hi_m[oa] : lo_m[oa], R.d[oa]);
     }
     double t_end = R.tw;
     int ea = 3;
