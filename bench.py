@@ -126,8 +126,8 @@ FP64_NOMINAL_FLOPS = 1.25e12
 # is the same at both sizes.  Reported only while the kernel sources still hash to the
 # captured ones.
 TRAFFIC_SOURCES = ("bos_forward.cu", "bos_adjoint.cu", "bos_comp.cuh", "bos_device.cuh", "bos_full.cuh")
-TRAFFIC_CAPTURE = {"workload": "room_adj_small", "sha256": "a6c2ee3f5572d651d01933476ab0ddc80c33743882ce6a29c9f006c41a24d912",
-                   "render_kernel": 409570048 + 429263872, "adjoint_kernel": 953942016 + 249702912,
+TRAFFIC_CAPTURE = {"workload": "room_adj_small", "sha256": "2092c91fb34253f31fc5c750917ffa5f6df275f6c10693e96770b638bb97e63a",
+                   "render_kernel": 412102912 + 429808896, "adjoint_kernel": 955188992 + 249414912,
                    # per-ray algorithmic bytes of the captured launches (512^2 rays, 8,650,752 checkpoints)
                    "rays": {"render_kernel": 417333248, "adjoint_kernel": 417333248}}
 
