@@ -1229,8 +1229,7 @@ static cudaError_t launch_adjoint_batch_c(const BatchJob* jobs, int njobs, int t
                                           int k_max, int num_sms, cudaStream_t st) {
     const size_t smem = (size_t)kAdjWarps * 32 * kRow * sizeof(float);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_batch_kernel<E, QUASI>,
-                                                                  kAdjWarps * 32, smem);
+    cudaError_t e = occupancy_prefer_l1(adjoint_batch_kernel<E, QUASI>, kAdjWarps * 32, smem, per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int blocks = num_sms * per_sm < kAdjMaxBlocks ? num_sms * per_sm : kAdjMaxBlocks;
@@ -1262,7 +1261,7 @@ static cudaError_t launch_adjoint_c(const SceneDev& S, const CkptDev& ck, const 
         cudaFuncSetAttribute(adjoint_kernel<E, CONN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel<E, CONN>, kAdjWarps * 32, smem);
+    e = occupancy_prefer_l1(adjoint_kernel<E, CONN>, kAdjWarps * 32, smem, per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1 || adj.seg == nullptr) return cudaErrorInvalidConfiguration;
     const int blocks = num_sms * per_sm < kAdjMaxBlocks ? num_sms * per_sm : kAdjMaxBlocks;
@@ -1287,8 +1286,7 @@ static cudaError_t launch_adjoint_quasi_b(const SceneDev& S, const CkptDev& ck, 
                                           int num_sms, cudaStream_t st) {
     size_t smem = (size_t)kAdjWarps * 32 * kRow * sizeof(float);
     int per_sm = 0;
-    cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_quasi_kernel<E, MINB>, kAdjWarps * 32, smem);
+    cudaError_t e = occupancy_prefer_l1(adjoint_quasi_kernel<E, MINB>, kAdjWarps * 32, smem, per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     adjoint_quasi_kernel<E, MINB><<<num_sms * per_sm, kAdjWarps * 32, smem, st>>>(S, ck, adj, w);

@@ -617,8 +617,7 @@ template <int MODE, int INTEG, bool CONN, bool FEW = false>
 static cudaError_t launch_render_c(const SceneDev& S, const RenderOut& o, const WorkDev& w, const CkptDev& ck,
                                    int num_sms, cudaStream_t st) {
     int per_sm = 0;
-    cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<MODE, INTEG, CONN, FEW>, 128, 0);
+    cudaError_t e = occupancy_prefer_l1(render_kernel<MODE, INTEG, CONN, FEW>, 128, 0, per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     render_kernel<MODE, INTEG, CONN, FEW><<<num_sms * per_sm, 128, 0, st>>>(S, o, w, ck);
@@ -664,7 +663,7 @@ template <int MODE, int INTEG>
 static cudaError_t launch_render_batch_c(const BatchJob* jobs, int njobs, int total, int* counter, int num_sms,
                                          cudaStream_t st) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_batch_kernel<MODE, INTEG>, 128, 0);
+    cudaError_t e = occupancy_prefer_l1(render_batch_kernel<MODE, INTEG>, 128, 0, per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     render_batch_kernel<MODE, INTEG><<<num_sms * per_sm, 128, 0, st>>>(jobs, njobs, total, counter);
