@@ -130,8 +130,10 @@ struct Sums {
 };
 
 // Integrate one ray of the comp path (N > 0) from the pinhole rs; optionally store its
-// checkpoints every K steps in `state` (slot `ray`).  Leaves the end state in st.
-template <class E, int INTEG>
+// checkpoints every K steps in `state` (slot `ray`).  Leaves the end state in st.  CACHE:
+// the Sharma stages go through the ray's cell cache (the refracted connection's kernels,
+// which hold a second ray's state, go without: at 96 registers they spill).
+template <class E, int INTEG, bool CACHE = true>
 __device__ __forceinline__ void comp_run(const SceneDev& S, const CompField<E>& F, const double rs[3], const Ray& R,
                                          const CkptDev& ck, float4* state, long long ray, CompState& st,
                                          double& eta_in) {
@@ -139,6 +141,12 @@ __device__ __forceinline__ void comp_run(const SceneDev& S, const CompField<E>& 
     double rin[3];
     comp_setup(S, F, rs, R, st, k, eta_in, rin);
     BrickCache bc = {0xffffffffu, 0u};
+    CellRecs cr;
+    cr.o = 0xffffffffu;
+    auto eval = [&](const long long U[3], const float q[3], BrickCache& b, int ci[3], float cf[3]) {
+        if constexpr (CACHE) return comp_eval_c(F, U, q, b, cr, ci, cf);
+        else return comp_eval(F, U, q, b, ci, cf);
+    };
     const int K = ck.every;
 #ifndef BOS_FWD_PIPELINE
 #define BOS_FWD_PIPELINE 1
@@ -202,7 +210,7 @@ __device__ __forceinline__ void comp_run(const SceneDev& S, const CompField<E>& 
         BrickCache bc1 = {0xffffffffu, 0u};
         int ci[3];
         float cf[3], A[3], D[3];
-        rhs_of(comp_eval(F, st.U, st.dr, bc1, ci, cf), D);
+        rhs_of(eval(st.U, st.dr, bc1, ci, cf), D);
         const float dt = k.dt;
         for (int a = 0; a < 3; ++a) A[a] = dt * D[a];
         for (int n = 0; n < R.N; ++n) {
@@ -219,7 +227,7 @@ __device__ __forceinline__ void comp_run(const SceneDev& S, const CompField<E>& 
                 U2[a] = st.U[a] + k.dUh[a];
                 U3[a] = st.U[a] + k.dU[a];
             }
-            rhs_of(comp_eval(F, U2, q, bc, ci, cf), D);
+            rhs_of(eval(U2, q, bc, ci, cf), D);
             for (int a = 0; a < 3; ++a) B[a] = dt * D[a];
             for (int a = 0; a < 3; ++a) {
                 q[a] = st.dr[a] + dt * st.dv[a] + (0.5f * dt) * B[a];
@@ -233,11 +241,11 @@ __device__ __forceinline__ void comp_run(const SceneDev& S, const CompField<E>& 
             }
             // independent: stage 3 of this step and stage 1 of the next
             float D1[3] = {0.0f, 0.0f, 0.0f};
-            rhs_of(comp_eval(F, U3, q, bc, ci, cf), D);
+            rhs_of(eval(U3, q, bc, ci, cf), D);
             if (n + 1 < R.N) {
                 int ci1[3];
                 float cf1[3];
-                rhs_of(comp_eval(F, U3, dr1, bc1, ci1, cf1), D1);
+                rhs_of(eval(U3, dr1, bc1, ci1, cf1), D1);
             }
             for (int a = 0; a < 3; ++a) {
                 C[a] = dt * D[a];
@@ -287,7 +295,7 @@ __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const 
     if (R.N > 0) {
         CompState st;
         double eta_in;
-        comp_run<E, INTEG>(S, F, S.cam.pos, R, ck, ck.state, ray, st, eta_in);
+        comp_run<E, INTEG, !CONN>(S, F, S.cam.pos, R, ck, ck.state, ray, st, eta_in);
         if (ck.state != nullptr) ck.excess[ray] = st.excess;
         steps += (unsigned long long)R.N;
         float dr[3], dv[3];
@@ -312,7 +320,7 @@ __device__ RayResult trace_comp(const SceneDev& S, const CompField<E>& F, const 
                 if (Rp.wall && Rp.N > 0) {
                     CompState sp;
                     double eta_p;
-                    comp_run<E, INTEG>(S, F, P, Rp, ck, m == 0 ? ck.pstate : nullptr, ray, sp, eta_p);
+                    comp_run<E, INTEG, !CONN>(S, F, P, Rp, ck, m == 0 ? ck.pstate : nullptr, ray, sp, eta_p);
                     steps += (unsigned long long)Rp.N;
                     float pr[3], pv[3];
                     comp_end(sp, pr, pv);
@@ -418,9 +426,17 @@ __device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, 
 #ifndef BOS_FWD_MIN_BLOCKS
 #define BOS_FWD_MIN_BLOCKS 6              // resident 128-thread blocks per SM the register budget is cut for
 #endif
+#ifndef BOS_FWD_CACHED_MIN_BLOCKS
+#define BOS_FWD_CACHED_MIN_BLOCKS 5       // the same for the Sharma tracer on the paired float32 store, whose
+#endif                                    // cell cache holds 32 more values per ray (96 registers)
 #ifndef BOS_FWD_QUASI_MIN_BLOCKS
 #define BOS_FWD_QUASI_MIN_BLOCKS 3        // the same for quasi-linear tracing (more registers, more overlap)
 #endif
+constexpr int render_min_blocks(int mode, int integ, bool conn) {
+    return integ == 2 ? BOS_FWD_QUASI_MIN_BLOCKS
+                      : (mode == 1 && integ == 0 && !conn && BOS_FWD_PIPELINE) ? BOS_FWD_CACHED_MIN_BLOCKS
+                                                                              : BOS_FWD_MIN_BLOCKS;
+}
 // One warp tile of a render: the rays of its (up to) 32 lanes, averaged per pixel, written
 // to the outputs; adds the traced ray-steps to my_steps.
 template <int MODE, int INTEG, bool CONN>
@@ -491,7 +507,7 @@ __device__ __forceinline__ void add_steps(unsigned long long* steps, unsigned lo
 // FEW: the form for launches with few warp tiles (a pixel minibatch), without a register
 // cap: the GPU is not full either way, and each ray finishes sooner without spills.
 template <int MODE, int INTEG, bool CONN, bool FEW = false>
-__global__ void __launch_bounds__(128, FEW ? 1 : INTEG == 2 ? BOS_FWD_QUASI_MIN_BLOCKS : BOS_FWD_MIN_BLOCKS)
+__global__ void __launch_bounds__(128, FEW ? 1 : render_min_blocks(MODE, INTEG, CONN))
     render_kernel(SceneDev S, RenderOut out, WorkDev wk, CkptDev ck) {
     const TileShape ts = tile_shape(S.cam.width, S.cam.height, S.cam.spp);
     const int ntiles = tile_count(S, ts);
@@ -512,7 +528,7 @@ __global__ void __launch_bounds__(128, FEW ? 1 : INTEG == 2 ? BOS_FWD_QUASI_MIN_
 // jobs[j + 1].first and is that job's tile jobs[j].tile0 + (g - jobs[j].first).  Warps
 // pull items in order, so the jobs' tiles are interleaved as they are listed.
 template <int MODE, int INTEG>
-__global__ void __launch_bounds__(128, INTEG == 2 ? BOS_FWD_QUASI_MIN_BLOCKS : BOS_FWD_MIN_BLOCKS)
+__global__ void __launch_bounds__(128, render_min_blocks(MODE, INTEG, false))
     render_batch_kernel(const BatchJob* __restrict__ jobs, int njobs, int total, int* counter) {
     const int lane = threadIdx.x & 31;
     for (;;) {
