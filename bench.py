@@ -126,8 +126,8 @@ FP64_NOMINAL_FLOPS = 1.25e12
 # is the same at both sizes.  Reported only while the kernel sources still hash to the
 # captured ones.
 TRAFFIC_SOURCES = ("bos_forward.cu", "bos_adjoint.cu", "bos_comp.cuh", "bos_device.cuh", "bos_full.cuh")
-TRAFFIC_CAPTURE = {"workload": "room_adj_small", "sha256": "f71f9de872cb3de9fe35a1c563604fdd4699f3f3e961cc9b77f0aa810a39ab20",
-                   "render_kernel": 409386240 + 428757248, "adjoint_kernel": 952242432 + 244201472,
+TRAFFIC_CAPTURE = {"workload": "room_adj_small", "sha256": "b064b9f20783b67499183f9337622324512056778dd37799586aeb6269fecb29",
+                   "render_kernel": 406876672 + 430358016, "adjoint_kernel": 953205760 + 244881408,
                    # per-ray algorithmic bytes of the captured launches (512^2 rays, 8,650,752 checkpoints)
                    "rays": {"render_kernel": 417333248, "adjoint_kernel": 417333248}}
 
@@ -637,6 +637,9 @@ def kernel_entries(res, prec: str, P: dict) -> dict:
 
     k = {"render_kernel": entry(statistics.mean(res["render_ms"]), FLOPS_PER_STEP.get(integ), fwd_b, fwd_l1,
                                 "render_kernel")}
+    if prec == "fp32_comp" and integ == "rkn" and scene.light.mode != 2:
+        k["render_kernel"]["l1_note"] = ("algorithmic gathered bytes: the tracer keeps each ray's last cell in "
+                                         "registers, so most stages load nothing through L1")
     if wl["adjoint"]:
         k["adjoint_kernel"] = entry(statistics.mean(res["back_ms"]), ADJ_FLOPS_PER_STEP.get(integ), adj_b, adj_l1,
                                     "adjoint_kernel")
@@ -723,7 +726,7 @@ def gpu_arm(args):
                        "bytes_per_ray_step": dk["l1_bytes_per_ray_step"],
                        "peak_source": "in-run L1 read probe (bos_probe_read_l1, 256-bit loads, 64 KiB x 200 passes "
                                       "per block, best of 10)",
-                       "note": "the gathers' bytes loaded through L1 per ray-step over the L1 read bandwidth"},
+                       "note": "the gathers' algorithmic bytes per ray-step over the L1 read bandwidth"},
                 "hbm_peak_gbs": P["file"].get("hbm_gbs")}
     if P["file"].get("hbm_gbs"):
         # the same kernel against the HBM roofline: DRAM bytes per launch (measured on the
