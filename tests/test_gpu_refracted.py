@@ -74,6 +74,21 @@ def gpu_grad(bos, scene, w):
     return out
 
 
+@pytest.mark.parametrize("spp", [1, 3])
+def test_camera_rays_are_identical_with_and_without_the_cell_cache(bos, spp):
+    """The Sharma tracer on the paired float32 store reuses each ray's last cell; the kernels
+    of the refracted connection trace their camera rays without that cache.  The camera
+    rays' wall hits and displacements do not depend on the light, so the two renders of one
+    scene must agree bit for bit: the cache changes where the records come from, not the
+    arithmetic."""
+    sc = refracted(S.room((64, 64, 48), 96, 72, spp, 4150 + spp))
+    a = gpu_render(straight_connection(sc), bos.BOS_PREC_FP32_COMP, hit=True)   # cached tracer
+    b = gpu_render(sc, bos.BOS_PREC_FP32_COMP, hit=True)                        # uncached tracer
+    assert np.abs(a["disp"]).max() > 0
+    assert np.array_equal(a["disp"], b["disp"])
+    assert np.array_equal(a["hit"], b["hit"])
+
+
 @pytest.mark.parametrize("spp", [1, 2])
 def test_refracted_gradient_matches_oracle(bos, orc, spp):
     sc = refracted(S.room((40, 40, 30), 70, 52, spp, 4200 + spp))
