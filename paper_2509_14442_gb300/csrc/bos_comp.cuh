@@ -2,8 +2,6 @@
 // adjoint kernels so that the adjoint recomputes exactly the forward's arithmetic.
 #pragma once
 
-#include <type_traits>
-
 #include "bos_device.cuh"
 
 namespace bos {
@@ -88,23 +86,32 @@ __device__ __forceinline__ float4 comp_eval(const CompField<E>& F, const long lo
     return trilinear2(F.store, o, cf[0], cf[1], cf[2]);
 }
 
-// The four paired records of the last cell a ray gathered (paired float32 store).  A ray's
-// consecutive stage points are a quarter of a voxel apart or less, and the next step's first
-// stage is within rounding of this step's third, so most evaluations find their cell here
-// and load nothing; the interpolation is the same operations on the same records as
-// `trilinear2`, so the values are bit-identical.
+// The four paired records of the last cell a ray gathered, as the first interpolation level
+// uses them: each record and its x difference.  A ray's consecutive stage points are a
+// quarter of a voxel apart or less, and the next step's first stage is within rounding of
+// this step's third, so most evaluations find their cell here and load (and, for the
+// bfloat16 store, widen) nothing; the interpolation is the same operations on the same
+// values as `trilinear2`, so the results are bit-identical.
 struct CellRecs {
     uint32_t o;            // element offset of the cached cell's base corner (0xffffffff: none)
     Cell2 v[4], d[4];      // pairs at o, o + 9, o + 81, o + 90: records and x differences
 };
 
-__device__ __forceinline__ float4 trilinear_cached(const F4P* s, uint32_t o, float f0, float f1, float f2,
-                                                   CellRecs& c) {
+__device__ __forceinline__ void load_rec(const F4P* s, uint32_t o, Cell2& v, Cell2& d) { load_pair(s, o, v, d); }
+__device__ __forceinline__ void load_rec(const B4P* s, uint32_t o, Cell2& v, Cell2& d) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(s + o));
+    const Cell2 b = bf16_cell(make_uint2(u.z, u.w));
+    v = bf16_cell(make_uint2(u.x, u.y));
+    d = Cell2{sub2(b.lo, v.lo), sub2(b.hi, v.hi)};
+}
+
+template <class E>
+__device__ __forceinline__ float4 trilinear_cached(const E* s, uint32_t o, float f0, float f1, float f2, CellRecs& c) {
     if (o != c.o) {   // per lane: lanes whose cell is cached issue no load
-        load_pair(s, o, c.v[0], c.d[0]);
-        load_pair(s, o + 9, c.v[1], c.d[1]);
-        load_pair(s, o + 81, c.v[2], c.d[2]);
-        load_pair(s, o + 90, c.v[3], c.d[3]);
+        load_rec(s, o, c.v[0], c.d[0]);
+        load_rec(s, o + 9, c.v[1], c.d[1]);
+        load_rec(s, o + 81, c.v[2], c.d[2]);
+        load_rec(s, o + 90, c.v[3], c.d[3]);
         c.o = o;
     }
     const f32x2 t0 = pack2(f0, f0), t1 = pack2(f1, f1), t2 = pack2(f2, f2);
@@ -118,17 +125,13 @@ __device__ __forceinline__ float4 trilinear_cached(const F4P* s, uint32_t o, flo
     return v;
 }
 
-// comp_eval through the cell cache (paired float32 store); other stores gather every time.
+// comp_eval through the cell cache (the paired float32 and bfloat16 stores).
 template <class E>
 __device__ __forceinline__ float4 comp_eval_c(const CompField<E>& F, const long long U[3], const float q[3],
                                               BrickCache& bc, CellRecs& cr, int ci[3], float cf[3]) {
-    if constexpr (std::is_same<E, F4P>::value) {
-        comp_cell(F, U, q, ci, cf);
-        const uint32_t o = comp_offset(F, bc, ci);
-        return trilinear_cached(F.store, o, cf[0], cf[1], cf[2], cr);
-    } else {
-        return comp_eval(F, U, q, bc, ci, cf);
-    }
+    comp_cell(F, U, q, ci, cf);
+    const uint32_t o = comp_offset(F, bc, ci);
+    return trilinear_cached(F.store, o, cf[0], cf[1], cf[2], cr);
 }
 
 __device__ __forceinline__ void rhs_of(float4 v, float D[3]) {

@@ -427,15 +427,15 @@ __device__ __forceinline__ RayResult trace_ray(const SceneDev& S, const Ray& R, 
 #define BOS_FWD_MIN_BLOCKS 6              // resident 128-thread blocks per SM the register budget is cut for
 #endif
 #ifndef BOS_FWD_CACHED_MIN_BLOCKS
-#define BOS_FWD_CACHED_MIN_BLOCKS 5       // the same for the Sharma tracer on the paired float32 store, whose
-#endif                                    // cell cache holds 32 more values per ray (96 registers)
+#define BOS_FWD_CACHED_MIN_BLOCKS 5       // the same for the Sharma tracer on the paired stores, whose cell
+#endif                                    // cache holds 32 more values per ray (96 registers)
 #ifndef BOS_FWD_QUASI_MIN_BLOCKS
 #define BOS_FWD_QUASI_MIN_BLOCKS 3        // the same for quasi-linear tracing (more registers, more overlap)
 #endif
 constexpr int render_min_blocks(int mode, int integ, bool conn) {
     return integ == 2 ? BOS_FWD_QUASI_MIN_BLOCKS
-                      : (mode == 1 && integ == 0 && !conn && BOS_FWD_PIPELINE) ? BOS_FWD_CACHED_MIN_BLOCKS
-                                                                              : BOS_FWD_MIN_BLOCKS;
+                      : ((mode == 1 || mode == 2) && integ == 0 && !conn && BOS_FWD_PIPELINE) ? BOS_FWD_CACHED_MIN_BLOCKS
+                                                                                             : BOS_FWD_MIN_BLOCKS;
 }
 // One warp tile of a render: the rays of its (up to) 32 lanes, averaged per pixel, written
 // to the outputs; adds the traced ray-steps to my_steps.
