@@ -126,8 +126,8 @@ FP64_NOMINAL_FLOPS = 1.25e12
 # is the same at both sizes.  Reported only while the kernel sources still hash to the
 # captured ones.
 TRAFFIC_SOURCES = ("bos_forward.cu", "bos_adjoint.cu", "bos_comp.cuh", "bos_device.cuh", "bos_full.cuh")
-TRAFFIC_CAPTURE = {"workload": "room_adj_small", "sha256": "b064b9f20783b67499183f9337622324512056778dd37799586aeb6269fecb29",
-                   "render_kernel": 406876672 + 430358016, "adjoint_kernel": 953205760 + 244881408,
+TRAFFIC_CAPTURE = {"workload": "room_adj_small", "sha256": "7fac1ee6e2e1104ea8741aca7bf56e4f7191c9d44ffaa67a74c5589f51ee5e94",
+                   "render_kernel": 409746176 + 430900736, "adjoint_kernel": 952656896 + 245624320,
                    # per-ray algorithmic bytes of the captured launches (512^2 rays, 8,650,752 checkpoints)
                    "rays": {"render_kernel": 417333248, "adjoint_kernel": 417333248}}
 
