@@ -144,8 +144,8 @@ def test_wide_view_with_tied_slab_faces(bos, orc):
     diagonals |d_x| = |d_z| exactly, so a ray leaves through an x face and a z face at the
     same distance (a tie the slab test breaks in axis order); the centre row and column have
     d_z = 0 or d_x = 0; border rays miss the cube.  Step counts are bit-exact and images
-    within the usual tolerances, so the slab test's ordering shortcut decides like the
-    plain evaluation."""
+    within the usual tolerances: the slab test breaks ties like the oracle's plain float64
+    evaluation, and the straight reference render (which skips the slab test) agrees too."""
     base = S.blob_cube(n=24, width=65, height=65, steps=32)
     sc = with_camera(base, fx=40.0, fy=40.0, cx=32.5, cy=32.5).replace(
         integ=S.Integrator(fixed_steps=0, max_step_vox=0.5, integrator=0, ckpt_every=16))
